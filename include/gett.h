@@ -1,0 +1,254 @@
+/*
+ * gett.h -- C ABI of the GB300 (sm_103a) xGETT library.
+ *
+ * The operation is the binary tensor contraction of Hornblad, "BLAS-like
+ * Interface for Binary Tensor Contractions" (arXiv 2410.06770):
+ *
+ *   C[o] <- C[o] + sum over contracted coordinates kappa of A[...] * B[...]
+ *
+ * (Sec. 2.2, the contraction equation; Sec. 5, Alg. 1 adds every product to
+ * the value C already holds, so C is ACCUMULATED into, never overwritten).
+ *
+ * Argument order and meaning are those of the final interface (Sec. 4.7):
+ *
+ *   xGETT(RANKA, EXTA, INCA, A,  RANKB, EXTB, INCB, B,
+ *         CONTS, CONTA, CONTB, PERM,  INCC, C)
+ *
+ *   RANKA, RANKB  rank of A / B (>= 0; rank 0 is a scalar).
+ *   EXTA, EXTB    extents, one per mode (>= 0).  Host arrays, read during
+ *                 the call only; may be NULL when the rank is 0.
+ *   INCA, INCB    increments in ELEMENTS (not bytes) between neighbours
+ *                 along each mode; may be negative (Sec. 6, negative
+ *                 increment tests) or zero (broadcast).  Host arrays.
+ *   A, B          DEVICE pointers to the element whose coordinates are all
+ *                 zero (the "first used data point", Sec. 4.1); with a
+ *                 negative increment the other elements lie below it.
+ *                 Read only; A and B may alias each other.
+ *   CONTS         number of contracted mode pairs (0 <= CONTS <=
+ *                 min(RANKA, RANKB)).
+ *   CONTA, CONTB  0-based mode indices; CONTA[t] of A is summed against
+ *                 CONTB[t] of B, extents must match.  Host arrays; may be
+ *                 NULL when CONTS is 0.  Entries of each list are distinct.
+ *   PERM          length r_C = RANKA + RANKB - 2*CONTS.  The free indices
+ *                 are A's non-contracted modes in ascending order followed
+ *                 by B's; PERM[p] is the 0-based OUTPUT POSITION of free
+ *                 index p (Sec. 4.6, the fourth encoding).  Must be a
+ *                 permutation of 0..r_C-1.  Host array.
+ *   INCC          r_C increments of C in elements, indexed by output
+ *                 position (the "array of two values" wording of Sec. 4.7 is
+ *                 left over from the matrix stage; Sec. 4.4 generalises LD
+ *                 to one increment per mode).  Host array.
+ *   C             DEVICE pointer to C's coordinate-zero element; read and
+ *                 written.  Elements outside the logical tensor (gaps of a
+ *                 sub-tensor) are never touched.
+ *
+ * Extents of C follow from the arguments: EXTC[PERM[p]] = extent of free
+ * index p.  A zero free extent means there is nothing to do; a zero
+ * contracted extent adds an empty sum (C unchanged).
+ *
+ * Types: s = float, d = double, c = interleaved single complex, z =
+ * interleaved double complex (Sec. 4, prefixes); complex products are not
+ * conjugated.  Extension: sbgett takes bfloat16 A and B and a float C.
+ *
+ * Errors.  Every entry point returns a gett_status.  GETT_ERR_ARG: an
+ * argument is invalid; gett_last_error_arg() then returns its 1-based
+ * position (1..14, xerbla style) for the calling thread.  GETT_ERR_ALIAS: C
+ * overlaps A or B, or C's layout maps two coordinates to the same element
+ * (checked by a sufficient test on sorted increments).  GETT_ERR_UNSUPPORTED:
+ * more than GETT_MAX_MODES modes of extent > 1 remain in one class after
+ * mode fusion.  GETT_ERR_CUDA: a CUDA call failed (gett_last_cuda_error()
+ * gives the cudaError_t).  GETT_ERR_TIMEOUT: a device-side wait exceeded its
+ * iteration limit; the kernel gave up and the result is undefined.
+ *
+ * Synchronous forms (xgett) run on the legacy default stream and return
+ * after the contraction finished.  _async forms enqueue on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) and return at once; device
+ * errors of async calls are reported by gett_device_status().
+ *
+ * There is no CPU fallback: without a usable CUDA device every call returns
+ * GETT_ERR_CUDA.
+ */
+#ifndef GETT_H
+#define GETT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GETT_MAX_RANK 64   /* per tensor, as passed by the caller          */
+#define GETT_MAX_MODES 24  /* per M/N/K class after squeezing and fusion   */
+
+typedef enum gett_status {
+    GETT_OK = 0,
+    GETT_ERR_ARG = -1,
+    GETT_ERR_ALIAS = -2,
+    GETT_ERR_UNSUPPORTED = -3,
+    GETT_ERR_CUDA = -4,
+    GETT_ERR_TIMEOUT = -5,
+    GETT_ERR_NOMEM = -6
+} gett_status;
+
+typedef struct gett_complex_float { float re, im; } gett_complex_float;
+typedef struct gett_complex_double { double re, im; } gett_complex_double;
+
+/* ---------------------------------------------------------------------- */
+/* Plain xGETT (Sec. 4.7).  Synchronous.                                   */
+/* ---------------------------------------------------------------------- */
+int sgett(int RANKA, const int64_t *EXTA, const int64_t *INCA, const float *A,
+          int RANKB, const int64_t *EXTB, const int64_t *INCB, const float *B,
+          int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+          const int64_t *INCC, float *C);
+int dgett(int RANKA, const int64_t *EXTA, const int64_t *INCA, const double *A,
+          int RANKB, const int64_t *EXTB, const int64_t *INCB, const double *B,
+          int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+          const int64_t *INCC, double *C);
+int cgett(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_float *A,
+          int RANKB, const int64_t *EXTB, const int64_t *INCB, const gett_complex_float *B,
+          int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+          const int64_t *INCC, gett_complex_float *C);
+int zgett(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_double *A,
+          int RANKB, const int64_t *EXTB, const int64_t *INCB, const gett_complex_double *B,
+          int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+          const int64_t *INCC, gett_complex_double *C);
+/* Extension (no counterpart in the thesis): bfloat16 A and B given as raw
+ * 16-bit patterns, float C, products accumulated in float. */
+int sbgett(int RANKA, const int64_t *EXTA, const int64_t *INCA, const uint16_t *A,
+           int RANKB, const int64_t *EXTB, const int64_t *INCB, const uint16_t *B,
+           int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+           const int64_t *INCC, float *C);
+
+/* ---------------------------------------------------------------------- */
+/* Stream-ordered forms: same arguments plus a cudaStream_t.               */
+/* ---------------------------------------------------------------------- */
+int sgett_async(int RANKA, const int64_t *EXTA, const int64_t *INCA, const float *A,
+                int RANKB, const int64_t *EXTB, const int64_t *INCB, const float *B,
+                int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                const int64_t *INCC, float *C, void *stream);
+int dgett_async(int RANKA, const int64_t *EXTA, const int64_t *INCA, const double *A,
+                int RANKB, const int64_t *EXTB, const int64_t *INCB, const double *B,
+                int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                const int64_t *INCC, double *C, void *stream);
+int cgett_async(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_float *A,
+                int RANKB, const int64_t *EXTB, const int64_t *INCB, const gett_complex_float *B,
+                int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                const int64_t *INCC, gett_complex_float *C, void *stream);
+int zgett_async(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_double *A,
+                int RANKB, const int64_t *EXTB, const int64_t *INCB, const gett_complex_double *B,
+                int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                const int64_t *INCC, gett_complex_double *C, void *stream);
+int sbgett_async(int RANKA, const int64_t *EXTA, const int64_t *INCA, const uint16_t *A,
+                 int RANKB, const int64_t *EXTB, const int64_t *INCB, const uint16_t *B,
+                 int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                 const int64_t *INCC, float *C, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Extended forms: algorithm / kernel-configuration choice and a report.   */
+/* ---------------------------------------------------------------------- */
+typedef enum gett_algo {
+    GETT_ALGO_DEFAULT = 0,    /* library's choice (native arithmetic)      */
+    GETT_ALGO_NATIVE = 1,     /* arithmetic in the operand type            */
+    GETT_ALGO_OZAKI_BF16 = 2, /* d/z: split-precision modular form on bf16 */
+                              /* tensor cores, fp64 recombination          */
+    GETT_ALGO_BF16X3 = 3,     /* s/c: fp32 split into 2 bf16 pieces, 3     */
+                              /* products on tensor cores                  */
+    GETT_ALGO_BF16X6 = 4      /* s/c: 3 bf16 pieces, 6 products            */
+} gett_algo;
+
+typedef enum gett_family {
+    GETT_FAMILY_AUTO = 0,
+    GETT_FAMILY_NOOP = 1,     /* empty output or empty sum                 */
+    GETT_FAMILY_DENSE = 2,    /* tiled GETT on CUDA cores / DMMA           */
+    GETT_FAMILY_OUTER = 3,    /* streaming: no contracted extent > 1       */
+    GETT_FAMILY_REDUCE = 4,   /* streaming: few outputs, long sums         */
+    GETT_FAMILY_SKINNY = 5,   /* streaming: a free extent <= 8             */
+    GETT_FAMILY_TC = 6        /* tensor-core (tcgen05) GEMM on packed data */
+} gett_family;
+
+typedef struct gett_options {
+    int algo;        /* gett_algo                                          */
+    int family;      /* gett_family; AUTO lets the selector decide         */
+    int config;      /* kernel configuration id within the family; -1 auto */
+    int split_k;     /* DENSE: number of K slices (0 = auto, 1 = none)     */
+    int moduli;      /* OZAKI_BF16: number of moduli (0 = auto)            */
+    int reserved[3];
+} gett_options;
+
+typedef struct gett_report {
+    int family;      /* family that ran                                    */
+    int config;      /* configuration that ran                             */
+    int split_k;
+    int moduli;
+    int nm, nn, nk;  /* modes per class after squeeze + fusion             */
+    int selector;    /* 0 heuristic, 1 tuning table, 2 learned model, 3 forced */
+    int64_t M, N, K; /* products of the class extents                      */
+    double flops;    /* 2*M*N*K real (8*M*N*K complex)                      */
+} gett_report;
+
+void gett_options_init(gett_options *opt);
+
+int sgett_ex(int RANKA, const int64_t *EXTA, const int64_t *INCA, const float *A,
+             int RANKB, const int64_t *EXTB, const int64_t *INCB, const float *B,
+             int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+             const int64_t *INCC, float *C,
+             const gett_options *opt, gett_report *rep, void *stream);
+int dgett_ex(int RANKA, const int64_t *EXTA, const int64_t *INCA, const double *A,
+             int RANKB, const int64_t *EXTB, const int64_t *INCB, const double *B,
+             int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+             const int64_t *INCC, double *C,
+             const gett_options *opt, gett_report *rep, void *stream);
+int cgett_ex(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_float *A,
+             int RANKB, const int64_t *EXTB, const int64_t *INCB, const gett_complex_float *B,
+             int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+             const int64_t *INCC, gett_complex_float *C,
+             const gett_options *opt, gett_report *rep, void *stream);
+int zgett_ex(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_double *A,
+             int RANKB, const int64_t *EXTB, const int64_t *INCB, const gett_complex_double *B,
+             int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+             const int64_t *INCC, gett_complex_double *C,
+             const gett_options *opt, gett_report *rep, void *stream);
+int sbgett_ex(int RANKA, const int64_t *EXTA, const int64_t *INCA, const uint16_t *A,
+              int RANKB, const int64_t *EXTB, const int64_t *INCB, const uint16_t *B,
+              int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+              const int64_t *INCC, float *C,
+              const gett_options *opt, gett_report *rep, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Planner inspection (host only, no device work).  Validates the 14       */
+/* arguments (pointers are not inspected) and describes the canonical      */
+/* problem: modes of each class after dropping extent-1 modes, flipping    */
+/* negative increments and fusing stride-compatible neighbours.            */
+/* ---------------------------------------------------------------------- */
+typedef struct gett_plan_info {
+    int nm, nn, nk;
+    int empty;                              /* nothing to compute          */
+    int64_t M, N, K;
+    int64_t m_ext[GETT_MAX_MODES], m_inca[GETT_MAX_MODES], m_incc[GETT_MAX_MODES];
+    int64_t n_ext[GETT_MAX_MODES], n_incb[GETT_MAX_MODES], n_incc[GETT_MAX_MODES];
+    int64_t k_ext[GETT_MAX_MODES], k_inca[GETT_MAX_MODES], k_incb[GETT_MAX_MODES];
+    int64_t off_a, off_b, off_c;            /* element offsets from flips   */
+} gett_plan_info;
+
+int gett_plan_describe(int RANKA, const int64_t *EXTA, const int64_t *INCA,
+                       int RANKB, const int64_t *EXTB, const int64_t *INCB,
+                       int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                       const int64_t *INCC, gett_plan_info *out);
+
+/* ---------------------------------------------------------------------- */
+/* Diagnostics.                                                            */
+/* ---------------------------------------------------------------------- */
+int gett_last_error_arg(void);       /* 1-based argument of last GETT_ERR_ARG */
+int gett_last_cuda_error(void);      /* cudaError_t of last GETT_ERR_CUDA     */
+const char *gett_status_string(int status);
+/* Reads (and clears) the device error word that kernels set when a bounded
+ * wait gives up; synchronises the device.  GETT_OK or GETT_ERR_TIMEOUT. */
+int gett_device_status(void);
+int gett_version(void);              /* major*10000 + minor*100 + patch      */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GETT_H */

@@ -1,0 +1,244 @@
+// api.cu -- the exported C ABI: argument checks, family selection, scratch
+// memory and dispatch to the kernel families.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+#include "kernels.h"
+#include "select.h"
+
+namespace gett {
+
+namespace {
+
+struct DevState {
+    bool init = false;
+    int sms = 0;
+    int *err = nullptr;  // device error word written by kernels with bounded waits
+};
+DevState g_dev[64];
+std::mutex g_mu;
+
+int dev_state(DevState **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &st = g_dev[dev];
+    if (!st.init) {
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) {
+            set_last_cuda_error(e);
+            return GETT_ERR_CUDA;
+        }
+        int *err = nullptr;
+        e = cudaMalloc(&err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            set_last_cuda_error(e);
+            return GETT_ERR_CUDA;
+        }
+        st.sms = sms;
+        st.err = err;
+        st.init = true;
+    }
+    *out = &st;
+    return GETT_OK;
+}
+
+size_t out_elem_size(DType t) { return t == DT_BF16 ? 4 : dtype_size(t); }
+size_t in_align(DType t) { return t == DT_C64 ? 16 : (t == DT_C32 ? 8 : dtype_size(t)); }
+size_t out_align(DType t) { return t == DT_BF16 ? 4 : in_align(t); }
+
+bool ranges_overlap(const void *p, int64_t lo, int64_t hi, size_t esz, const void *q, int64_t qlo,
+                    int64_t qhi, size_t qesz)
+{
+    auto a0 = reinterpret_cast<intptr_t>(p) + (intptr_t)(lo * (int64_t)esz);
+    auto a1 = reinterpret_cast<intptr_t>(p) + (intptr_t)((hi + 1) * (int64_t)esz);
+    auto b0 = reinterpret_cast<intptr_t>(q) + (intptr_t)(qlo * (int64_t)qesz);
+    auto b1 = reinterpret_cast<intptr_t>(q) + (intptr_t)((qhi + 1) * (int64_t)qesz);
+    return a0 < b1 && b0 < a1;
+}
+
+cudaError_t run_family(const Plan &p, DType t, const Choice &ch, const void *A, const void *B, void *C,
+                       const DevState &st, cudaStream_t s)
+{
+    size_t ws_bytes = 0;
+    if (ch.family == GETT_FAMILY_DENSE) ws_bytes = dense_workspace_bytes(p, t, ch.config, ch.split_k);
+    else if (ch.family == GETT_FAMILY_REDUCE) ws_bytes = reduce_workspace_bytes(p, t, st.sms);
+    void *ws = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (ws_bytes) {
+        e = cudaMallocAsync(&ws, ws_bytes, s);
+        if (e != cudaSuccess) return e;
+    }
+    switch (ch.family) {
+    case GETT_FAMILY_DENSE: e = launch_dense(p, t, A, B, C, ch.config, ch.split_k, ws, s); break;
+    case GETT_FAMILY_OUTER: e = launch_outer(p, t, A, B, C, st.sms, s); break;
+    case GETT_FAMILY_REDUCE: e = launch_reduce(p, t, A, B, C, st.sms, ws, s); break;
+    default: e = cudaErrorInvalidValue; break;
+    }
+    if (ws) {
+        cudaError_t f = cudaFreeAsync(ws, s);
+        if (e == cudaSuccess) e = f;
+    }
+    return e;
+}
+
+int run(DType t, const Args &a, const void *A, const void *B, void *C, const gett_options *opt,
+        gett_report *rep, cudaStream_t s, bool sync)
+{
+    Plan p;
+    int bad = 0;
+    int rc = make_plan(a, &p, &bad);
+    set_last_error_arg(bad);
+    if (rc != GETT_OK) return rc;
+    if (rep) {
+        std::memset(rep, 0, sizeof(*rep));
+        rep->family = GETT_FAMILY_NOOP;
+    }
+    if (p.empty) return GETT_OK;
+    const size_t esz = dtype_size(t), osz = out_elem_size(t);
+    if (!A || reinterpret_cast<uintptr_t>(A) % in_align(t)) { set_last_error_arg(4); return GETT_ERR_ARG; }
+    if (!B || reinterpret_cast<uintptr_t>(B) % in_align(t)) { set_last_error_arg(8); return GETT_ERR_ARG; }
+    if (!C || reinterpret_cast<uintptr_t>(C) % out_align(t)) { set_last_error_arg(14); return GETT_ERR_ARG; }
+    if (ranges_overlap(C, p.c_lo, p.c_hi, osz, A, p.a_lo, p.a_hi, esz) ||
+        ranges_overlap(C, p.c_lo, p.c_hi, osz, B, p.b_lo, p.b_hi, esz))
+        return GETT_ERR_ALIAS;
+
+    DevState *st = nullptr;
+    rc = dev_state(&st);
+    if (rc != GETT_OK) return rc;
+    Choice ch;
+    rc = choose(p, t, opt, st->sms, &ch);
+    if (rc != GETT_OK) return rc;
+    if (rep) {
+        rep->family = ch.family;
+        rep->config = ch.config;
+        rep->split_k = ch.split_k;
+        rep->moduli = ch.moduli;
+        rep->selector = ch.selector;
+        rep->nm = p.m.n;
+        rep->nn = p.n.n;
+        rep->nk = p.k.n;
+        rep->M = p.M;
+        rep->N = p.N;
+        rep->K = p.K;
+        rep->flops = (t == DT_C32 || t == DT_C64 ? 8.0 : 2.0) * (double)p.M * (double)p.N * (double)p.K;
+    }
+    cudaError_t e = run_family(p, t, ch, A, B, C, *st, s);
+    if (e == cudaSuccess && sync) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    if (sync && ch.family == GETT_FAMILY_TC) {
+        int word = 0;
+        e = cudaMemcpy(&word, st->err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            set_last_cuda_error(e);
+            return GETT_ERR_CUDA;
+        }
+        if (word) {
+            cudaMemset(st->err, 0, sizeof(int));
+            return GETT_ERR_TIMEOUT;
+        }
+    }
+    return GETT_OK;
+}
+
+}  // namespace
+
+int device_sms()
+{
+    DevState *st = nullptr;
+    if (dev_state(&st) != GETT_OK) return 0;
+    return st->sms;
+}
+
+}  // namespace gett
+
+using gett::Args;
+
+#define GETT_ARGS_DECL(T)                                                                      \
+    int RANKA, const int64_t *EXTA, const int64_t *INCA, const T *A, int RANKB,               \
+        const int64_t *EXTB, const int64_t *INCB, const T *B, int CONTS, const int *CONTA,    \
+        const int *CONTB, const int *PERM, const int64_t *INCC
+#define GETT_ARGS Args{RANKA, EXTA, INCA, RANKB, EXTB, INCB, CONTS, CONTA, CONTB, PERM, INCC}
+
+#define DEFINE_ENTRY(prefix, T, TC, DT)                                                          \
+    extern "C" int prefix##gett(GETT_ARGS_DECL(T), TC *C)                                          \
+    {                                                                                             \
+        return gett::run(gett::DT, GETT_ARGS, A, B, C, nullptr, nullptr, (cudaStream_t)0, true);  \
+    }                                                                                             \
+    extern "C" int prefix##gett_async(GETT_ARGS_DECL(T), TC *C, void *stream)                      \
+    {                                                                                             \
+        return gett::run(gett::DT, GETT_ARGS, A, B, C, nullptr, nullptr, (cudaStream_t)stream,   \
+                         false);                                                                  \
+    }                                                                                             \
+    extern "C" int prefix##gett_ex(GETT_ARGS_DECL(T), TC *C, const gett_options *opt,              \
+                                   gett_report *rep, void *stream)                                \
+    {                                                                                             \
+        return gett::run(gett::DT, GETT_ARGS, A, B, C, opt, rep, (cudaStream_t)stream, true);    \
+    }
+
+DEFINE_ENTRY(s, float, float, DT_F32)
+DEFINE_ENTRY(d, double, double, DT_F64)
+DEFINE_ENTRY(c, gett_complex_float, gett_complex_float, DT_C32)
+DEFINE_ENTRY(z, gett_complex_double, gett_complex_double, DT_C64)
+DEFINE_ENTRY(sb, uint16_t, float, DT_BF16)
+
+extern "C" void gett_options_init(gett_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->algo = GETT_ALGO_DEFAULT;
+    opt->family = GETT_FAMILY_AUTO;
+    opt->config = -1;
+    opt->split_k = 0;
+    opt->moduli = 0;
+}
+
+extern "C" const char *gett_status_string(int status)
+{
+    switch (status) {
+    case GETT_OK: return "GETT_OK";
+    case GETT_ERR_ARG: return "GETT_ERR_ARG: invalid argument";
+    case GETT_ERR_ALIAS: return "GETT_ERR_ALIAS: C overlaps A/B or is not injective";
+    case GETT_ERR_UNSUPPORTED: return "GETT_ERR_UNSUPPORTED: beyond compiled limits";
+    case GETT_ERR_CUDA: return "GETT_ERR_CUDA: CUDA error";
+    case GETT_ERR_TIMEOUT: return "GETT_ERR_TIMEOUT: device wait exceeded its limit";
+    case GETT_ERR_NOMEM: return "GETT_ERR_NOMEM: out of device memory";
+    }
+    return "unknown gett_status";
+}
+
+extern "C" int gett_device_status(void)
+{
+    gett::DevState *st = nullptr;
+    int rc = gett::dev_state(&st);
+    if (rc != GETT_OK) return rc;
+    cudaError_t e = cudaDeviceSynchronize();
+    int word = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&word, st->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        gett::set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    if (word) {
+        cudaMemset(st->err, 0, sizeof(int));
+        return GETT_ERR_TIMEOUT;
+    }
+    return GETT_OK;
+}
+
+extern "C" int gett_version(void) { return 100; }

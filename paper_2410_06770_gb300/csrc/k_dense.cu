@@ -1,0 +1,357 @@
+// k_dense.cu -- tiled GETT on CUDA cores for every element type.
+//
+// The planner reduces any contraction to C[m,n] += sum_k A[m,k] B[k,n] over
+// multi-mode index sets M, N, K (Sec. 2.2 / Alg. 1 computed tile by tile
+// instead of element by element).  A setup kernel turns each class's mode
+// list into offset tables (the element offset of every flat m, n, k in the
+// tensors that carry that class), so the tiled kernel can gather a BM x BK
+// tile of A and a BK x BN tile of B through arbitrary increments -- padded,
+// negative, zero or non-unit -- and scatter the BM x BN result into C through
+// INCC/PERM.
+//
+// Staging: each thread prefetches its share of the next K tile into
+// registers while the current tile is multiplied from shared memory (double
+// buffered).  Threads walk the tile along whichever index has the smaller
+// increment so global loads coalesce.  The epilogue maps lanes along the
+// index with C's smaller increment so the read-modify-write of C coalesces.
+//
+// Split-K: with S > 1 slices each CTA sums one slice of K into a workspace
+// tile and a second kernel adds the S partial tiles into C in slice order,
+// so results do not depend on scheduling.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gett {
+
+namespace {
+
+__global__ void build_tables_kernel(ModeList L, int64_t count, int64_t *t0, int64_t *t1)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a, b;
+        decode2(L, i, a, b);
+        t0[i] = a;
+        t1[i] = b;
+    }
+}
+
+struct DenseParams {
+    const void *A;
+    const void *B;
+    void *C;
+    const int64_t *rowA, *rowC, *colB, *colC, *kA, *kB;
+    int64_t M, N, K;
+    int64_t k_per_split;
+    int tiles_m, tiles_n;
+    int a_m_fast, b_n_fast, c_m_fast;
+    void *partial;  // split-K partial tiles (Acc), null when S == 1
+};
+
+template <class T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+dense_kernel(DenseParams p)
+{
+    using R = Tr<T>;
+    using Acc = typename R::Acc;
+    using Out = typename R::Out;
+    constexpr int NT = (BM / TM) * (BN / TN);
+    constexpr int LA = BM * BK / NT;
+    constexpr int LB = BN * BK / NT;
+    static_assert(LA * NT == BM * BK && LB * NT == BN * BK, "tile/threads mismatch");
+
+    __shared__ Acc sA[2][BK][BM];
+    __shared__ Acc sB[2][BK][BN];
+    __shared__ int64_t sRowA[BM];
+    __shared__ int64_t sColB[BN];
+
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int tile_m = tile % p.tiles_m;
+    const int tile_n = tile / p.tiles_m;
+    const int64_t m0 = (int64_t)tile_m * BM;
+    const int64_t n0 = (int64_t)tile_n * BN;
+    const int split = blockIdx.y;
+    const int64_t kbeg = split * p.k_per_split;
+    const int64_t kend = min(p.K, kbeg + p.k_per_split);
+
+    const T *A = static_cast<const T *>(p.A);
+    const T *B = static_cast<const T *>(p.B);
+
+    for (int i = tid; i < BM; i += NT) sRowA[i] = (m0 + i < p.M) ? p.rowA[m0 + i] : 0;
+    for (int i = tid; i < BN; i += NT) sColB[i] = (n0 + i < p.N) ? p.colB[n0 + i] : 0;
+    __syncthreads();
+
+    Acc ra[LA], rb[LB];
+    auto load_tile = [&](int64_t k0) {
+#pragma unroll
+        for (int r = 0; r < LA; ++r) {
+            int e = tid + r * NT;
+            int mm, kk;
+            if (p.a_m_fast) { mm = e % BM; kk = e / BM; }
+            else { kk = e % BK; mm = e / BK; }
+            int64_t k = k0 + kk;
+            ra[r] = (m0 + mm < p.M && k < kend) ? R::load(A + sRowA[mm] + p.kA[k]) : R::zero();
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+            int e = tid + r * NT;
+            int nn, kk;
+            if (p.b_n_fast) { nn = e % BN; kk = e / BN; }
+            else { kk = e % BK; nn = e / BK; }
+            int64_t k = k0 + kk;
+            rb[r] = (n0 + nn < p.N && k < kend) ? R::load(B + sColB[nn] + p.kB[k]) : R::zero();
+        }
+    };
+    auto store_tile = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < LA; ++r) {
+            int e = tid + r * NT;
+            int mm, kk;
+            if (p.a_m_fast) { mm = e % BM; kk = e / BM; }
+            else { kk = e % BK; mm = e / BK; }
+            sA[buf][kk][mm] = ra[r];
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+            int e = tid + r * NT;
+            int nn, kk;
+            if (p.b_n_fast) { nn = e % BN; kk = e / BN; }
+            else { kk = e % BK; nn = e / BK; }
+            sB[buf][kk][nn] = rb[r];
+        }
+    };
+
+    int tm, tn;
+    if (p.c_m_fast) { tm = tid % (BM / TM); tn = tid / (BM / TM); }
+    else { tn = tid % (BN / TN); tm = tid / (BN / TN); }
+
+    Acc acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = R::zero();
+
+    const int64_t nkt = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+    if (nkt > 0) {
+        load_tile(kbeg);
+        store_tile(0);
+        __syncthreads();
+    }
+    for (int64_t kt = 0; kt < nkt; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nkt) load_tile(kbeg + (kt + 1) * BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            Acc a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = sA[cur][kk][tm + i * (BM / TM)];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = sB[cur][kk][tn + j * (BN / TN)];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) R::mac(acc[i][j], a[i], b[j]);
+        }
+        if (kt + 1 < nkt) store_tile(cur ^ 1);
+        __syncthreads();
+    }
+
+    // epilogue
+    if (p.partial) {
+        Acc *P = static_cast<Acc *>(p.partial) + (int64_t)split * p.M * p.N;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            int64_t m = m0 + tm + i * (BM / TM);
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                int64_t n = n0 + tn + j * (BN / TN);
+                if (m < p.M && n < p.N) P[p.c_m_fast ? n * p.M + m : m * p.N + n] = acc[i][j];
+            }
+        }
+        return;
+    }
+    Out *C = static_cast<Out *>(p.C);
+    int64_t rc[TM], cc[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int64_t m = m0 + tm + i * (BM / TM);
+        rc[i] = m < p.M ? p.rowC[m] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        int64_t n = n0 + tn + j * (BN / TN);
+        cc[j] = n < p.N ? p.colC[n] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int64_t m = m0 + tm + i * (BM / TM);
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            int64_t n = n0 + tn + j * (BN / TN);
+            if (m < p.M && n < p.N) R::store_add(C + rc[i] + cc[j], acc[i][j]);
+        }
+    }
+}
+
+template <class T>
+__global__ void splitk_reduce_kernel(DenseParams p, int S)
+{
+    using R = Tr<T>;
+    using Acc = typename R::Acc;
+    using Out = typename R::Out;
+    const Acc *P = static_cast<const Acc *>(p.partial);
+    Out *C = static_cast<Out *>(p.C);
+    const int64_t MN = p.M * p.N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m, n;
+        if (p.c_m_fast) { m = i % p.M; n = i / p.M; }
+        else { n = i % p.N; m = i / p.N; }
+        Acc s = P[i];
+        for (int t = 1; t < S; ++t) s = R::add(s, P[(int64_t)t * MN + i]);
+        R::store_add(C + p.rowC[m] + p.colC[n], s);
+    }
+}
+
+struct TileCfg {
+    int bm, bn, bk;
+};
+constexpr TileCfg kCfg[DENSE_NUM_CONFIGS] = {{128, 128, 8}, {64, 64, 8}, {32, 32, 16}};
+
+template <class T>
+bool cfg_allowed(int cfg)
+{
+    // complex double at 128x128 would need 256 accumulator registers a thread
+    return !(sizeof(T) == 16 && cfg == 0);
+}
+
+template <class T>
+cudaError_t launch_typed(const DenseParams &p, int cfg, int S, cudaStream_t s)
+{
+    dim3 grid(p.tiles_m * p.tiles_n, S);
+    switch (cfg) {
+    case 0:
+        if constexpr (sizeof(T) != 16) {
+            dense_kernel<T, 128, 128, 8, 8, 8><<<grid, 256, 0, s>>>(p);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    case 1:
+        dense_kernel<T, 64, 64, 8, 4, 4><<<grid, 256, 0, s>>>(p);
+        break;
+    case 2:
+        dense_kernel<T, 32, 32, 16, 2, 2><<<grid, 256, 0, s>>>(p);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || S == 1) return e;
+    int64_t MN = p.M * p.N;
+    int blocks = (int)std::min<int64_t>((MN + 255) / 256, 4096);
+    splitk_reduce_kernel<T><<<blocks, 256, 0, s>>>(p, S);
+    return cudaGetLastError();
+}
+
+size_t acc_size(DType t)
+{
+    switch (t) {
+    case DT_F32: case DT_BF16: return 4;
+    case DT_F64: return 8;
+    case DT_C32: return 8;
+    case DT_C64: return 16;
+    }
+    return 0;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+bool dense_config_valid(DType t, int cfg)
+{
+    if (cfg < 0 || cfg >= DENSE_NUM_CONFIGS) return false;
+    return !(t == DT_C64 && cfg == 0);
+}
+
+void dense_tile_shape(int cfg, int *bm, int *bn, int *bk)
+{
+    *bm = kCfg[cfg].bm;
+    *bn = kCfg[cfg].bn;
+    *bk = kCfg[cfg].bk;
+}
+
+size_t dense_workspace_bytes(const Plan &p, DType t, int cfg, int split_k)
+{
+    size_t tables = align256(sizeof(int64_t) * 2 * (size_t)(p.M + p.N + p.K));
+    size_t partial = split_k > 1 ? align256(acc_size(t) * (size_t)split_k * p.M * p.N) : 0;
+    (void)cfg;
+    return tables + partial;
+}
+
+cudaError_t launch_dense(const Plan &pl, DType t, const void *A, const void *B, void *C, int cfg,
+                         int split_k, void *ws, cudaStream_t s)
+{
+    if (!dense_config_valid(t, cfg)) return cudaErrorInvalidValue;
+    int64_t *tab = static_cast<int64_t *>(ws);
+    int64_t *rowA = tab, *rowC = rowA + pl.M, *colB = rowC + pl.M, *colC = colB + pl.N;
+    int64_t *kA = colC + pl.N, *kB = kA + pl.K;
+    auto build = [&](const ModeList &L, int64_t count, int64_t *t0, int64_t *t1) {
+        int blocks = (int)std::min<int64_t>((count + 255) / 256, 2048);
+        if (blocks < 1) blocks = 1;
+        build_tables_kernel<<<blocks, 256, 0, s>>>(L, count, t0, t1);
+    };
+    build(pl.m, pl.M, rowA, rowC);
+    build(pl.n, pl.N, colB, colC);
+    build(pl.k, pl.K, kA, kB);
+
+    const TileCfg c = kCfg[cfg];
+    DenseParams p{};
+    size_t esz = dtype_size(t);
+    p.A = static_cast<const char *>(A) + pl.offA * (int64_t)esz;
+    p.B = static_cast<const char *>(B) + pl.offB * (int64_t)esz;
+    size_t csz = (t == DT_BF16) ? 4 : esz;
+    p.C = static_cast<char *>(C) + pl.offC * (int64_t)csz;
+    p.rowA = rowA; p.rowC = rowC; p.colB = colB; p.colC = colC; p.kA = kA; p.kB = kB;
+    p.M = pl.M; p.N = pl.N; p.K = pl.K;
+    int S = split_k < 1 ? 1 : split_k;
+    int64_t kps = (pl.K + S - 1) / S;
+    kps = (kps + c.bk - 1) / c.bk * c.bk;
+    S = (int)((pl.K + kps - 1) / kps);
+    p.k_per_split = kps;
+    p.tiles_m = (int)((pl.M + c.bm - 1) / c.bm);
+    p.tiles_n = (int)((pl.N + c.bn - 1) / c.bn);
+    // coalescing choices: the index with the smaller increment runs fastest
+    auto first = [](const ModeList &L, const int64_t *s) { return L.n ? (s[0] < 0 ? -s[0] : s[0]) : 0; };
+    int64_t am = first(pl.m, pl.m.s0), ak = first(pl.k, pl.k.s0);
+    int64_t bn = first(pl.n, pl.n.s0), bk = first(pl.k, pl.k.s1);
+    int64_t cm = first(pl.m, pl.m.s1), cn = first(pl.n, pl.n.s1);
+    p.a_m_fast = (am != 0 && (ak == 0 || am <= ak)) ? 1 : 0;
+    p.b_n_fast = (bn != 0 && (bk == 0 || bn <= bk)) ? 1 : 0;
+    p.c_m_fast = (cm != 0 && (cn == 0 || cm <= cn)) ? 1 : 0;
+    p.partial = S > 1 ? static_cast<char *>(ws) + align256(sizeof(int64_t) * 2 * (size_t)(pl.M + pl.N + pl.K))
+                      : nullptr;
+    if ((int64_t)p.tiles_m * p.tiles_n > (int64_t)INT32_MAX || S > 65535) return cudaErrorInvalidValue;
+    switch (t) {
+    case DT_F32: return launch_typed<float>(p, cfg, S, s);
+    case DT_F64: return launch_typed<double>(p, cfg, S, s);
+    case DT_C32: return launch_typed<cf>(p, cfg, S, s);
+    case DT_C64: return launch_typed<zd>(p, cfg, S, s);
+    case DT_BF16: return launch_typed<uint16_t>(p, cfg, S, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int dense_effective_split(const Plan &pl, int cfg, int split_k)
+{
+    const TileCfg c = kCfg[cfg];
+    int S = split_k < 1 ? 1 : split_k;
+    int64_t kps = (pl.K + S - 1) / S;
+    kps = (kps + c.bk - 1) / c.bk * c.bk;
+    return (int)((pl.K + kps - 1) / kps);
+}
+
+}  // namespace gett

@@ -1,0 +1,28 @@
+// kernels.h -- host-side launchers of the xGETT kernel families.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace gett {
+
+// ---- dense tiled GETT on CUDA cores (k_dense.cu) ----
+constexpr int DENSE_NUM_CONFIGS = 3;
+bool dense_config_valid(DType t, int cfg);
+void dense_tile_shape(int cfg, int *bm, int *bn, int *bk);
+size_t dense_workspace_bytes(const Plan &p, DType t, int cfg, int split_k);
+int dense_effective_split(const Plan &p, int cfg, int split_k);
+cudaError_t launch_dense(const Plan &p, DType t, const void *A, const void *B, void *C, int cfg,
+                         int split_k, void *ws, cudaStream_t s);
+
+// ---- streaming kernels (k_stream.cu) ----
+// OUTER: no contracted mode of extent > 1 (K == 1).
+cudaError_t launch_outer(const Plan &p, DType t, const void *A, const void *B, void *C, int num_sms,
+                         cudaStream_t s);
+// REDUCE: few outputs (M*N small), long sums; deterministic two-pass.
+size_t reduce_workspace_bytes(const Plan &p, DType t, int num_sms);
+cudaError_t launch_reduce(const Plan &p, DType t, const void *A, const void *B, void *C, int num_sms,
+                          void *ws, cudaStream_t s);
+
+}  // namespace gett

@@ -1,0 +1,96 @@
+// select.cpp -- which kernel family runs a planned contraction.
+//
+// Heuristic (the fixed planner every other selector falls back to):
+//  * K == 1 (no contracted extent > 1): OUTER streaming kernel;
+//  * at most 32 outputs and K >= 8192: REDUCE streaming kernel;
+//  * otherwise the DENSE tiled kernel with the largest tile that still gives
+//    at least one tile per SM, else the smallest tile plus split-K so the
+//    grid covers the SMs.
+#include <algorithm>
+
+#include "kernels.h"
+#include "select.h"
+
+namespace gett {
+
+Choice heuristic_choice(const Plan &p, DType t, int num_sms)
+{
+    Choice c;
+    c.selector = 0;
+    if (p.empty) {
+        c.family = GETT_FAMILY_NOOP;
+        return c;
+    }
+    if (p.K == 1) {
+        c.family = GETT_FAMILY_OUTER;
+        return c;
+    }
+    const int64_t O = p.M * p.N;
+    if (O <= 32 && p.K >= 8192) {
+        c.family = GETT_FAMILY_REDUCE;
+        return c;
+    }
+    c.family = GETT_FAMILY_DENSE;
+    for (int cfg = 0; cfg < DENSE_NUM_CONFIGS; ++cfg) {
+        if (!dense_config_valid(t, cfg)) continue;
+        int bm, bn, bk;
+        dense_tile_shape(cfg, &bm, &bn, &bk);
+        int64_t tiles = ((p.M + bm - 1) / bm) * ((p.N + bn - 1) / bn);
+        if (tiles >= num_sms) {
+            c.config = cfg;
+            c.split_k = 1;
+            return c;
+        }
+    }
+    const int cfg = DENSE_NUM_CONFIGS - 1;
+    int bm, bn, bk;
+    dense_tile_shape(cfg, &bm, &bn, &bk);
+    int64_t tiles = ((p.M + bm - 1) / bm) * ((p.N + bn - 1) / bn);
+    int64_t want = (num_sms + tiles - 1) / tiles;
+    int64_t kmax = std::max<int64_t>(1, p.K / (4 * bk));
+    c.config = cfg;
+    c.split_k = (int)std::max<int64_t>(1, std::min<int64_t>({want, kmax, 64}));
+    return c;
+}
+
+int choose(const Plan &p, DType t, const gett_options *opt, int num_sms, Choice *out)
+{
+    Choice c = heuristic_choice(p, t, num_sms);
+    if (opt) {
+        if (opt->algo != GETT_ALGO_DEFAULT && opt->algo != GETT_ALGO_NATIVE)
+            return GETT_ERR_UNSUPPORTED;
+        if (opt->family != GETT_FAMILY_AUTO) {
+            Choice f;
+            f.family = opt->family;
+            f.selector = 3;
+            f.config = opt->config >= 0 ? opt->config : 0;
+            f.split_k = opt->split_k > 0 ? opt->split_k : 1;
+            bool ok = false;
+            switch (f.family) {
+            case GETT_FAMILY_DENSE: ok = dense_config_valid(t, f.config); break;
+            case GETT_FAMILY_OUTER: ok = p.K == 1; break;
+            case GETT_FAMILY_REDUCE: ok = p.M * p.N <= 4096; break;
+            default: ok = false;
+            }
+            if (!ok) {
+                set_last_error_arg(0);
+                return GETT_ERR_UNSUPPORTED;
+            }
+            c = f;
+        } else if (c.family == GETT_FAMILY_DENSE) {
+            if (opt->config >= 0 && dense_config_valid(t, opt->config)) {
+                c.config = opt->config;
+                c.selector = 3;
+            }
+            if (opt->split_k > 0) {
+                c.split_k = opt->split_k;
+                c.selector = 3;
+            }
+        }
+    }
+    if (c.family == GETT_FAMILY_DENSE) c.split_k = dense_effective_split(p, c.config, c.split_k);
+    *out = c;
+    return GETT_OK;
+}
+
+}  // namespace gett

@@ -295,10 +295,29 @@ def draw_values(rng: np.random.Generator, n: int, dist: str, dtype) -> np.ndarra
     return v.astype(dtype)
 
 
+def _dense_order(layout: Layout):
+    """If the layout fills its buffer exactly (a permutation of a column-major
+    layout, offset 0), the mode order from smallest to largest increment."""
+    if layout.off != 0 or layout.size != max(layout.numel, 1) or layout.numel == 0:
+        return None
+    order = sorted(range(layout.rank), key=lambda i: layout.inc[i])
+    s = 1
+    for i in order:
+        if layout.ext[i] > 1 and layout.inc[i] != s:
+            return None
+        s *= layout.ext[i]
+    return order
+
+
 def fill(layout: Layout, values: np.ndarray, dtype, gap) -> np.ndarray:
     """Buffer of layout.size with `values` scattered to the logical positions
     (first coordinate fastest) and `gap` everywhere else."""
     dtype = np.dtype(dtype)
+    order = _dense_order(layout)
+    if order is not None:
+        t = np.asarray(values, dtype=dtype).reshape(layout.ext, order="F")
+        return np.ascontiguousarray(t.transpose(order)).ravel(order="F") if layout.rank > 1 \
+            else np.array(values, dtype=dtype).reshape(-1)
     buf = np.full(layout.size, gap, dtype=dtype)
     if layout.numel:
         buf[_positions_f(layout.ext, layout.inc, layout.off)] = values
@@ -309,6 +328,12 @@ def gather(layout: Layout, buf: np.ndarray) -> np.ndarray:
     """Logical values (first coordinate fastest) read back from a buffer."""
     if layout.numel == 0:
         return np.zeros(0, dtype=buf.dtype)
+    order = _dense_order(layout)
+    if order is not None and layout.rank > 1:
+        shape = [layout.ext[i] for i in order]
+        t = buf.reshape(shape, order="F")
+        inv = np.argsort(order)
+        return t.transpose(inv).ravel(order="F")
     return buf[_positions_f(layout.ext, layout.inc, layout.off)]
 
 
@@ -458,14 +483,21 @@ def cfg_cc(variant="plain", dtype=np.float64, scale=128, small_ij=32) -> Problem
                         layouts=(la, lb, lc), name=f"cc_{variant}_{n}x{m}")
 
 
-def cfg_stream(dtype=np.float64, a_ext=(256, 256, 64), b_ext=(64, 8)) -> Problem:
-    """Outer product (CONTS=0) of rank-3 A and rank-2 B, output (A modes, B modes)."""
+def cfg_stream(dtype=np.float64, a_ext=(256, 256, 64), b_ext=(64, 8), c_host=True) -> Problem:
+    """Outer product (CONTS=0) of rank-3 A and rank-2 B, output (A modes, B modes),
+    uniform[-1,1] values (A seed 4, B seed 5), C = 0.  With c_host=False the
+    (large) zero C is not materialised on the host: Problem.C is a 1-element
+    placeholder and meta["c_zero"] is set."""
     sig = Signature(tuple(a_ext), tuple(b_ext), (), (), tuple(range(len(a_ext) + len(b_ext))))
     la, lb = layout_contiguous(a_ext), layout_contiguous(b_ext)
     lc = layout_contiguous(sig.extc())
-    rng = np.random.default_rng(7)
-    return make_problem(sig, rng, dtype, "uniform", c_dist="zeros", seeds=(4, 5),
-                        layouts=(la, lb, lc), name="stream_outer")
+    if c_host:
+        rng = np.random.default_rng(7)
+        return make_problem(sig, rng, dtype, "uniform", c_dist="zeros", seeds=(4, 5),
+                            layouts=(la, lb, lc), name="stream_outer")
+    A = fill(la, draw_values(np.random.default_rng(4), la.numel, "uniform", dtype), dtype, np.nan)
+    B = fill(lb, draw_values(np.random.default_rng(5), lb.numel, "uniform", dtype), dtype, np.nan)
+    return Problem(sig, la, lb, lc, A, B, np.zeros(1, dtype=dtype), "stream_outer", {"c_zero": True})
 
 
 def batched_signatures(n=4096, seed=7, min_ext=2, max_ext=64, cap=1 << 18,

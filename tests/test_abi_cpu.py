@@ -1,0 +1,187 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every symbol the
+public header declares, validates arguments (Sec. 4.7 rules) and plans
+correctly.  No device work is started: every call here fails validation or is
+the host-only planner."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_06770_gb300 import gett, synth
+from tests._einsum_ref import einsum_logical
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2410_06770_gb300 import build
+    build.build()
+    return gett.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, re.M):
+            name = m.group(1)
+            if name not in ("if", "while", "for", "sizeof", "return"):
+                names.add(name)
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert "dgett" in names and "zgett_async" in names and "gett_plan_describe" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def _args(**kw):
+    base = dict(RANKA=2, EXTA=(3, 4), INCA=(1, 3), RANKB=2, EXTB=(4, 5), INCB=(1, 4), CONTS=1,
+                CONTA=(1,), CONTB=(0,), PERM=(0, 1), INCC=(1, 3))
+    base.update(kw)
+    return base
+
+
+def _call(L, **kw):
+    a = _args(**kw)
+    st, _ = gett.xgett("d", a["RANKA"], a["EXTA"], a["INCA"], 0, a["RANKB"], a["EXTB"], a["INCB"], 0,
+                       a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], 0,
+                       raise_on_error=False)
+    return st, gett.last_error_arg()
+
+
+@pytest.mark.parametrize("kw,pos", [
+    (dict(RANKA=-1), 1),
+    (dict(EXTA=None), 2),
+    (dict(EXTA=(3, -4)), 2),
+    (dict(INCA=None), 3),
+    (dict(RANKB=-2), 5),
+    (dict(EXTB=None), 6),
+    (dict(INCB=None), 7),
+    (dict(CONTS=3), 9),
+    (dict(CONTA=(2,)), 10),
+    (dict(CONTB=(2,)), 11),
+    (dict(CONTB=(1,), PERM=(0, 1)), 11),  # extents 4 vs 5 do not match
+    (dict(PERM=(0, 0)), 12),
+    (dict(PERM=(0, 2)), 12),
+    (dict(PERM=None), 12),
+    (dict(INCC=None), 13),
+    (dict(CONTS=2, CONTA=(1, 1), CONTB=(0, 1)), 10),
+    (dict(CONTS=2, CONTA=(0, 1), CONTB=(0, 0)), 11),
+])
+def test_invalid_arguments(L, kw, pos):
+    st, arg = _call(L, **kw)
+    assert st == gett.GETT_ERR_ARG
+    assert arg == pos
+
+
+def test_null_pointers_reported(L):
+    st, arg = _call(L)
+    assert st == gett.GETT_ERR_ARG and arg == 4
+
+
+def test_non_injective_c_is_alias(L):
+    # two free modes of extent 3 and 4 mapped onto overlapping increments
+    st, _ = _call(L, INCC=(1, 2))
+    assert st == gett.GETT_ERR_ALIAS
+    st, _ = _call(L, INCC=(0, 3))
+    assert st == gett.GETT_ERR_ALIAS
+
+
+def test_empty_problem_is_noop(L):
+    # zero free extent: nothing to do, no pointer needed
+    st, _ = _call(L, EXTA=(0, 4))
+    assert st == gett.GETT_OK
+    # zero contracted extent: empty sum, C unchanged
+    st, _ = _call(L, EXTA=(3, 0), EXTB=(0, 5), INCC=(1, 3))
+    assert st == gett.GETT_OK
+
+
+def test_status_strings(L):
+    for s in (0, -1, -2, -3, -4, -5, -6):
+        assert L.gett_status_string(s)
+
+
+def test_plan_small_config(L):
+    p = synth.cfg_small_dgett()
+    a = p.args()
+    st, info = gett.plan_describe(a["RANKA"], a["EXTA"], a["INCA"], a["RANKB"], a["EXTB"], a["INCB"],
+                                  a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"])
+    assert st == 0
+    assert (info["M"], info["N"], info["K"]) == (512, 336, 480)
+    assert (info["nm"], info["nn"], info["nk"]) == (2, 2, 2)
+
+
+def test_plan_fuses_colmajor_cc_to_gemm(L):
+    p = synth.cfg_cc("plain", scale=8, small_ij=4)
+    a = p.args()
+    st, info = gett.plan_describe(a["RANKA"], a["EXTA"], a["INCA"], a["RANKB"], a["EXTB"], a["INCB"],
+                                  a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"])
+    assert st == 0
+    assert (info["nm"], info["nn"], info["nk"]) == (1, 1, 1)
+    assert info["m"] == [(64, 1, 1)]
+    assert info["k"] == [(64, 64, 1)]
+    assert info["n"] == [(16, 64, 64)]
+
+
+def test_plan_transposed_a_keeps_modes(L):
+    p = synth.cfg_cc("perm_transA", scale=8, small_ij=4)
+    a = p.args()
+    st, info = gett.plan_describe(a["RANKA"], a["EXTA"], a["INCA"], a["RANKB"], a["EXTB"], a["INCB"],
+                                  a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"])
+    assert st == 0
+    assert (info["nm"], info["nn"], info["nk"]) == (2, 2, 2)
+
+
+def _planned_problem(p, info):
+    """The canonical M/N/K problem the planner describes, as an xGETT call on
+    the same buffers: A'(M modes, K modes), B'(K modes, N modes), C'(M, N)."""
+    nm, nn, nk = info["nm"], info["nn"], info["nk"]
+    exta = [e for e, _, _ in info["m"]] + [e for e, _, _ in info["k"]]
+    inca = [s for _, s, _ in info["m"]] + [s for _, s, _ in info["k"]]
+    extb = [e for e, _, _ in info["k"]] + [e for e, _, _ in info["n"]]
+    incb = [s for _, _, s in info["k"]] + [s for _, s, _ in info["n"]]
+    incc = [s for _, _, s in info["m"]] + [s for _, _, s in info["n"]]
+    conta = list(range(nm, nm + nk))
+    contb = list(range(nk))
+    perm = list(range(nm + nn))
+    return dict(RANKA=nm + nk, EXTA=exta, INCA=inca, RANKB=nk + nn, EXTB=extb, INCB=incb,
+                CONTS=nk, CONTA=conta, CONTB=contb, PERM=perm, INCC=incc)
+
+
+@pytest.mark.parametrize("family", synth.THESIS_TESTS)
+@pytest.mark.parametrize("seed", range(3))
+def test_planner_preserves_the_contraction(L, family, seed):
+    """Planner property: the canonical problem (after squeeze, flips, fusion,
+    ordering) evaluated by the oracle on the same buffers gives exactly the
+    original problem's result on integer data."""
+    p = synth.thesis_problem(family, 9000 + seed, np.float64, "int", c_dist="int")
+    a = p.args()
+    st, info = gett.plan_describe(a["RANKA"], a["EXTA"], a["INCA"], a["RANKB"], a["EXTB"], a["INCB"],
+                                  a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"])
+    assert st == 0
+    ref = oracle.gett_problem(p)
+    if info["empty"]:
+        assert np.array_equal(ref, p.C)
+        return
+    q = _planned_problem(p, info)
+    Cq = p.C.copy()
+    rc = oracle.gett_raw("f64", q["RANKA"], q["EXTA"], q["INCA"], p.A, p.la.off + info["off_a"],
+                         q["RANKB"], q["EXTB"], q["INCB"], p.B, p.lb.off + info["off_b"],
+                         q["CONTS"], q["CONTA"], q["CONTB"], q["PERM"], q["INCC"], Cq,
+                         p.lc.off + info["off_c"])
+    assert rc == 0
+    assert np.array_equal(Cq, ref)
+    # canonical form: positive C increments on free modes, sorted classes
+    for _, _, sc in info["m"] + info["n"]:
+        assert sc > 0
+    for _, sa, sb in info["k"]:
+        assert sa > 0 or (sa == 0 and sb >= 0)

@@ -411,7 +411,10 @@ def test_planted_mistakes_are_caught(mutant, tmp_path):
             if p.sig.rank_c < 2 and mutant in ("perm_inverse", "free_b_first"):
                 continue
             ref = einsum_logical(p, np.int64).astype(np.float64)
-            C = oracle.widen(p.C).copy()
+            # a mutant may address C outside its layout: give it a large guard band
+            guard = 32 * p.C.size + 4096
+            C_big = np.zeros(p.C.size + 2 * guard)
+            C_big[guard:guard + p.C.size] = oracle.widen(p.C)
             a = p.args()
             i64 = lambda xs: (ctypes.c_int64 * max(len(xs), 1))(*xs)
             i32 = lambda xs: (ctypes.c_int * max(len(xs), 1))(*xs)
@@ -422,7 +425,9 @@ def test_planted_mistakes_are_caught(mutant, tmp_path):
                     ctypes.c_int(a["RANKB"]), i64(a["EXTB"]), i64(a["INCB"]),
                     ctypes.c_void_p(B.ctypes.data + 8 * p.lb.off),
                     ctypes.c_int(a["CONTS"]), i32(a["CONTA"]), i32(a["CONTB"]), i32(a["PERM"]),
-                    i64(a["INCC"]), ctypes.c_void_p(C.ctypes.data + 8 * p.lc.off), ctypes.c_int(1))
+                    i64(a["INCC"]), ctypes.c_void_p(C_big.ctypes.data + 8 * (guard + p.lc.off)),
+                    ctypes.c_int(1))
+            C = C_big[guard:guard + p.C.size]
             if rc != 0 or not np.array_equal(synth.logical(p.lc, C), ref):
                 caught = True
                 break
