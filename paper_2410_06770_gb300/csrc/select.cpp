@@ -63,7 +63,8 @@ int choose(const Plan &p, DType t, const gett_options *opt, int num_sms, Choice 
             Choice f;
             f.family = opt->family;
             f.selector = 3;
-            f.config = opt->config >= 0 ? opt->config : 0;
+            f.config = opt->config >= 0 ? opt->config
+                                        : (c.family == GETT_FAMILY_DENSE ? c.config : DENSE_NUM_CONFIGS - 1);
             f.split_k = opt->split_k > 0 ? opt->split_k : 1;
             bool ok = false;
             switch (f.family) {

@@ -1,0 +1,53 @@
+"""Run one contraction of a named workload through the C ABI, for profilers.
+
+    python -m paper_2410_06770_gb300.profile_case WORKLOAD [SCALE] [--calls N] [--algo A]
+
+WORKLOAD: cc, cc_perm_transA (extents a..d = SCALE, i,j = SCALE/4), stream
+(A(SCALE, SCALE, 64) x B(64, 8)), small.  Inputs are generated on the host,
+copied once, then the call is made N times (default 2) and synchronised.
+"""
+import argparse
+import sys
+
+import numpy as np
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload")
+    ap.add_argument("scale", nargs="?", type=int, default=128)
+    ap.add_argument("--calls", type=int, default=2)
+    ap.add_argument("--algo", default="native")
+    ap.add_argument("--prefix", default="d")
+    args = ap.parse_args(argv)
+    import torch
+
+    from . import build, gett, synth
+    build.build()
+    if args.workload == "cc":
+        p = synth.cfg_cc("plain", scale=args.scale, small_ij=max(1, args.scale // 4))
+    elif args.workload == "cc_perm_transA":
+        p = synth.cfg_cc("perm_transA", scale=args.scale, small_ij=max(1, args.scale // 4))
+    elif args.workload == "stream":
+        p = synth.cfg_stream(a_ext=(args.scale, args.scale, 64), b_ext=(64, 8))
+    elif args.workload == "small":
+        p = synth.cfg_small_dgett()
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    dA = torch.from_numpy(p.A).cuda()
+    dB = torch.from_numpy(p.B).cuda()
+    dC = torch.from_numpy(p.C).cuda()
+    a = p.args()
+    opts = gett.options(algo=args.algo)
+    rep = None
+    for _ in range(args.calls):
+        _, rep = gett.xgett(args.prefix, a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"],
+                            a["INCB"], dB, a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], dC,
+                            a_off=p.la.off, b_off=p.lb.off, c_off=p.lc.off, mode="ex", opts=opts)
+    torch.cuda.synchronize()
+    print(rep)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
