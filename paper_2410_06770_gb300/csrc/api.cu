@@ -47,6 +47,13 @@ int dev_state(DevState **out)
             set_last_cuda_error(e);
             return GETT_ERR_CUDA;
         }
+        // keep memory freed by cudaFreeAsync in the device pool instead of
+        // returning it to the driver at every synchronisation
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
         st.sms = sms;
         st.err = err;
         st.init = true;
@@ -75,6 +82,9 @@ cudaError_t run_family(const Plan &p, DType t, const Choice &ch, const void *A, 
     size_t ws_bytes = 0;
     if (ch.family == GETT_FAMILY_DENSE) ws_bytes = dense_workspace_bytes(p, t, ch.config, ch.split_k);
     else if (ch.family == GETT_FAMILY_REDUCE) ws_bytes = reduce_workspace_bytes(p, t, st.sms);
+    else if (ch.family == GETT_FAMILY_TC)
+        ws_bytes = ch.algo == GETT_ALGO_OZAKI_BF16 ? ozaki_workspace_bytes(p, ch.moduli)
+                                                   : tc_split_workspace_bytes(p, ch.algo);
     void *ws = nullptr;
     cudaError_t e = cudaSuccess;
     if (ws_bytes) {
@@ -85,6 +95,10 @@ cudaError_t run_family(const Plan &p, DType t, const Choice &ch, const void *A, 
     case GETT_FAMILY_DENSE: e = launch_dense(p, t, A, B, C, ch.config, ch.split_k, ws, s); break;
     case GETT_FAMILY_OUTER: e = launch_outer(p, t, A, B, C, st.sms, s); break;
     case GETT_FAMILY_REDUCE: e = launch_reduce(p, t, A, B, C, st.sms, ws, s); break;
+    case GETT_FAMILY_TC:
+        e = ch.algo == GETT_ALGO_OZAKI_BF16 ? launch_ozaki(p, ch.moduli, A, B, C, ws, st.sms, st.err, s)
+                                            : launch_tc_split(p, t, ch.algo, A, B, C, ws, st.sms, st.err, s);
+        break;
     default: e = cudaErrorInvalidValue; break;
     }
     if (ws) {

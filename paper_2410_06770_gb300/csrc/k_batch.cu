@@ -1,0 +1,408 @@
+// k_batch.cu -- thousands of xGETT contractions in one persistent launch.
+//
+// gett_batch_create plans every problem on the host (validation, squeeze,
+// flips, fusion -- the same planner as single calls), picks a tile
+// configuration per problem (heuristic, fixed, caller table or learned
+// model), decodes the offset tables of all problems into one buffer, and
+// builds a work list with one entry per output tile, sorted by decreasing
+// tile cost so long tiles start first.  The persistent kernel runs
+// ctas_per_sm CTAs per SM; each CTA takes the next work item from an atomic
+// counter and computes that tile with the shared CUDA-core tile routine
+// (float arithmetic; bf16 operands are widened on load).  Every tile is
+// computed by exactly one CTA, so results do not depend on scheduling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "dense_tile.cuh"
+#include "gett_batch.h"
+#include "internal.h"
+#include "learn.h"
+
+namespace gett {
+
+namespace {
+
+constexpr int BT = 256;  // threads per CTA for every configuration
+constexpr int NCFG = 4;
+struct BCfg {
+    int bm, bn, bk, tm, tn;
+};
+constexpr BCfg kB[NCFG] = {{128, 64, 8, 8, 4}, {64, 64, 16, 4, 4}, {32, 32, 16, 2, 2}, {64, 32, 16, 4, 2}};
+
+struct BatchProb {
+    const void *A;
+    const void *B;
+    float *C;
+    int64_t M, N, K;
+    int64_t tab;  // offset of this problem's tables in the table buffer
+    int tiles_m, tiles_n;
+    int cfg, dtype;
+    int a_m_fast, b_n_fast, c_m_fast;
+};
+
+template <class T, int CFG>
+__device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tables, int tile, float *smem_f,
+                                         int64_t *smem_i)
+{
+    constexpr BCfg c = kB[CFG];
+    const int tm = tile / pr.tiles_n, tn = tile % pr.tiles_n;
+    TileArgs a;
+    a.A = pr.A;
+    a.B = pr.B;
+    a.C = pr.C;
+    const int64_t *t = tables + pr.tab;
+    a.rowA = t;
+    a.rowC = t + pr.M;
+    a.colB = t + 2 * pr.M;
+    a.colC = t + 2 * pr.M + pr.N;
+    a.kA = t + 2 * pr.M + 2 * pr.N;
+    a.kB = t + 2 * pr.M + 2 * pr.N + pr.K;
+    a.M = pr.M;
+    a.N = pr.N;
+    a.m0 = (int64_t)tm * c.bm;
+    a.n0 = (int64_t)tn * c.bn;
+    a.kbeg = 0;
+    a.kend = pr.K;
+    a.a_m_fast = pr.a_m_fast;
+    a.b_n_fast = pr.b_n_fast;
+    a.c_m_fast = pr.c_m_fast;
+    a.partial = nullptr;
+    dense_tile<T, c.bm, c.bn, c.bk, c.tm, c.tn>(a, smem_f, smem_f + 2 * c.bk * c.bm, smem_i, smem_i + c.bm);
+}
+
+// largest shared footprint over the configurations (floats / int64s)
+constexpr int smem_floats()
+{
+    int m = 0;
+    for (int i = 0; i < NCFG; ++i) m = std::max(m, 2 * kB[i].bk * (kB[i].bm + kB[i].bn));
+    return m;
+}
+constexpr int smem_ints()
+{
+    int m = 0;
+    for (int i = 0; i < NCFG; ++i) m = std::max(m, kB[i].bm + kB[i].bn);
+    return m;
+}
+
+__global__ void __launch_bounds__(BT) batch_kernel(const BatchProb *__restrict__ probs, const uint2 *__restrict__ work,
+                                                   int64_t nwork, const int64_t *__restrict__ tables,
+                                                   unsigned long long *counter)
+{
+    __shared__ float smem_f[smem_floats()];
+    __shared__ int64_t smem_i[smem_ints()];
+    __shared__ unsigned long long s_item;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
+        __syncthreads();
+        const unsigned long long it = s_item;
+        __syncthreads();
+        if (it >= (unsigned long long)nwork) break;
+        const uint2 w = work[it];
+        const BatchProb pr = probs[w.x];
+        const int key = pr.cfg * 2 + pr.dtype;
+        switch (key) {
+        case 0: run_tile<float, 0>(pr, tables, w.y, smem_f, smem_i); break;
+        case 1: run_tile<uint16_t, 0>(pr, tables, w.y, smem_f, smem_i); break;
+        case 2: run_tile<float, 1>(pr, tables, w.y, smem_f, smem_i); break;
+        case 3: run_tile<uint16_t, 1>(pr, tables, w.y, smem_f, smem_i); break;
+        case 4: run_tile<float, 2>(pr, tables, w.y, smem_f, smem_i); break;
+        case 5: run_tile<uint16_t, 2>(pr, tables, w.y, smem_f, smem_i); break;
+        case 6: run_tile<float, 3>(pr, tables, w.y, smem_f, smem_i); break;
+        case 7: run_tile<uint16_t, 3>(pr, tables, w.y, smem_f, smem_i); break;
+        default: break;
+        }
+        __syncthreads();
+    }
+}
+
+void decode_host(const ModeList &L, int64_t count, int64_t *t0, int64_t *t1)
+{
+    // first mode fastest; incremental odometer (the order Alg. 2 visits)
+    int64_t coord[GETT_MAX_MODES] = {0};
+    int64_t a = 0, b = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        t0[i] = a;
+        t1[i] = b;
+        for (int d = 0; d < L.n; ++d) {
+            coord[d]++;
+            a += L.s0[d];
+            b += L.s1[d];
+            if (coord[d] < L.ext[d]) break;
+            a -= L.s0[d] * L.ext[d];
+            b -= L.s1[d] * L.ext[d];
+            coord[d] = 0;
+        }
+    }
+}
+
+int64_t first_abs(const ModeList &L, const int64_t *s) { return L.n ? (s[0] < 0 ? -s[0] : s[0]) : 0; }
+
+}  // namespace
+
+int batch_heuristic_config(int64_t M, int64_t N, int64_t K)
+{
+    (void)K;
+    if (M >= 128 && N >= 64) return 0;
+    if (M >= 64 && N >= 64) return 1;
+    if (M >= 64 && N < 64) return 3;
+    return 2;
+}
+
+}  // namespace gett
+
+struct gett_batch {
+    int n = 0;
+    int nonempty = 0;
+    int64_t nwork = 0;
+    double flops = 0;
+    int config_count[8] = {};
+    int fallbacks = 0;
+    int ctas = 0;
+    gett::BatchProb *d_probs = nullptr;
+    uint2 *d_work = nullptr;
+    int64_t *d_tables = nullptr;
+    unsigned long long *d_counter = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cap = nullptr;
+};
+
+using namespace gett;
+
+extern "C" int gett_batch_num_configs(void) { return NCFG; }
+
+extern "C" int gett_batch_config_shape(int config, int *bm, int *bn)
+{
+    if (config < 0 || config >= NCFG) return GETT_ERR_ARG;
+    if (bm) *bm = kB[config].bm;
+    if (bn) *bn = kB[config].bn;
+    return GETT_OK;
+}
+
+extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const gett_batch_options *opt,
+                                 gett_batch **out, int *bad_index)
+{
+    if (bad_index) *bad_index = -1;
+    if (!out || n < 0 || (n > 0 && !probs)) return GETT_ERR_ARG;
+    *out = nullptr;
+    gett_batch_options o{};
+    if (opt) o = *opt;
+    if (o.select == GETT_BATCH_SELECT_FIXED && (o.config < 0 || o.config >= NCFG)) return GETT_ERR_ARG;
+    if (o.select == GETT_BATCH_SELECT_TABLE && !o.configs) return GETT_ERR_ARG;
+
+    std::vector<Plan> plans(n);
+    std::vector<BatchProb> hp;
+    std::vector<int> hp_index;
+    int64_t table_len = 0;
+    struct Span {
+        intptr_t lo, hi;
+        int idx;
+    };
+    std::vector<Span> cspans, inspans;
+    int fallbacks = 0;
+    for (int i = 0; i < n; ++i) {
+        const gett_problem_desc &d = probs[i];
+        if (d.dtype != GETT_BATCH_F32 && d.dtype != GETT_BATCH_BF16) {
+            if (bad_index) *bad_index = i;
+            set_last_error_arg(0);
+            return GETT_ERR_ARG;
+        }
+        Args a{d.RANKA, d.EXTA, d.INCA, d.RANKB, d.EXTB, d.INCB, d.CONTS, d.CONTA, d.CONTB, d.PERM, d.INCC};
+        int bad = 0;
+        int rc = make_plan(a, &plans[i], &bad);
+        if (rc != GETT_OK) {
+            set_last_error_arg(bad);
+            if (bad_index) *bad_index = i;
+            return rc;
+        }
+        const Plan &p = plans[i];
+        if (p.empty) continue;
+        const size_t esz = d.dtype == GETT_BATCH_F32 ? 4 : 2;
+        if (!d.A || !d.B || !d.C) {
+            set_last_error_arg(!d.A ? 4 : (!d.B ? 8 : 14));
+            if (bad_index) *bad_index = i;
+            return GETT_ERR_ARG;
+        }
+        auto span = [](const void *ptr, int64_t lo, int64_t hi, size_t e, int idx) {
+            intptr_t b = reinterpret_cast<intptr_t>(ptr);
+            return Span{b + (intptr_t)(lo * (int64_t)e), b + (intptr_t)((hi + 1) * (int64_t)e), idx};
+        };
+        cspans.push_back(span(d.C, p.c_lo, p.c_hi, 4, i));
+        inspans.push_back(span(d.A, p.a_lo, p.a_hi, esz, i));
+        inspans.push_back(span(d.B, p.b_lo, p.b_hi, esz, i));
+        int cfg = -1;
+        if (o.select == GETT_BATCH_SELECT_FIXED) cfg = o.config;
+        else if (o.select == GETT_BATCH_SELECT_TABLE) cfg = o.configs[i];
+        else if (o.select == GETT_BATCH_SELECT_LEARNED) cfg = learned_batch_config(p, d.dtype, NCFG);
+        if (cfg < 0 || cfg >= NCFG) {
+            if (o.select == GETT_BATCH_SELECT_TABLE || o.select == GETT_BATCH_SELECT_LEARNED) ++fallbacks;
+            cfg = batch_heuristic_config(p.M, p.N, p.K);
+        }
+        BatchProb b{};
+        b.A = static_cast<const char *>(d.A) + p.offA * (int64_t)esz;
+        b.B = static_cast<const char *>(d.B) + p.offB * (int64_t)esz;
+        b.C = d.C + p.offC;
+        b.M = p.M;
+        b.N = p.N;
+        b.K = p.K;
+        b.tab = table_len;
+        b.cfg = cfg;
+        b.dtype = d.dtype;
+        b.tiles_m = (int)((p.M + kB[cfg].bm - 1) / kB[cfg].bm);
+        b.tiles_n = (int)((p.N + kB[cfg].bn - 1) / kB[cfg].bn);
+        const int64_t am = first_abs(p.m, p.m.s0), ak = first_abs(p.k, p.k.s0);
+        const int64_t bnn = first_abs(p.n, p.n.s0), bk = first_abs(p.k, p.k.s1);
+        const int64_t cm = first_abs(p.m, p.m.s1), cn = first_abs(p.n, p.n.s1);
+        b.a_m_fast = (am != 0 && (ak == 0 || am <= ak)) ? 1 : 0;
+        b.b_n_fast = (bnn != 0 && (bk == 0 || bnn <= bk)) ? 1 : 0;
+        b.c_m_fast = (cm != 0 && (cn == 0 || cm <= cn)) ? 1 : 0;
+        table_len += 2 * (p.M + p.N + p.K);
+        hp.push_back(b);
+        hp_index.push_back(i);
+    }
+    // C of different problems must not overlap each other or any input
+    std::sort(cspans.begin(), cspans.end(), [](const Span &x, const Span &y) { return x.lo < y.lo; });
+    for (size_t i = 1; i < cspans.size(); ++i)
+        if (cspans[i].lo < cspans[i - 1].hi) {
+            if (bad_index) *bad_index = cspans[i].idx;
+            return GETT_ERR_ALIAS;
+        }
+    for (const Span &s : inspans) {
+        auto it = std::upper_bound(cspans.begin(), cspans.end(), s.lo,
+                                   [](intptr_t v, const Span &c) { return v < c.lo; });
+        if (it != cspans.begin() && std::prev(it)->hi > s.lo) {
+            if (bad_index) *bad_index = s.idx;
+            return GETT_ERR_ALIAS;
+        }
+        if (it != cspans.end() && it->lo < s.hi) {
+            if (bad_index) *bad_index = s.idx;
+            return GETT_ERR_ALIAS;
+        }
+    }
+
+    gett_batch *b = new gett_batch();
+    b->n = n;
+    b->nonempty = (int)hp.size();
+    b->fallbacks = fallbacks;
+    std::vector<int64_t> tables((size_t)std::max<int64_t>(table_len, 1));
+    std::vector<uint2> work;
+    std::vector<double> cost;
+    for (size_t j = 0; j < hp.size(); ++j) {
+        const Plan &p = plans[hp_index[j]];
+        BatchProb &pr = hp[j];
+        int64_t *t = tables.data() + pr.tab;
+        decode_host(p.m, p.M, t, t + p.M);
+        decode_host(p.n, p.N, t + 2 * p.M, t + 2 * p.M + p.N);
+        decode_host(p.k, p.K, t + 2 * p.M + 2 * p.N, t + 2 * p.M + 2 * p.N + p.K);
+        b->flops += 2.0 * (double)p.M * (double)p.N * (double)p.K;
+        b->config_count[pr.cfg]++;
+        const int nt = pr.tiles_m * pr.tiles_n;
+        for (int tt = 0; tt < nt; ++tt) {
+            work.push_back(make_uint2((unsigned)j, (unsigned)tt));
+            cost.push_back((double)kB[pr.cfg].bm * kB[pr.cfg].bn * (double)p.K);
+        }
+    }
+    // longest tiles first
+    std::vector<size_t> order(work.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<uint2> sorted(work.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = work[order[i]];
+    b->nwork = (int64_t)sorted.size();
+
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->ctas = sms * (o.ctas_per_sm > 0 ? o.ctas_per_sm : 2);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, sizeof(BatchProb) * std::max<size_t>(hp.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_work, sizeof(uint2) * std::max<size_t>(sorted.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tables, sizeof(int64_t) * tables.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess && !hp.empty())
+        e = cudaMemcpy(b->d_probs, hp.data(), sizeof(BatchProb) * hp.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !sorted.empty())
+        e = cudaMemcpy(b->d_work, sorted.data(), sizeof(uint2) * sorted.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tables, tables.data(), sizeof(int64_t) * tables.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        gett_batch_destroy(b);
+        return e == cudaErrorMemoryAllocation ? GETT_ERR_NOMEM : GETT_ERR_CUDA;
+    }
+    *out = b;
+    return GETT_OK;
+}
+
+static cudaError_t enqueue(gett_batch *b, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || b->nwork == 0) return e;
+    const int ctas = (int)std::min<int64_t>(b->ctas, b->nwork);
+    batch_kernel<<<ctas, BT, 0, s>>>(b->d_probs, b->d_work, b->nwork, b->d_tables, b->d_counter);
+    return cudaGetLastError();
+}
+
+extern "C" int gett_batch_launch(gett_batch *b, void *stream)
+{
+    if (!b) return GETT_ERR_ARG;
+    cudaError_t e = enqueue(b, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    return GETT_OK;
+}
+
+extern "C" int gett_batch_launch_graph(gett_batch *b, void *stream)
+{
+    if (!b) return GETT_ERR_ARG;
+    cudaError_t e = cudaSuccess;
+    if (!b->exec) {
+        if (!b->cap) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = enqueue(b, b->cap);
+            e = cudaStreamEndCapture(b->cap, &b->graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    return GETT_OK;
+}
+
+extern "C" int gett_batch_get_info(const gett_batch *b, gett_batch_info *info)
+{
+    if (!b || !info) return GETT_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n = b->n;
+    info->nonempty = b->nonempty;
+    info->tiles = b->nwork;
+    info->flops = b->flops;
+    for (int i = 0; i < 8; ++i) info->config_count[i] = b->config_count[i];
+    info->fallbacks = b->fallbacks;
+    return GETT_OK;
+}
+
+extern "C" int gett_batch_destroy(gett_batch *b)
+{
+    if (!b) return GETT_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->d_probs) cudaFree(b->d_probs);
+    if (b->d_work) cudaFree(b->d_work);
+    if (b->d_tables) cudaFree(b->d_tables);
+    if (b->d_counter) cudaFree(b->d_counter);
+    delete b;
+    return GETT_OK;
+}

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "dense_tile.cuh"
 #include "kernels.h"
 
 namespace gett {
@@ -54,146 +55,31 @@ template <class T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 dense_kernel(DenseParams p)
 {
-    using R = Tr<T>;
-    using Acc = typename R::Acc;
-    using Out = typename R::Out;
-    constexpr int NT = (BM / TM) * (BN / TN);
-    constexpr int LA = BM * BK / NT;
-    constexpr int LB = BN * BK / NT;
-    static_assert(LA * NT == BM * BK && LB * NT == BN * BK, "tile/threads mismatch");
-
-    __shared__ Acc sA[2][BK][BM];
-    __shared__ Acc sB[2][BK][BN];
+    using Acc = typename Tr<T>::Acc;
+    __shared__ Acc sA[2 * BK * BM];
+    __shared__ Acc sB[2 * BK * BN];
     __shared__ int64_t sRowA[BM];
     __shared__ int64_t sColB[BN];
-
-    const int tid = threadIdx.x;
     const int tile = blockIdx.x;
     const int tile_m = tile % p.tiles_m;
     const int tile_n = tile / p.tiles_m;
-    const int64_t m0 = (int64_t)tile_m * BM;
-    const int64_t n0 = (int64_t)tile_n * BN;
     const int split = blockIdx.y;
-    const int64_t kbeg = split * p.k_per_split;
-    const int64_t kend = min(p.K, kbeg + p.k_per_split);
-
-    const T *A = static_cast<const T *>(p.A);
-    const T *B = static_cast<const T *>(p.B);
-
-    for (int i = tid; i < BM; i += NT) sRowA[i] = (m0 + i < p.M) ? p.rowA[m0 + i] : 0;
-    for (int i = tid; i < BN; i += NT) sColB[i] = (n0 + i < p.N) ? p.colB[n0 + i] : 0;
-    __syncthreads();
-
-    Acc ra[LA], rb[LB];
-    auto load_tile = [&](int64_t k0) {
-#pragma unroll
-        for (int r = 0; r < LA; ++r) {
-            int e = tid + r * NT;
-            int mm, kk;
-            if (p.a_m_fast) { mm = e % BM; kk = e / BM; }
-            else { kk = e % BK; mm = e / BK; }
-            int64_t k = k0 + kk;
-            ra[r] = (m0 + mm < p.M && k < kend) ? R::load(A + sRowA[mm] + p.kA[k]) : R::zero();
-        }
-#pragma unroll
-        for (int r = 0; r < LB; ++r) {
-            int e = tid + r * NT;
-            int nn, kk;
-            if (p.b_n_fast) { nn = e % BN; kk = e / BN; }
-            else { kk = e % BK; nn = e / BK; }
-            int64_t k = k0 + kk;
-            rb[r] = (n0 + nn < p.N && k < kend) ? R::load(B + sColB[nn] + p.kB[k]) : R::zero();
-        }
-    };
-    auto store_tile = [&](int buf) {
-#pragma unroll
-        for (int r = 0; r < LA; ++r) {
-            int e = tid + r * NT;
-            int mm, kk;
-            if (p.a_m_fast) { mm = e % BM; kk = e / BM; }
-            else { kk = e % BK; mm = e / BK; }
-            sA[buf][kk][mm] = ra[r];
-        }
-#pragma unroll
-        for (int r = 0; r < LB; ++r) {
-            int e = tid + r * NT;
-            int nn, kk;
-            if (p.b_n_fast) { nn = e % BN; kk = e / BN; }
-            else { kk = e % BK; nn = e / BK; }
-            sB[buf][kk][nn] = rb[r];
-        }
-    };
-
-    int tm, tn;
-    if (p.c_m_fast) { tm = tid % (BM / TM); tn = tid / (BM / TM); }
-    else { tn = tid % (BN / TN); tm = tid / (BN / TN); }
-
-    Acc acc[TM][TN];
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = R::zero();
-
-    const int64_t nkt = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
-    if (nkt > 0) {
-        load_tile(kbeg);
-        store_tile(0);
-        __syncthreads();
-    }
-    for (int64_t kt = 0; kt < nkt; ++kt) {
-        const int cur = kt & 1;
-        if (kt + 1 < nkt) load_tile(kbeg + (kt + 1) * BK);
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            Acc a[TM], b[TN];
-#pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = sA[cur][kk][tm + i * (BM / TM)];
-#pragma unroll
-            for (int j = 0; j < TN; ++j) b[j] = sB[cur][kk][tn + j * (BN / TN)];
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) R::mac(acc[i][j], a[i], b[j]);
-        }
-        if (kt + 1 < nkt) store_tile(cur ^ 1);
-        __syncthreads();
-    }
-
-    // epilogue
-    if (p.partial) {
-        Acc *P = static_cast<Acc *>(p.partial) + (int64_t)split * p.M * p.N;
-#pragma unroll
-        for (int i = 0; i < TM; ++i) {
-            int64_t m = m0 + tm + i * (BM / TM);
-#pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                int64_t n = n0 + tn + j * (BN / TN);
-                if (m < p.M && n < p.N) P[p.c_m_fast ? n * p.M + m : m * p.N + n] = acc[i][j];
-            }
-        }
-        return;
-    }
-    Out *C = static_cast<Out *>(p.C);
-    int64_t rc[TM], cc[TN];
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        int64_t m = m0 + tm + i * (BM / TM);
-        rc[i] = m < p.M ? p.rowC[m] : 0;
-    }
-#pragma unroll
-    for (int j = 0; j < TN; ++j) {
-        int64_t n = n0 + tn + j * (BN / TN);
-        cc[j] = n < p.N ? p.colC[n] : 0;
-    }
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        int64_t m = m0 + tm + i * (BM / TM);
-#pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            int64_t n = n0 + tn + j * (BN / TN);
-            if (m < p.M && n < p.N) R::store_add(C + rc[i] + cc[j], acc[i][j]);
-        }
-    }
+    TileArgs a;
+    a.A = p.A;
+    a.B = p.B;
+    a.C = p.C;
+    a.rowA = p.rowA; a.rowC = p.rowC; a.colB = p.colB; a.colC = p.colC; a.kA = p.kA; a.kB = p.kB;
+    a.M = p.M;
+    a.N = p.N;
+    a.m0 = (int64_t)tile_m * BM;
+    a.n0 = (int64_t)tile_n * BN;
+    a.kbeg = split * p.k_per_split;
+    a.kend = min(p.K, a.kbeg + p.k_per_split);
+    a.a_m_fast = p.a_m_fast;
+    a.b_n_fast = p.b_n_fast;
+    a.c_m_fast = p.c_m_fast;
+    a.partial = p.partial ? static_cast<Acc *>(p.partial) + (int64_t)split * p.M * p.N : nullptr;
+    dense_tile<T, BM, BN, BK, TM, TN>(a, sA, sB, sRowA, sColB);
 }
 
 template <class T>
@@ -271,6 +157,20 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+cudaError_t launch_build_tables(const Plan &pl, int64_t *rowA, int64_t *rowC, int64_t *colB, int64_t *colC,
+                                int64_t *kA, int64_t *kB, cudaStream_t s)
+{
+    auto build = [&](const ModeList &L, int64_t count, int64_t *t0, int64_t *t1) {
+        int blocks = (int)std::min<int64_t>((count + 255) / 256, 2048);
+        if (blocks < 1) blocks = 1;
+        build_tables_kernel<<<blocks, 256, 0, s>>>(L, count, t0, t1);
+    };
+    build(pl.m, pl.M, rowA, rowC);
+    build(pl.n, pl.N, colB, colC);
+    build(pl.k, pl.K, kA, kB);
+    return cudaGetLastError();
+}
+
 bool dense_config_valid(DType t, int cfg)
 {
     if (cfg < 0 || cfg >= DENSE_NUM_CONFIGS) return false;
@@ -299,14 +199,8 @@ cudaError_t launch_dense(const Plan &pl, DType t, const void *A, const void *B, 
     int64_t *tab = static_cast<int64_t *>(ws);
     int64_t *rowA = tab, *rowC = rowA + pl.M, *colB = rowC + pl.M, *colC = colB + pl.N;
     int64_t *kA = colC + pl.N, *kB = kA + pl.K;
-    auto build = [&](const ModeList &L, int64_t count, int64_t *t0, int64_t *t1) {
-        int blocks = (int)std::min<int64_t>((count + 255) / 256, 2048);
-        if (blocks < 1) blocks = 1;
-        build_tables_kernel<<<blocks, 256, 0, s>>>(L, count, t0, t1);
-    };
-    build(pl.m, pl.M, rowA, rowC);
-    build(pl.n, pl.N, colB, colC);
-    build(pl.k, pl.K, kA, kB);
+    cudaError_t te = launch_build_tables(pl, rowA, rowC, colB, colC, kA, kB, s);
+    if (te != cudaSuccess) return te;
 
     const TileCfg c = kCfg[cfg];
     DenseParams p{};

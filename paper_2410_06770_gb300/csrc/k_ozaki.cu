@@ -1,0 +1,443 @@
+// k_ozaki.cu -- split-precision DGETT on bf16 tensor cores (modular
+// "Ozaki scheme II" form), with fp64 used only for the scaling, the integer
+// conversion of the inputs and the final recombination into C.
+//
+// For the canonical problem C[m,n] += sum_k A[m,k] B[k,n]:
+//  1. scale scan: for every row m of A the largest |A[m,k]| over K, for every
+//     column n of B the largest |B[k,n]| over K (bit patterns, atomicMax);
+//  2. integer conversion: A'[m,k] = round(A[m,k] * 2^{s_m}) with s_m chosen so
+//     |A'| <= 2^{ka}; B' likewise with t_n and kb bits.  ka + kb is fixed by
+//     the moduli: P = p_1 ... p_L must exceed 2 K 2^{ka+kb}, so the exact
+//     integer product A'B' is determined by its residues modulo the p_l;
+//  3. residues: A' mod p_l, symmetric in [-(p_l-1)/2, (p_l-1)/2] (|.| <= 127,
+//     exact in bf16), packed K-major, one slice per modulus;
+//  4. one tensor-core GEMM per modulus (all moduli in one launch), exact
+//     because K is consumed in chunks whose partial sums stay below 2^24 and
+//     are reduced modulo p_l after every chunk (the MODE_MOD epilogue);
+//  5. recombination: Garner's mixed-radix form of the residues, sign from a
+//     digit comparison with (P-1)/2, fp64 Horner evaluation, scaling by
+//     2^{-(s_m+t_n)} and C[m,n] += value.
+// Moduli: pairwise coprime odd numbers <= 255 (largest first).  The error
+// per element is at most about 2^-ka |A_m|max sum_k |B[k,n]| + 2^-kb
+// sum_k |A[m,k]| |B_n|max (the rounding of A' and B'), far below fp64
+// accuracy loss of a plain product for the default ka, kb >= 50.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_gemm.h"
+
+namespace gett {
+
+namespace {
+
+constexpr int TR = 32, TKP = 64, PT = 256;
+
+struct OzConsts {
+    int L;
+    int ka, kb;
+    int p[OZ_MAX_L];
+    float pf[OZ_MAX_L];
+    float invp[OZ_MAX_L];
+    float c21[OZ_MAX_L], c42[OZ_MAX_L];     // 2^21 mod p, 2^42 mod p
+    int inv[OZ_MAX_L][OZ_MAX_L];            // inv[i][j] = p_j^{-1} mod p_i (j < i)
+    int half[OZ_MAX_L];                     // mixed-radix digits of (P-1)/2
+};
+
+__device__ __forceinline__ uint16_t f2bf_bits(float x)
+{
+    __nv_bfloat16 b = __float2bfloat16_rn(x);
+    return *reinterpret_cast<uint16_t *>(&b);
+}
+
+// floor(log2(v)) of a positive finite double given its bit pattern
+__device__ __forceinline__ int ilog2_bits(uint64_t bits)
+{
+    const int e = (int)((bits >> 52) & 0x7FF);
+    if (e != 0) return e - 1023;
+    const uint64_t mant = bits & ((1ull << 52) - 1);
+    return -1074 + (63 - __clzll((long long)mant));
+}
+
+// shift s such that max * 2^s lies in [2^(k-1), 2^k); 0 for an all-zero row
+__device__ __forceinline__ int shift_for(uint64_t maxbits, int k)
+{
+    return maxbits == 0 ? 0 : (k - 1 - ilog2_bits(maxbits));
+}
+
+// round(|x| * 2^s) for |x| * 2^s < 2^53 (bit manipulation, no fp64 math)
+__device__ __forceinline__ uint64_t scaled_int(uint64_t bits, int s)
+{
+    const int e = (int)((bits >> 52) & 0x7FF);
+    if (e == 0x7FF) return 0;  // inf/nan: not supported by the split forms
+    const uint64_t mant = (bits & ((1ull << 52) - 1)) | (e ? (1ull << 52) : 0ull);
+    const int eff = e ? e : 1;
+    const int sh = eff - 1075 + s;  // value = mant * 2^sh
+    if (sh >= 0) return mant << (sh > 11 ? 11 : sh);  // only reachable for k = 53 edge cases
+    const int rs = -sh;
+    if (rs >= 60) return 0;
+    return (mant + (1ull << (rs - 1))) >> rs;
+}
+
+template <int ROW_FAST>
+__global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict__ src,
+                                                       const int64_t *__restrict__ rowT,
+                                                       const int64_t *__restrict__ kT, int64_t rows, int64_t K,
+                                                       unsigned long long *__restrict__ maxbits)
+{
+    __shared__ unsigned long long smax[TR];
+    __shared__ int64_t srow[TR];
+    __shared__ int64_t sk[TKP];
+    const int64_t tiles_k = (K + TKP - 1) / TKP;
+    const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
+        __syncthreads();
+        if (threadIdx.x < TR) {
+            srow[threadIdx.x] = r0 + threadIdx.x < rows ? rowT[r0 + threadIdx.x] : 0;
+            smax[threadIdx.x] = 0;
+        }
+        if (threadIdx.x < TKP) sk[threadIdx.x] = k0 + threadIdx.x < K ? kT[k0 + threadIdx.x] : 0;
+        __syncthreads();
+        unsigned long long local[TR * TKP / PT];
+        int lr[TR * TKP / PT];
+#pragma unroll
+        for (int j = 0; j < TR * TKP / PT; ++j) {
+            int e = threadIdx.x + j * PT;
+            int r, k;
+            if (ROW_FAST) { r = e % TR; k = e / TR; }
+            else { k = e % TKP; r = e / TKP; }
+            unsigned long long b = 0;
+            if (r0 + r < rows && k0 + k < K)
+                b = (unsigned long long)__double_as_longlong(__ldg(src + srow[r] + sk[k])) & 0x7FFFFFFFFFFFFFFFull;
+            if ((b >> 52) == 0x7FF) b = 0;
+            local[j] = b;
+            lr[j] = r;
+        }
+#pragma unroll
+        for (int j = 0; j < TR * TKP / PT; ++j)
+            if (local[j]) atomicMax(&smax[lr[j]], local[j]);
+        __syncthreads();
+        if (threadIdx.x < TR && r0 + threadIdx.x < rows && smax[threadIdx.x])
+            atomicMax(&maxbits[r0 + threadIdx.x], smax[threadIdx.x]);
+    }
+}
+
+// residues of round(x * 2^shift) for every modulus, packed [L][rows][ld] bf16
+template <int ROW_FAST>
+__global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict__ src,
+                                                       const int64_t *__restrict__ rowT,
+                                                       const int64_t *__restrict__ kT, int64_t rows, int64_t K,
+                                                       const unsigned long long *__restrict__ maxbits, int kbits,
+                                                       OzConsts c, uint16_t *__restrict__ out, int64_t ld)
+{
+    __shared__ uint64_t tile[TR][TKP + 1];
+    __shared__ int64_t srow[TR];
+    __shared__ int sshift[TR];
+    __shared__ int64_t sk[TKP];
+    const int64_t tiles_k = (K + TKP - 1) / TKP;
+    const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
+    const int64_t plane = rows * ld;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
+        __syncthreads();
+        if (threadIdx.x < TR) {
+            const bool in = r0 + threadIdx.x < rows;
+            srow[threadIdx.x] = in ? rowT[r0 + threadIdx.x] : 0;
+            sshift[threadIdx.x] = in ? shift_for(maxbits[r0 + threadIdx.x], kbits) : 0;
+        }
+        if (threadIdx.x < TKP) sk[threadIdx.x] = k0 + threadIdx.x < K ? kT[k0 + threadIdx.x] : 0;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < TR * TKP / PT; ++j) {
+            int e = threadIdx.x + j * PT;
+            int r, k;
+            if (ROW_FAST) { r = e % TR; k = e / TR; }
+            else { k = e % TKP; r = e / TKP; }
+            uint64_t b = 0;
+            if (r0 + r < rows && k0 + k < K) b = (uint64_t)__double_as_longlong(__ldg(src + srow[r] + sk[k]));
+            tile[r][k] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < TR * TKP / PT; ++j) {
+            int e = threadIdx.x + j * PT;
+            int k = e % TKP, r = e / TKP;
+            if (r0 + r >= rows || k0 + k >= K) continue;
+            const uint64_t bits = tile[r][k];
+            const bool neg = (bits >> 63) != 0;
+            const uint64_t v = scaled_int(bits & 0x7FFFFFFFFFFFFFFFull, sshift[r]);
+            const float lo = (float)(uint32_t)(v & 0x1FFFFF);
+            const float mid = (float)(uint32_t)((v >> 21) & 0x1FFFFF);
+            const float hi = (float)(uint32_t)(v >> 42);
+            uint16_t *o = out + (r0 + r) * ld + k0 + k;
+            for (int l = 0; l < c.L; ++l) {
+                const float pf = c.pf[l], ip = c.invp[l];
+                const float lr = fmaf(-rintf(lo * ip), pf, lo);
+                const float mr = fmaf(-rintf(mid * ip), pf, mid);
+                const float s = fmaf(hi, c.c42[l], fmaf(mr, c.c21[l], lr));
+                float x = fmaf(-rintf(s * ip), pf, s);
+                const float half = 0.5f * (pf - 1.f);
+                x = x > half ? x - pf : x;
+                x = x < -half ? x + pf : x;
+                o[l * plane] = f2bf_bits(neg ? -x : x);
+            }
+        }
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ R, int64_t M, int64_t N,
+                                                    const unsigned long long *__restrict__ maxA,
+                                                    const unsigned long long *__restrict__ maxB,
+                                                    const int64_t *__restrict__ rowC,
+                                                    const int64_t *__restrict__ colC, double *__restrict__ C,
+                                                    OzConsts c)
+{
+    const int64_t MN = M * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i % M, n = i / M;
+        int v[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            int r = R[(int64_t)l * MN + i];
+            v[l] = r < 0 ? r + c.p[l] : r;
+        }
+        // Garner: v[i] becomes the i-th mixed-radix digit
+#pragma unroll
+        for (int a = 1; a < L; ++a) {
+            int t = v[a];
+            const int pa = c.p[a];
+            const float ipa = c.invp[a];
+#pragma unroll
+            for (int b = 0; b < a; ++b) {
+                const int d = t - v[b] + 2 * pa;
+                const int x = d * c.inv[a][b];
+                int q = (int)((float)x * ipa);
+                int r = x - q * pa;
+                r = r < 0 ? r + pa : r;
+                r = r >= pa ? r - pa : r;
+                t = r;
+            }
+            v[a] = t;
+        }
+        // sign: compare with (P-1)/2 from the most significant digit
+        int cmp = 0;
+#pragma unroll
+        for (int a = L - 1; a >= 0; --a)
+            if (cmp == 0) cmp = v[a] > c.half[a] ? 1 : (v[a] < c.half[a] ? -1 : 0);
+        const bool negv = cmp > 0;
+        double h = 0.0;
+#pragma unroll
+        for (int a = L - 1; a >= 0; --a) {
+            const int d = negv ? (c.p[a] - 1 - v[a]) : v[a];
+            h = fma(h, (double)c.p[a], (double)d);
+        }
+        if (negv) h = -(h + 1.0);
+        const int e = -(shift_for(maxA[m], c.ka) + shift_for(maxB[n], c.kb));
+        // h * 2^e in two exact power-of-two steps (no overflow of the factors)
+        const int e1 = e / 2, e2 = e - e1;
+        const double f1 = __longlong_as_double((long long)(e1 + 1023) << 52);
+        const double f2 = __longlong_as_double((long long)(e2 + 1023) << 52);
+        const double val = (h * f1) * f2;
+        double *dst = C + rowC[m] + colC[n];
+        *dst = *dst + val;
+    }
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int modinv(int a, int m)
+{
+    int t = 0, nt = 1, r = m, nr = a % m;
+    while (nr) {
+        int q = r / nr;
+        int tmp = t - q * nt;
+        t = nt;
+        nt = tmp;
+        tmp = r - q * nr;
+        r = nr;
+        nr = tmp;
+    }
+    return t < 0 ? t + m : t;
+}
+
+// Number of moduli and bit budgets for a sum of length K.
+void oz_setup(int64_t K, int want_L, OzConsts *c)
+{
+    const double lk = std::log2((double)(K > 1 ? K : 1));
+    int L = want_L;
+    if (L <= 0) {
+        // smallest L that leaves >= 50 bits per operand
+        for (L = 8; L < OZ_MAX_L; ++L) {
+            double lp = 0;
+            for (int i = 0; i < L; ++i) lp += std::log2((double)kOzModuli[i]);
+            if (std::floor((lp - 1.0 - lk - 1e-6) / 2.0) >= 50) break;
+        }
+    }
+    if (L > OZ_MAX_L) L = OZ_MAX_L;
+    if (L < 2) L = 2;
+    double lp = 0;
+    for (int i = 0; i < L; ++i) lp += std::log2((double)kOzModuli[i]);
+    int kk = (int)std::floor((lp - 1.0 - lk - 1e-6) / 2.0);
+    if (kk > 52) kk = 52;
+    if (kk < 1) kk = 1;
+    c->L = L;
+    c->ka = kk;
+    c->kb = kk;
+    for (int i = 0; i < L; ++i) {
+        const int p = kOzModuli[i];
+        c->p[i] = p;
+        c->pf[i] = (float)p;
+        c->invp[i] = 1.0f / (float)p;
+        long long m21 = (1LL << 21) % p;
+        c->c21[i] = (float)m21;
+        c->c42[i] = (float)((m21 * m21) % p);
+        for (int j = 0; j < OZ_MAX_L; ++j) c->inv[i][j] = (j < i) ? modinv(kOzModuli[j] % p, p) : 0;
+    }
+    // digits of (P-1)/2: long division of the digits (p_i - 1) by 2 from the top
+    int carry = 0;
+    for (int i = L - 1; i >= 0; --i) {
+        const int cur = carry * c->p[i] + (c->p[i] - 1);
+        c->half[i] = cur / 2;
+        carry = cur % 2;
+    }
+}
+
+template <int L>
+void launch_crt_t(const int8_t *R, int64_t M, int64_t N, const unsigned long long *maxA,
+                  const unsigned long long *maxB, const int64_t *rowC, const int64_t *colC, double *C,
+                  const OzConsts &c, int num_sms, cudaStream_t s)
+{
+    const int64_t MN = M * N;
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((MN + 255) / 256, (int64_t)num_sms * 16));
+    oz_crt_kernel<L><<<blocks, 256, 0, s>>>(R, M, N, maxA, maxB, rowC, colC, C, c);
+}
+
+cudaError_t launch_crt(const int8_t *R, int64_t M, int64_t N, const unsigned long long *maxA,
+                       const unsigned long long *maxB, const int64_t *rowC, const int64_t *colC, double *C,
+                       const OzConsts &c, int num_sms, cudaStream_t s)
+{
+#define CASE(L)                                                                       \
+    case L:                                                                           \
+        launch_crt_t<L>(R, M, N, maxA, maxB, rowC, colC, C, c, num_sms, s);           \
+        break;
+    switch (c.L) {
+        CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
+        CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20)
+    default: return cudaErrorInvalidValue;
+    }
+#undef CASE
+    return cudaGetLastError();
+}
+
+struct OzLayout {
+    int64_t *rowA, *rowC, *colB, *colC, *kA, *kB;
+    unsigned long long *maxA, *maxB;
+    uint16_t *RA, *RB;
+    int8_t *R;
+    int64_t ld;
+    size_t total;
+};
+
+OzLayout oz_layout(const Plan &p, int L, void *ws)
+{
+    OzLayout o{};
+    char *w = static_cast<char *>(ws);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *r = w ? w + off : nullptr;
+        off += a256(bytes);
+        return r;
+    };
+    o.ld = tc_ld(p.K);
+    char *tab = take(sizeof(int64_t) * 2 * (size_t)(p.M + p.N + p.K));
+    o.rowA = reinterpret_cast<int64_t *>(tab);
+    if (tab) {
+        o.rowC = o.rowA + p.M;
+        o.colB = o.rowC + p.M;
+        o.colC = o.colB + p.N;
+        o.kA = o.colC + p.N;
+        o.kB = o.kA + p.K;
+    }
+    o.maxA = reinterpret_cast<unsigned long long *>(take(8 * (size_t)p.M));
+    o.maxB = reinterpret_cast<unsigned long long *>(take(8 * (size_t)p.N));
+    o.RA = reinterpret_cast<uint16_t *>(take(2 * (size_t)L * p.M * o.ld));
+    o.RB = reinterpret_cast<uint16_t *>(take(2 * (size_t)L * p.N * o.ld));
+    o.R = reinterpret_cast<int8_t *>(take((size_t)L * p.M * p.N));
+    o.total = off;
+    return o;
+}
+
+}  // namespace
+
+int ozaki_moduli_for(int64_t K, int want)
+{
+    OzConsts c;
+    oz_setup(K, want, &c);
+    return c.L;
+}
+
+int ozaki_bits_for(int64_t K, int L)
+{
+    OzConsts c;
+    oz_setup(K, L, &c);
+    return c.ka;
+}
+
+size_t ozaki_workspace_bytes(const Plan &p, int L)
+{
+    return oz_layout(p, L, nullptr).total;
+}
+
+cudaError_t launch_ozaki(const Plan &pl, int L_req, const void *A, const void *B, void *C, void *ws, int num_sms,
+                         int *err, cudaStream_t s)
+{
+    OzConsts c;
+    oz_setup(pl.K, L_req, &c);
+    OzLayout o = oz_layout(pl, c.L, ws);
+    cudaError_t e = launch_build_tables(pl, o.rowA, o.rowC, o.colB, o.colC, o.kA, o.kB, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(o.maxA, 0, 8 * (size_t)pl.M, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o.maxB, 0, 8 * (size_t)pl.N, s);
+    if (e != cudaSuccess) return e;
+    const double *Ab = static_cast<const double *>(A) + pl.offA;
+    const double *Bb = static_cast<const double *>(B) + pl.offB;
+    double *Cb = static_cast<double *>(C) + pl.offC;
+    auto first = [](const ModeList &Lm, const int64_t *st) { return Lm.n ? (st[0] < 0 ? -st[0] : st[0]) : 0; };
+    const bool a_row_fast = first(pl.m, pl.m.s0) != 0 && first(pl.m, pl.m.s0) <= first(pl.k, pl.k.s0);
+    const bool b_row_fast = first(pl.n, pl.n.s0) != 0 && first(pl.n, pl.n.s0) <= first(pl.k, pl.k.s1);
+    auto blocks_for = [&](int64_t rows) {
+        int64_t n = ((rows + TR - 1) / TR) * ((pl.K + TKP - 1) / TKP);
+        return (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * 8));
+    };
+    if (a_row_fast) oz_maxbits_kernel<1><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA);
+    else oz_maxbits_kernel<0><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA);
+    if (b_row_fast) oz_maxbits_kernel<1><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB);
+    else oz_maxbits_kernel<0><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB);
+    if (a_row_fast)
+        oz_residue_kernel<1><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA, c.ka, c, o.RA, o.ld);
+    else
+        oz_residue_kernel<0><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA, c.ka, c, o.RA, o.ld);
+    if (b_row_fast)
+        oz_residue_kernel<1><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB, c.kb, c, o.RB, o.ld);
+    else
+        oz_residue_kernel<0><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB, c.kb, c, o.RB, o.ld);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    TcGemmParams p{};
+    p.M = pl.M;
+    p.N = pl.N;
+    p.K = pl.K;
+    p.err = err;
+    p.kc_tiles = OZ_CHUNK_K / 64;
+    p.R = o.R;
+    e = launch_tc_gemm(TC_MODE_MOD, o.RA, o.RB, c.L, p, s);
+    if (e != cudaSuccess) return e;
+    return launch_crt(o.R, pl.M, pl.N, o.maxA, o.maxB, o.rowC, o.colC, Cb, c, num_sms, s);
+}
+
+}  // namespace gett

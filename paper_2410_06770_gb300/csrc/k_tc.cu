@@ -1,0 +1,305 @@
+// k_tc.cu -- tensor-core GEMM on packed bf16 operands (tcgen05 + TMA + TMEM).
+//
+// Every tensor-core form of xGETT first packs its operands into K-major bf16
+// matrices (one "slice" per z index: a modulus, a split piece group or a
+// batch entry), so this kernel only sees dense matrices:
+//     D_z[m, n] = sum_k Ap_z[m, k] * Bp_z[n, k]      (fp32 in TMEM)
+// The strided gather, the permutation and the precision logic live in the
+// packing kernels and in the epilogues.
+//
+// CTA = one 128 x 256 output tile of one slice.  Warp 0 issues TMA loads of
+// 128x64 (A) and 256x64 (B) bf16 tiles, 128-byte swizzled, into a 4-stage
+// shared-memory ring; warp 1 owns the TMEM allocation and issues the
+// tcgen05.mma instructions (M=128, N=256, K=16, four per stage) from one
+// thread; warps 2..9 are the epilogue: each reads its 32-lane quarter and
+// 128-column half of the accumulator with tcgen05.ld.
+//
+// Epilogue modes:
+//  * MODE_MOD (split-precision DGETT): K is processed in chunks short enough
+//    that every partial sum of integer residues stays below 2^24 and is
+//    therefore exact in fp32; after each chunk the epilogue folds the chunk's
+//    accumulator into a running residue modulo p_z held in registers, while
+//    the MMA warp already fills the other of two TMEM accumulators.  The
+//    final symmetric residues are stored as int8, layout [z][n][m].
+//  * MODE_F32: one chunk over all of K; the epilogue adds the fp32 tile into
+//    C through the planner's row/column offset tables (C[rowC[m] + colC[n]]).
+//
+// Every wait is bounded (tc::mbar_wait); a wait that gives up records an
+// error code in the device error word, and all roles fall through to the
+// common teardown, which releases TMEM.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_common.cuh"
+#include "tc_gemm.h"
+
+namespace gett {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NUM_EPI_WARPS = 8;
+constexpr int NUM_THREADS = (2 + NUM_EPI_WARPS) * 32;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+
+__constant__ float c_moduli[OZ_MAX_L] = {
+    kOzModuli[0],  kOzModuli[1],  kOzModuli[2],  kOzModuli[3],  kOzModuli[4],  kOzModuli[5],  kOzModuli[6],
+    kOzModuli[7],  kOzModuli[8],  kOzModuli[9],  kOzModuli[10], kOzModuli[11], kOzModuli[12], kOzModuli[13],
+    kOzModuli[14], kOzModuli[15], kOzModuli[16], kOzModuli[17], kOzModuli[18], kOzModuli[19]};
+
+template <int MODE>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               TcGemmParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;
+    uint64_t *acce = accf + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
+
+    constexpr uint32_t NCOLS = MODE == TC_MODE_MOD ? 512 : 256;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x;
+    const int tn = tile % p.tiles_n;
+    const int tm = tile / p.tiles_n;
+    const int z = blockIdx.y;
+    const int nkt = (p.K + BK - 1) / BK;
+    const int kc = MODE == TC_MODE_MOD ? p.kc_tiles : (nkt > 0 ? nkt : 1);
+    const int chunks = (nkt + kc - 1) / kc;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&accf[b], 1);
+            tc::mbar_init(&acce[b], NUM_EPI_WARPS);
+        }
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tmem_slot, NCOLS);
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tc::prefetch_tmap(&tmA);
+            tc::prefetch_tmap(&tmB);
+            int kt = 0;
+            for (; kt < nkt; ++kt) {
+                const int s = kt % STAGES;
+                if (!tc::mbar_wait(&empty[s], ((kt / STAGES) & 1) ^ 1, p.err, tc::ERR_WAIT_EMPTY)) break;
+                uint8_t *sa = base + s * STAGE_BYTES;
+                tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                tc::tma_load_3d(sa, &tmA, &full[s], kt * BK, tm * BM, z);
+                tc::tma_load_3d(sa + A_BYTES, &tmB, &full[s], kt * BK, tn * BN, z);
+            }
+            if (kt < nkt) {
+                // gave up: let the copies already issued land before the CTA exits
+                for (int j = (kt > STAGES ? kt - STAGES : 0); j < kt; ++j)
+                    tc::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, p.err, tc::ERR_WAIT_FULL);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            bool ok = true;
+            int kt = 0;
+            for (int c = 0; c < chunks && ok; ++c) {
+                const int buf = MODE == TC_MODE_MOD ? (c & 1) : 0;
+                if (!tc::mbar_wait(&acce[buf], ((c >> 1) & 1) ^ 1, p.err, tc::ERR_WAIT_ACC_EMPTY)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t d = tmem_base + buf * BN;
+                const int kend = min(nkt, (c + 1) * kc);
+                const int kbeg = kt;
+                for (; kt < kend; ++kt) {
+                    const int s = kt % STAGES;
+                    if (!tc::mbar_wait(&full[s], (kt / STAGES) & 1, p.err, tc::ERR_WAIT_FULL)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t sa = tc::smem_u32(base + s * STAGE_BYTES);
+                    const uint64_t ad = tc::smem_desc_sw128(sa);
+                    const uint64_t bd = tc::smem_desc_sw128(sa + A_BYTES);
+#pragma unroll
+                    for (int j = 0; j < BK / 16; ++j) {
+                        // advance 16 bf16 (32 bytes) along K inside the swizzled row
+                        tc::umma_bf16(d, ad + (uint64_t)(j * 2), bd + (uint64_t)(j * 2), idesc,
+                                      (kt > kbeg || j > 0) ? 1u : 0u);
+                    }
+                    tc::umma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                tc::umma_commit(&accf[buf]);
+            }
+        }
+    } else {
+        // epilogue warps
+        const int ew = warp - 2;
+        const int q = warp & 3;   // TMEM lane quarter this warp may access
+        const int h = ew >> 2;    // 128-column half
+        const int row = q * 32 + lane;
+        const int64_t m = (int64_t)tm * BM + row;
+        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        if (MODE == TC_MODE_MOD) {
+            const float pm = c_moduli[z];
+            const float inv = 1.0f / pm;
+            float res[128];
+#pragma unroll
+            for (int i = 0; i < 128; ++i) res[i] = 0.f;
+            bool ok = true;
+            for (int c = 0; c < chunks; ++c) {
+                const int buf = c & 1;
+                if (!tc::mbar_wait(&accf[buf], (c >> 1) & 1, p.err, tc::ERR_WAIT_ACC_FULL)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+                    uint32_t v[32];
+                    tc::tmem_ld_32x32b_x32(tmem_base + lane_addr + buf * BN + h * 128 + cb * 32, v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        // exact: |res| <= p/2 + 3 and |chunk sum| < 2^24 - 2^8
+                        const float x = res[cb * 32 + i] + __uint_as_float(v[i]);
+                        const float qq = rintf(x * inv);
+                        res[cb * 32 + i] = fmaf(-qq, pm, x);
+                    }
+                }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&acce[buf]);
+            }
+            if (ok && m < p.M) {
+                const float half = 0.5f * (pm - 1.f);
+                int8_t *R = p.R + (int64_t)z * p.N * p.M;
+#pragma unroll
+                for (int i = 0; i < 128; ++i) {
+                    const int64_t n = (int64_t)tn * BN + h * 128 + i;
+                    float r = res[i];
+                    r = r > half ? r - pm : r;
+                    r = r < -half ? r + pm : r;
+                    if (n < p.N) R[n * p.M + m] = (int8_t)__float2int_rn(r);
+                }
+            }
+        } else {
+            if (tc::mbar_wait(&accf[0], 0, p.err, tc::ERR_WAIT_ACC_FULL)) {
+                tc::tc_fence_after();
+                const int64_t rc = (m < p.M) ? p.rowC[m] : 0;
+                float *C = p.C + (int64_t)z * p.c_slice;
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+                    uint32_t v[32];
+                    tc::tmem_ld_32x32b_x32(tmem_base + lane_addr + h * 128 + cb * 32, v);
+                    tc::tmem_ld_wait();
+                    if (m < p.M) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const int64_t n = (int64_t)tn * BN + h * 128 + cb * 32 + i;
+                            if (n < p.N) {
+                                float *dst = C + rc + p.colC[n];
+                                *dst = *dst + __uint_as_float(v[i]);
+                            }
+                        }
+                    }
+                }
+                tc::tc_fence_before();
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem_base, NCOLS);
+    }
+}
+
+// ---- tensor maps ---------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
+
+// 3-D map over a packed operand [Z][rows][ld] of bf16: box 64 (K) x box_rows.
+bool make_map(CUtensorMap *map, const void *ptr, int64_t K, int64_t rows, int64_t ld, int64_t Z, int box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)Z};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(ld * 2 * rows)};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int64_t tc_ld(int64_t K) { return (K + 7) / 8 * 8; }
+
+cudaError_t launch_tc_gemm(int mode, const void *Ap, const void *Bp, int64_t Z, const TcGemmParams &prm,
+                           cudaStream_t s)
+{
+    if (prm.M <= 0 || prm.N <= 0 || prm.K <= 0 || Z <= 0) return cudaSuccess;
+    if (Z > 65535 || (mode == TC_MODE_MOD && Z > OZ_MAX_L)) return cudaErrorInvalidValue;
+    const int64_t ld = tc_ld(prm.K);
+    if ((reinterpret_cast<uintptr_t>(Ap) | reinterpret_cast<uintptr_t>(Bp)) & 15) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, Ap, prm.K, prm.M, ld, Z, BM) || !make_map(&mb, Bp, prm.K, prm.N, ld, Z, BN))
+        return cudaErrorInvalidValue;
+    TcGemmParams p = prm;
+    p.tiles_m = (int)((p.M + BM - 1) / BM);
+    p.tiles_n = (int)((p.N + BN - 1) / BN);
+    if ((int64_t)p.tiles_m * p.tiles_n > INT32_MAX) return cudaErrorInvalidValue;
+    dim3 grid(p.tiles_m * p.tiles_n, (unsigned)Z);
+    cudaError_t e;
+    if (mode == TC_MODE_MOD) {
+        if (p.kc_tiles < 1) return cudaErrorInvalidValue;
+        e = cudaFuncSetAttribute(tc_gemm_kernel<TC_MODE_MOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        tc_gemm_kernel<TC_MODE_MOD><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+    } else {
+        e = cudaFuncSetAttribute(tc_gemm_kernel<TC_MODE_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        tc_gemm_kernel<TC_MODE_F32><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gett

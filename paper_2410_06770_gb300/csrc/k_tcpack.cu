@@ -1,0 +1,186 @@
+// k_tcpack.cu -- the tensor-core forms of SGETT (fp32 split into bf16
+// pieces) and of the bf16-input contraction: gather the strided operands into
+// packed K-major bf16 matrices, then one tcgen05 GEMM whose epilogue adds the
+// fp32 result into C through INCC/PERM.
+//
+// Split forms.  x = hi + mid + lo with hi = bf16(x), mid = bf16(x - hi),
+// lo = bf16(x - hi - mid).  BF16X3 keeps two pieces and the products
+// hi*hi + hi*mid + mid*hi; BF16X6 keeps three pieces and the six products
+// whose piece ranks sum to at most 2.  The products are laid side by side
+// along K (A' = [hi | hi | mid], B' = [hi | mid | hi] for BF16X3), so one
+// GEMM over K' = 3K (6K) sums all of them into the same fp32 accumulator.
+//
+// Packing reads a 32 x 64 (row x k) tile through shared memory along
+// whichever index has the unit increment and writes packed rows along k.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_gemm.h"
+
+namespace gett {
+
+namespace {
+
+constexpr int TR = 32, TKP = 64, PT = 256;
+
+__device__ __forceinline__ uint16_t f2bf_bits(float x)
+{
+    __nv_bfloat16 b = __float2bfloat16_rn(x);
+    return *reinterpret_cast<uint16_t *>(&b);
+}
+
+__device__ __forceinline__ float bf_bits2f(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+template <class T>
+__device__ __forceinline__ float load_as_float(const T *p);
+template <>
+__device__ __forceinline__ float load_as_float<float>(const float *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_as_float<uint16_t>(const uint16_t *p) { return bf_bits2f(__ldg(p)); }
+
+// pieces[j] for block j of the packed K axis: 0 = hi, 1 = mid, 2 = lo
+struct PieceMap {
+    int nblocks;
+    int piece[8];
+};
+
+template <class T>
+__global__ void __launch_bounds__(PT) pack_pieces_kernel(const T *__restrict__ src, const int64_t *__restrict__ rowT,
+                                                        const int64_t *__restrict__ kT, int64_t rows, int64_t K,
+                                                        int row_fast, PieceMap pm, uint16_t *__restrict__ out,
+                                                        int64_t ld)
+{
+    __shared__ float tile[TR][TKP + 1];
+    __shared__ int64_t srow[TR];
+    __shared__ int64_t sk[TKP];
+    const int64_t tiles_k = (K + TKP - 1) / TKP;
+    const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
+        __syncthreads();
+        if (threadIdx.x < TR) srow[threadIdx.x] = r0 + threadIdx.x < rows ? rowT[r0 + threadIdx.x] : 0;
+        if (threadIdx.x < TKP) sk[threadIdx.x] = k0 + threadIdx.x < K ? kT[k0 + threadIdx.x] : 0;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < TR * TKP / PT; ++j) {
+            int e = threadIdx.x + j * PT;
+            int r, k;
+            if (row_fast) { r = e % TR; k = e / TR; }
+            else { k = e % TKP; r = e / TKP; }
+            float v = 0.f;
+            if (r0 + r < rows && k0 + k < K) v = load_as_float<T>(src + srow[r] + sk[k]);
+            tile[r][k] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < TR * TKP / PT; ++j) {
+            int e = threadIdx.x + j * PT;
+            int k = e % TKP, r = e / TKP;
+            if (r0 + r >= rows || k0 + k >= K) continue;
+            const float x = tile[r][k];
+            const uint16_t hb = f2bf_bits(x);
+            const float r1 = x - bf_bits2f(hb);
+            const uint16_t mb = f2bf_bits(r1);
+            const float r2 = r1 - bf_bits2f(mb);
+            const uint16_t lb = f2bf_bits(r2);
+            uint16_t *o = out + (r0 + r) * ld + k0 + k;
+            for (int b = 0; b < pm.nblocks; ++b) {
+                const int pc = pm.piece[b];
+                o[b * K] = pc == 0 ? hb : (pc == 1 ? mb : lb);
+            }
+        }
+    }
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+void pieces_for(int algo, bool is_a, PieceMap *pm)
+{
+    if (algo == GETT_ALGO_BF16X3) {
+        static const int A[3] = {0, 0, 1}, B[3] = {0, 1, 0};
+        pm->nblocks = 3;
+        for (int i = 0; i < 3; ++i) pm->piece[i] = is_a ? A[i] : B[i];
+    } else if (algo == GETT_ALGO_BF16X6) {
+        static const int A[6] = {0, 0, 1, 1, 0, 2}, B[6] = {0, 1, 0, 1, 2, 0};
+        pm->nblocks = 6;
+        for (int i = 0; i < 6; ++i) pm->piece[i] = is_a ? A[i] : B[i];
+    } else {
+        pm->nblocks = 1;
+        pm->piece[0] = 0;
+    }
+}
+
+}  // namespace
+
+int tc_split_blocks(int algo)
+{
+    return algo == GETT_ALGO_BF16X3 ? 3 : (algo == GETT_ALGO_BF16X6 ? 6 : 1);
+}
+
+size_t tc_split_workspace_bytes(const Plan &p, int algo)
+{
+    const int64_t Kp = p.K * tc_split_blocks(algo);
+    const int64_t ld = tc_ld(Kp);
+    return a256(sizeof(int64_t) * 2 * (size_t)(p.M + p.N + p.K)) + a256(2 * (size_t)p.M * ld) +
+           a256(2 * (size_t)p.N * ld);
+}
+
+cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, const void *B, void *C, void *ws,
+                            int num_sms, int *err, cudaStream_t s)
+{
+    if (t != DT_F32 && t != DT_BF16) return cudaErrorInvalidValue;
+    char *w = static_cast<char *>(ws);
+    int64_t *rowA = reinterpret_cast<int64_t *>(w);
+    int64_t *rowC = rowA + pl.M, *colB = rowC + pl.M, *colC = colB + pl.N, *kA = colC + pl.N, *kB = kA + pl.K;
+    w += a256(sizeof(int64_t) * 2 * (size_t)(pl.M + pl.N + pl.K));
+    const int nb = tc_split_blocks(algo);
+    const int64_t Kp = pl.K * nb, ld = tc_ld(Kp);
+    uint16_t *Ap = reinterpret_cast<uint16_t *>(w);
+    w += a256(2 * (size_t)pl.M * ld);
+    uint16_t *Bp = reinterpret_cast<uint16_t *>(w);
+
+    cudaError_t e = launch_build_tables(pl, rowA, rowC, colB, colC, kA, kB, s);
+    if (e != cudaSuccess) return e;
+    const size_t esz = dtype_size(t);
+    const char *Ab = static_cast<const char *>(A) + pl.offA * (int64_t)esz;
+    const char *Bb = static_cast<const char *>(B) + pl.offB * (int64_t)esz;
+    float *Cb = static_cast<float *>(C) + pl.offC;
+    auto first = [](const ModeList &L, const int64_t *st) { return L.n ? (st[0] < 0 ? -st[0] : st[0]) : 0; };
+    const int a_row_fast = first(pl.m, pl.m.s0) != 0 && first(pl.m, pl.m.s0) <= first(pl.k, pl.k.s0) ? 1 : 0;
+    const int b_row_fast = first(pl.n, pl.n.s0) != 0 && first(pl.n, pl.n.s0) <= first(pl.k, pl.k.s1) ? 1 : 0;
+    PieceMap pa, pb;
+    const int split_algo = t == DT_BF16 ? GETT_ALGO_NATIVE : algo;
+    pieces_for(split_algo, true, &pa);
+    pieces_for(split_algo, false, &pb);
+    auto blocks_for = [&](int64_t rows) {
+        int64_t n = ((rows + TR - 1) / TR) * ((pl.K + TKP - 1) / TKP);
+        return (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * 8));
+    };
+    if (t == DT_F32) {
+        pack_pieces_kernel<float><<<blocks_for(pl.M), PT, 0, s>>>((const float *)Ab, rowA, kA, pl.M, pl.K,
+                                                                   a_row_fast, pa, Ap, ld);
+        pack_pieces_kernel<float><<<blocks_for(pl.N), PT, 0, s>>>((const float *)Bb, colB, kB, pl.N, pl.K,
+                                                                   b_row_fast, pb, Bp, ld);
+    } else {
+        pack_pieces_kernel<uint16_t><<<blocks_for(pl.M), PT, 0, s>>>((const uint16_t *)Ab, rowA, kA, pl.M, pl.K,
+                                                                      a_row_fast, pa, Ap, ld);
+        pack_pieces_kernel<uint16_t><<<blocks_for(pl.N), PT, 0, s>>>((const uint16_t *)Bb, colB, kB, pl.N, pl.K,
+                                                                      b_row_fast, pb, Bp, ld);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    TcGemmParams p{};
+    p.M = pl.M;
+    p.N = pl.N;
+    p.K = Kp;
+    p.err = err;
+    p.C = Cb;
+    p.rowC = rowC;
+    p.colC = colC;
+    p.c_slice = 0;
+    return launch_tc_gemm(TC_MODE_F32, Ap, Bp, 1, p, s);
+}
+
+}  // namespace gett

@@ -16,6 +16,10 @@ int dense_effective_split(const Plan &p, int cfg, int split_k);
 cudaError_t launch_dense(const Plan &p, DType t, const void *A, const void *B, void *C, int cfg,
                          int split_k, void *ws, cudaStream_t s);
 
+// Offset tables of the three classes: rowA/rowC [M], colB/colC [N], kA/kB [K].
+cudaError_t launch_build_tables(const Plan &p, int64_t *rowA, int64_t *rowC, int64_t *colB, int64_t *colC,
+                                int64_t *kA, int64_t *kB, cudaStream_t s);
+
 // ---- streaming kernels (k_stream.cu) ----
 // OUTER: no contracted mode of extent > 1 (K == 1).
 cudaError_t launch_outer(const Plan &p, DType t, const void *A, const void *B, void *C, int num_sms,
@@ -24,5 +28,18 @@ cudaError_t launch_outer(const Plan &p, DType t, const void *A, const void *B, v
 size_t reduce_workspace_bytes(const Plan &p, DType t, int num_sms);
 cudaError_t launch_reduce(const Plan &p, DType t, const void *A, const void *B, void *C, int num_sms,
                           void *ws, cudaStream_t s);
+
+// ---- tensor-core forms ----
+// s / bf16 inputs: packed bf16 pieces + one tcgen05 GEMM (k_tcpack.cu)
+int tc_split_blocks(int algo);
+size_t tc_split_workspace_bytes(const Plan &p, int algo);
+cudaError_t launch_tc_split(const Plan &p, DType t, int algo, const void *A, const void *B, void *C, void *ws,
+                            int num_sms, int *err, cudaStream_t s);
+// d: split-precision modular form (k_ozaki.cu)
+int ozaki_moduli_for(int64_t K, int want);
+int ozaki_bits_for(int64_t K, int L);
+size_t ozaki_workspace_bytes(const Plan &p, int L);
+cudaError_t launch_ozaki(const Plan &p, int L, const void *A, const void *B, void *C, void *ws, int num_sms,
+                         int *err, cudaStream_t s);
 
 }  // namespace gett

@@ -30,6 +30,11 @@ Choice heuristic_choice(const Plan &p, DType t, int num_sms)
         c.family = GETT_FAMILY_REDUCE;
         return c;
     }
+    if (t == DT_BF16 && p.M >= 128 && p.N >= 128 && p.K >= 64) {
+        c.family = GETT_FAMILY_TC;
+        c.algo = GETT_ALGO_NATIVE;
+        return c;
+    }
     c.family = GETT_FAMILY_DENSE;
     for (int cfg = 0; cfg < DENSE_NUM_CONFIGS; ++cfg) {
         if (!dense_config_valid(t, cfg)) continue;
@@ -56,6 +61,34 @@ Choice heuristic_choice(const Plan &p, DType t, int num_sms)
 int choose(const Plan &p, DType t, const gett_options *opt, int num_sms, Choice *out)
 {
     Choice c = heuristic_choice(p, t, num_sms);
+    if (opt && opt->algo == GETT_ALGO_OZAKI_BF16) {
+        if (t != DT_F64) return GETT_ERR_UNSUPPORTED;
+        c = Choice{};
+        c.family = GETT_FAMILY_TC;
+        c.algo = GETT_ALGO_OZAKI_BF16;
+        c.moduli = ozaki_moduli_for(p.K, opt->moduli);
+        c.selector = 3;
+        *out = c;
+        return GETT_OK;
+    }
+    if (opt && (opt->algo == GETT_ALGO_BF16X3 || opt->algo == GETT_ALGO_BF16X6)) {
+        if (t != DT_F32) return GETT_ERR_UNSUPPORTED;
+        c = Choice{};
+        c.family = GETT_FAMILY_TC;
+        c.algo = opt->algo;
+        c.selector = 3;
+        *out = c;
+        return GETT_OK;
+    }
+    if (opt && opt->family == GETT_FAMILY_TC) {
+        if (t != DT_BF16) return GETT_ERR_UNSUPPORTED;
+        c = Choice{};
+        c.family = GETT_FAMILY_TC;
+        c.algo = GETT_ALGO_NATIVE;
+        c.selector = 3;
+        *out = c;
+        return GETT_OK;
+    }
     if (opt) {
         if (opt->algo != GETT_ALGO_DEFAULT && opt->algo != GETT_ALGO_NATIVE)
             return GETT_ERR_UNSUPPORTED;

@@ -1,0 +1,40 @@
+// tc_gemm.h -- host interface of the tensor-core GEMM on packed bf16 data.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace gett {
+
+enum TcMode : int { TC_MODE_F32 = 0, TC_MODE_MOD = 1 };
+
+// Moduli of the split-precision DGETT: pairwise coprime odd numbers <= 255,
+// largest first, so symmetric residues fit in [-127, 127] (exact in bf16).
+constexpr int OZ_MAX_L = 20;
+constexpr int kOzModuli[OZ_MAX_L] = {255, 253, 251, 247, 241, 239, 233, 229, 227, 223,
+                                     217, 211, 199, 197, 193, 191, 181, 179, 173, 167};
+// K per exact fp32 chunk: 1024 * 127^2 + 2^8 < 2^24.
+constexpr int OZ_CHUNK_K = 1024;
+
+struct TcGemmParams {
+    int64_t M, N, K;     // D_z is M x N, sum over K
+    int tiles_m, tiles_n;  // filled by the launcher
+    int kc_tiles;        // MODE_MOD: 64-wide K tiles per exact fp32 chunk
+    int *err;            // device error word (bounded waits)
+    // MODE_MOD: slice z is reduced modulo kOzModuli[z]
+    int8_t *R;            // [Z][N][M] symmetric residues
+    // MODE_F32: C[z * c_slice + rowC[m] + colC[n]] += D_z[m, n]
+    float *C;
+    const int64_t *rowC, *colC;
+    int64_t c_slice;
+};
+
+// Row pitch (elements) of a packed operand with K columns: multiple of 8
+// bf16 so every row starts on a 16-byte boundary (TMA requirement).
+int64_t tc_ld(int64_t K);
+
+// Ap: [Z][M][tc_ld(K)] bf16, Bp: [Z][N][tc_ld(K)] bf16, both 16-byte aligned.
+cudaError_t launch_tc_gemm(int mode, const void *Ap, const void *Bp, int64_t Z, const TcGemmParams &p,
+                           cudaStream_t s);
+
+}  // namespace gett

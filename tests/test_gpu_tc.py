@@ -1,0 +1,143 @@
+"""GPU parity of the tensor-core (tcgen05) forms against the oracle.
+
+* bf16 inputs, tensor cores (sbgett, family tc): integer data bit-exact,
+  float data within the fp32 rounding bound.
+* SGETT split forms (BF16X3, BF16X6): normwise error vs the fp64 oracle of
+  the fp32 inputs.
+* Split-precision DGETT (modular form on bf16 tensor cores): integer data
+  bit-exact (every scaled input is exact and the modular product is exact);
+  float data normwise within 1e-13 of the long-double oracle, including
+  log-uniform magnitudes over 1e-8..1e8 with random signs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_06770_gb300 import gett, synth
+from tests._gpu_util import compare, oracle_ref, problem_for, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2410_06770_gb300 import build
+    build.build()
+    gett.lib()
+
+
+def _normwise(p, got, ref):
+    g = synth.gather(p.lc, got).astype(np.float64)
+    r = synth.gather(p.lc, ref)
+    return float(np.linalg.norm(g - r) / np.linalg.norm(r))
+
+
+# shapes that span several 128x256 tiles with ragged M, N and K tails
+SHAPES = [
+    synth.Signature((130, 70), (70, 300), (1,), (0,), (0, 1)),                # GEMM, ragged
+    synth.Signature((37, 9, 5), (5, 9, 61), (1, 2), (1, 0), (1, 0, 2)),        # 2 K modes, permuted out
+    synth.Signature((257, 3, 33), (33, 129), (2,), (0,), (2, 0, 1)),          # M two modes
+    synth.Signature((64, 1100), (1100, 40), (1,), (0,), (1, 0)),              # K over one chunk
+]
+
+
+@pytest.mark.parametrize("idx", range(len(SHAPES)))
+@pytest.mark.parametrize("kinds", [("contig",) * 3, ("padded", "negative", "padded"), ("rowmajor", "lower_rank", "contig")])
+def test_bf16_tensor_core_integer_exact(idx, kinds):
+    rng = np.random.default_rng(10 + idx)
+    p = synth.make_problem(SHAPES[idx], rng, np.float64, "smallint", kinds, "int")
+    q = problem_for("sb", p)
+    got, rep = run_gpu("sb", q, mode="ex", opts=gett.options(family="tc"))
+    assert rep["family_name"] == "tc"
+    compare("sb", q, got, oracle_ref(q), exact=True)
+
+
+@pytest.mark.parametrize("idx", range(len(SHAPES)))
+def test_bf16_tensor_core_float(idx):
+    rng = np.random.default_rng(20 + idx)
+    p = synth.make_problem(SHAPES[idx], rng, np.float64, "uniform", ("padded", "contig", "negative"), "uniform")
+    q = problem_for("sb", p)
+    got, rep = run_gpu("sb", q, mode="ex", opts=gett.options(family="tc"))
+    compare("sb", q, got, oracle_ref(q))
+
+
+@pytest.mark.parametrize("algo,tol", [("bf16x6", 1e-5), ("bf16x3", 2e-5)])
+@pytest.mark.parametrize("idx", range(len(SHAPES)))
+@pytest.mark.parametrize("dist", ["uniform", "normal"])
+def test_sgett_split_forms(algo, tol, idx, dist):
+    rng = np.random.default_rng(30 + idx)
+    p = synth.make_problem(SHAPES[idx], rng, np.float64, dist, ("padded", "negative", "contig"), "zeros")
+    q = problem_for("s", p)
+    got, rep = run_gpu("s", q, mode="ex", opts=gett.options(algo=algo))
+    assert rep["family_name"] == "tc"
+    rel = _normwise(q, got, oracle_ref(q))
+    assert rel <= tol, rel
+
+
+def test_sgett_split_on_small_workload_shapes():
+    """32x24x16x20 shapes in fp32 (the split-precision workload's SGETT part)."""
+    p = synth.cfg_small_dgett(dist="logu")
+    q = problem_for("s", p)
+    got, _ = run_gpu("s", q, mode="ex", opts=gett.options(algo="bf16x6"))
+    assert _normwise(q, got, oracle_ref(q)) <= 1e-5
+
+
+@pytest.mark.parametrize("idx", range(len(SHAPES)))
+@pytest.mark.parametrize("kinds", [("contig",) * 3, ("padded", "negative", "padded")])
+def test_ozaki_integer_exact(idx, kinds):
+    rng = np.random.default_rng(40 + idx)
+    p = synth.make_problem(SHAPES[idx], rng, np.float64, "int", kinds, "int")
+    got, rep = run_gpu("d", p, mode="ex", opts=gett.options(algo="ozaki_bf16"))
+    assert rep["family_name"] == "tc" and rep["moduli"] >= 8
+    compare("d", p, got, oracle_ref(p), exact=True)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "normal", "logu"])
+@pytest.mark.parametrize("idx", range(len(SHAPES)))
+def test_ozaki_float(dist, idx):
+    rng = np.random.default_rng(50 + idx)
+    p = synth.make_problem(SHAPES[idx], rng, np.float64, dist, ("padded", "negative", "contig"), "uniform")
+    got, rep = run_gpu("d", p, mode="ex", opts=gett.options(algo="ozaki_bf16"))
+    ref = oracle.gett_problem(p, "ld", nthreads=4)
+    rel = _normwise(p, got, ref)
+    assert rel <= 1e-13, rel
+    gaps = synth.gap_mask(p.lc)
+    assert np.array_equal(got[gaps], p.C[gaps])
+
+
+@pytest.mark.parametrize("family", synth.THESIS_TESTS)
+def test_ozaki_thesis_families(family):
+    p = synth.thesis_problem(family, 60, np.float64, "uniform", c_dist="uniform")
+    got, _ = run_gpu("d", p, mode="ex", opts=gett.options(algo="ozaki_bf16"))
+    ref = oracle.gett_problem(p, "ld")
+    g = synth.gather(p.lc, got)
+    r = synth.gather(p.lc, ref)
+    nr = np.linalg.norm(r)
+    assert np.linalg.norm(g - r) <= 1e-13 * (nr if nr else 1.0)
+
+
+def test_ozaki_small_workload_logu():
+    """The split-precision workload: 32x24x16x20 shapes, log-uniform
+    magnitudes over 1e-8..1e8 with random signs, vs the long-double oracle."""
+    p = synth.cfg_small_dgett(dist="logu")
+    got, rep = run_gpu("d", p, mode="ex", opts=gett.options(algo="ozaki_bf16"))
+    ref = oracle.gett_problem(p, "ld", nthreads=4)
+    rel = _normwise(p, got, ref)
+    assert rel <= 1e-13, rel
+    plain, _ = run_gpu("d", p)
+    assert _normwise(p, plain, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("L", [10, 14, 18])
+def test_ozaki_moduli_counts(L):
+    p = synth.cfg_small_dgett(dist="normal")
+    got, rep = run_gpu("d", p, mode="ex", opts=gett.options(algo="ozaki_bf16", moduli=L))
+    assert rep["moduli"] == L
+    ref = oracle.gett_problem(p, "ld", nthreads=4)
+    rel = _normwise(p, got, ref)
+    # fewer moduli leave fewer bits per operand: error ~ 2^-bits, with
+    # bits = floor((log2(p_1...p_L) - 1 - log2 K) / 2), capped at 52
+    moduli = [255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193, 191, 181, 179]
+    lp = sum(np.log2(moduli[:L]))
+    bits = min(52, int(np.floor((lp - 1 - np.log2(480) - 1e-6) / 2)))
+    assert rel <= 2.0 ** (-bits + 6), (rel, bits)
