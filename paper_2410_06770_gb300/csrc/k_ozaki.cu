@@ -15,8 +15,10 @@
 //     because K is consumed in chunks whose partial sums stay below 2^24 and
 //     are reduced modulo p_l after every chunk (the MODE_MOD epilogue);
 //  5. recombination: Garner's mixed-radix form of the residues, sign from a
-//     digit comparison with (P-1)/2, fp64 Horner evaluation, scaling by
-//     2^{-(s_m+t_n)} and C[m,n] += value.
+//     digit comparison with (P-1)/2, exact integer Horner evaluation in three
+//     64-bit limbs, one correctly rounded conversion to fp64, scaling by
+//     2^{-(s_m+t_n)} and C[m,n] += value.  When the exact sum fits in 53 bits
+//     (integer data, for instance) the added value is exact.
 // Moduli: pairwise coprime odd numbers <= 255 (largest first).  The error
 // per element is at most about 2^-ka |A_m|max sum_k |B[k,n]| + 2^-kb
 // sum_k |A[m,k]| |B_n|max (the rounding of A' and B'), far below fp64
@@ -230,19 +232,56 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
         for (int a = L - 1; a >= 0; --a)
             if (cmp == 0) cmp = v[a] > c.half[a] ? 1 : (v[a] < c.half[a] ? -1 : 0);
         const bool negv = cmp > 0;
-        double h = 0.0;
+        // exact Horner evaluation of the mixed-radix digits in three 64-bit
+        // limbs (|X| < P < 2^160), then one correctly rounded conversion
+        uint64_t h0 = 0, h1 = 0, h2 = 0;
 #pragma unroll
         for (int a = L - 1; a >= 0; --a) {
-            const int d = negv ? (c.p[a] - 1 - v[a]) : v[a];
-            h = fma(h, (double)c.p[a], (double)d);
+            const uint64_t pa = (uint64_t)c.p[a];
+            const uint64_t d = (uint64_t)(negv ? (c.p[a] - 1 - v[a]) : v[a]);
+            const uint64_t l0 = h0 * pa, c0 = __umul64hi(h0, pa);
+            const uint64_t l1 = h1 * pa, c1 = __umul64hi(h1, pa);
+            h2 = h2 * pa + c1;
+            h1 = l1 + c0;
+            h2 += (h1 < c0) ? 1 : 0;
+            h0 = l0 + d;
+            const uint64_t k0 = (h0 < d) ? 1 : 0;
+            h1 += k0;
+            h2 += (k0 && h1 == 0) ? 1 : 0;
         }
-        if (negv) h = -(h + 1.0);
-        const int e = -(shift_for(maxA[m], c.ka) + shift_for(maxB[n], c.kb));
-        // h * 2^e in two exact power-of-two steps (no overflow of the factors)
+        if (negv) {  // value = -(X' + 1)
+            h0 += 1;
+            if (h0 == 0) {
+                h1 += 1;
+                if (h1 == 0) h2 += 1;
+            }
+        }
+        // normalise to 64 bits with a sticky bit, convert (round to nearest)
+        int drop;
+        uint64_t top;
+        if (h2) {
+            const int lz = __clzll((long long)h2);
+            top = (h2 << lz) | (lz ? (h1 >> (64 - lz)) : 0);
+            const uint64_t rest_hi = lz ? (h1 << lz) : h1;
+            top |= (rest_hi | h0) ? 1 : 0;
+            drop = 128 - lz;
+        } else if (h1) {
+            const int lz = __clzll((long long)h1);
+            top = (h1 << lz) | (lz ? (h0 >> (64 - lz)) : 0);
+            const uint64_t rest = lz ? (h0 << lz) : h0;
+            top |= rest ? 1 : 0;
+            drop = 64 - lz;
+        } else {
+            top = h0;
+            drop = 0;
+        }
+        const double mag = __ull2double_rn(top);
+        const int e = drop - (shift_for(maxA[m], c.ka) + shift_for(maxB[n], c.kb));
+        // mag * 2^e in two exact power-of-two steps (no overflow of the factors)
         const int e1 = e / 2, e2 = e - e1;
         const double f1 = __longlong_as_double((long long)(e1 + 1023) << 52);
         const double f2 = __longlong_as_double((long long)(e2 + 1023) << 52);
-        const double val = (h * f1) * f2;
+        const double val = negv ? -((mag * f1) * f2) : (mag * f1) * f2;
         double *dst = C + rowC[m] + colC[n];
         *dst = *dst + val;
     }

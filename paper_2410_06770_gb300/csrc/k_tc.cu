@@ -21,8 +21,13 @@
 //    accumulator into a running residue modulo p_z held in registers, while
 //    the MMA warp already fills the other of two TMEM accumulators.  The
 //    final symmetric residues are stored as int8, layout [z][n][m].
-//  * MODE_F32: one chunk over all of K; the epilogue adds the fp32 tile into
-//    C through the planner's row/column offset tables (C[rowC[m] + colC[n]]).
+//  * MODE_F32: K is processed in chunks of kc_tiles 64-wide tiles; the
+//    epilogue adds each chunk's fp32 sum into fp32 running sums held in
+//    registers (again overlapping the next chunk's MMAs through the two TMEM
+//    accumulators), and finally adds the tile into C through the planner's
+//    row/column offset tables (C[rowC[m] + colC[n]]).  Chunking bounds the
+//    length of every in-accumulator sum, which keeps long split-precision
+//    sums accurate.
 //
 // Every wait is bounded (tc::mbar_wait); a wait that gives up records an
 // error code in the device error word, and all roles fall through to the
@@ -67,14 +72,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint64_t *acce = accf + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
 
-    constexpr uint32_t NCOLS = MODE == TC_MODE_MOD ? 512 : 256;
+    constexpr uint32_t NCOLS = 512;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x;
     const int tn = tile % p.tiles_n;
     const int tm = tile / p.tiles_n;
     const int z = blockIdx.y;
     const int nkt = (p.K + BK - 1) / BK;
-    const int kc = MODE == TC_MODE_MOD ? p.kc_tiles : (nkt > 0 ? nkt : 1);
+    const int kc = p.kc_tiles > 0 ? p.kc_tiles : (nkt > 0 ? nkt : 1);
     const int chunks = (nkt + kc - 1) / kc;
 
     if (threadIdx.x == 0) {
@@ -118,7 +123,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             bool ok = true;
             int kt = 0;
             for (int c = 0; c < chunks && ok; ++c) {
-                const int buf = MODE == TC_MODE_MOD ? (c & 1) : 0;
+                const int buf = c & 1;
                 if (!tc::mbar_wait(&acce[buf], ((c >> 1) & 1) ^ 1, p.err, tc::ERR_WAIT_ACC_EMPTY)) {
                     ok = false;
                     break;
@@ -157,38 +162,42 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int row = q * 32 + lane;
         const int64_t m = (int64_t)tm * BM + row;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-        if (MODE == TC_MODE_MOD) {
-            const float pm = c_moduli[z];
-            const float inv = 1.0f / pm;
-            float res[128];
+        const float pm = MODE == TC_MODE_MOD ? c_moduli[z] : 1.f;
+        const float inv = 1.0f / pm;
+        float res[128];
 #pragma unroll
-            for (int i = 0; i < 128; ++i) res[i] = 0.f;
-            bool ok = true;
-            for (int c = 0; c < chunks; ++c) {
-                const int buf = c & 1;
-                if (!tc::mbar_wait(&accf[buf], (c >> 1) & 1, p.err, tc::ERR_WAIT_ACC_FULL)) {
-                    ok = false;
-                    break;
-                }
-                tc::tc_fence_after();
+        for (int i = 0; i < 128; ++i) res[i] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < chunks; ++c) {
+            const int buf = c & 1;
+            if (!tc::mbar_wait(&accf[buf], (c >> 1) & 1, p.err, tc::ERR_WAIT_ACC_FULL)) {
+                ok = false;
+                break;
+            }
+            tc::tc_fence_after();
 #pragma unroll
-                for (int cb = 0; cb < 4; ++cb) {
-                    uint32_t v[32];
-                    tc::tmem_ld_32x32b_x32(tmem_base + lane_addr + buf * BN + h * 128 + cb * 32, v);
-                    tc::tmem_ld_wait();
+            for (int cb = 0; cb < 4; ++cb) {
+                uint32_t v[32];
+                tc::tmem_ld_32x32b_x32(tmem_base + lane_addr + buf * BN + h * 128 + cb * 32, v);
+                tc::tmem_ld_wait();
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
+                for (int i = 0; i < 32; ++i) {
+                    const float x = res[cb * 32 + i] + __uint_as_float(v[i]);
+                    if (MODE == TC_MODE_MOD) {
                         // exact: |res| <= p/2 + 3 and |chunk sum| < 2^24 - 2^8
-                        const float x = res[cb * 32 + i] + __uint_as_float(v[i]);
                         const float qq = rintf(x * inv);
                         res[cb * 32 + i] = fmaf(-qq, pm, x);
+                    } else {
+                        res[cb * 32 + i] = x;
                     }
                 }
-                tc::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&acce[buf]);
             }
-            if (ok && m < p.M) {
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[buf]);
+        }
+        if (ok && m < p.M) {
+            if (MODE == TC_MODE_MOD) {
                 const float half = 0.5f * (pm - 1.f);
                 int8_t *R = p.R + (int64_t)z * p.N * p.M;
 #pragma unroll
@@ -199,29 +208,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     r = r < -half ? r + pm : r;
                     if (n < p.N) R[n * p.M + m] = (int8_t)__float2int_rn(r);
                 }
-            }
-        } else {
-            if (tc::mbar_wait(&accf[0], 0, p.err, tc::ERR_WAIT_ACC_FULL)) {
-                tc::tc_fence_after();
-                const int64_t rc = (m < p.M) ? p.rowC[m] : 0;
-                float *C = p.C + (int64_t)z * p.c_slice;
+            } else {
+                float *C = p.C + (int64_t)z * p.c_slice + p.rowC[m];
 #pragma unroll
-                for (int cb = 0; cb < 4; ++cb) {
-                    uint32_t v[32];
-                    tc::tmem_ld_32x32b_x32(tmem_base + lane_addr + h * 128 + cb * 32, v);
-                    tc::tmem_ld_wait();
-                    if (m < p.M) {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const int64_t n = (int64_t)tn * BN + h * 128 + cb * 32 + i;
-                            if (n < p.N) {
-                                float *dst = C + rc + p.colC[n];
-                                *dst = *dst + __uint_as_float(v[i]);
-                            }
-                        }
+                for (int i = 0; i < 128; ++i) {
+                    const int64_t n = (int64_t)tn * BN + h * 128 + i;
+                    if (n < p.N) {
+                        float *dst = C + p.colC[n];
+                        *dst = *dst + res[i];
                     }
                 }
-                tc::tc_fence_before();
             }
         }
     }
@@ -288,7 +284,7 @@ cudaError_t launch_tc_gemm(int mode, const void *Ap, const void *Bp, int64_t Z, 
     dim3 grid(p.tiles_m * p.tiles_n, (unsigned)Z);
     cudaError_t e;
     if (mode == TC_MODE_MOD) {
-        if (p.kc_tiles < 1) return cudaErrorInvalidValue;
+        if (p.kc_tiles < 1 || p.kc_tiles * BK > OZ_CHUNK_K) return cudaErrorInvalidValue;
         e = cudaFuncSetAttribute(tc_gemm_kernel<TC_MODE_MOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SMEM_BYTES);
         if (e != cudaSuccess) return e;

@@ -46,16 +46,19 @@ struct PieceMap {
     int piece[8];
 };
 
+// Writes, for every row, nblocks blocks of Kb (>= K, multiple of 64) packed
+// values; block b holds piece pm.piece[b] of the row's K values followed by
+// zeros up to Kb, so every 64-wide K tile belongs to exactly one block.
 template <class T>
 __global__ void __launch_bounds__(PT) pack_pieces_kernel(const T *__restrict__ src, const int64_t *__restrict__ rowT,
                                                         const int64_t *__restrict__ kT, int64_t rows, int64_t K,
-                                                        int row_fast, PieceMap pm, uint16_t *__restrict__ out,
-                                                        int64_t ld)
+                                                        int64_t Kb, int row_fast, PieceMap pm,
+                                                        uint16_t *__restrict__ out, int64_t ld)
 {
     __shared__ float tile[TR][TKP + 1];
     __shared__ int64_t srow[TR];
     __shared__ int64_t sk[TKP];
-    const int64_t tiles_k = (K + TKP - 1) / TKP;
+    const int64_t tiles_k = (Kb + TKP - 1) / TKP;
     const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
@@ -78,8 +81,8 @@ __global__ void __launch_bounds__(PT) pack_pieces_kernel(const T *__restrict__ s
         for (int j = 0; j < TR * TKP / PT; ++j) {
             int e = threadIdx.x + j * PT;
             int k = e % TKP, r = e / TKP;
-            if (r0 + r >= rows || k0 + k >= K) continue;
-            const float x = tile[r][k];
+            if (r0 + r >= rows || k0 + k >= Kb) continue;
+            const float x = tile[r][k];  // zero for k >= K
             const uint16_t hb = f2bf_bits(x);
             const float r1 = x - bf_bits2f(hb);
             const uint16_t mb = f2bf_bits(r1);
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(PT) pack_pieces_kernel(const T *__restrict__ s
             uint16_t *o = out + (r0 + r) * ld + k0 + k;
             for (int b = 0; b < pm.nblocks; ++b) {
                 const int pc = pm.piece[b];
-                o[b * K] = pc == 0 ? hb : (pc == 1 ? mb : lb);
+                o[b * Kb] = pc == 0 ? hb : (pc == 1 ? mb : lb);
             }
         }
     }
@@ -119,9 +122,11 @@ int tc_split_blocks(int algo)
     return algo == GETT_ALGO_BF16X3 ? 3 : (algo == GETT_ALGO_BF16X6 ? 6 : 1);
 }
 
+int64_t block_len(int64_t K) { return (K + 63) / 64 * 64; }
+
 size_t tc_split_workspace_bytes(const Plan &p, int algo)
 {
-    const int64_t Kp = p.K * tc_split_blocks(algo);
+    const int64_t Kp = block_len(p.K) * tc_split_blocks(algo);
     const int64_t ld = tc_ld(Kp);
     return a256(sizeof(int64_t) * 2 * (size_t)(p.M + p.N + p.K)) + a256(2 * (size_t)p.M * ld) +
            a256(2 * (size_t)p.N * ld);
@@ -135,8 +140,8 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
     int64_t *rowA = reinterpret_cast<int64_t *>(w);
     int64_t *rowC = rowA + pl.M, *colB = rowC + pl.M, *colC = colB + pl.N, *kA = colC + pl.N, *kB = kA + pl.K;
     w += a256(sizeof(int64_t) * 2 * (size_t)(pl.M + pl.N + pl.K));
-    const int nb = tc_split_blocks(algo);
-    const int64_t Kp = pl.K * nb, ld = tc_ld(Kp);
+    const int nb = t == DT_BF16 ? 1 : tc_split_blocks(algo);
+    const int64_t Kb = block_len(pl.K), Kp = Kb * nb, ld = tc_ld(Kp);
     uint16_t *Ap = reinterpret_cast<uint16_t *>(w);
     w += a256(2 * (size_t)pl.M * ld);
     uint16_t *Bp = reinterpret_cast<uint16_t *>(w);
@@ -155,19 +160,19 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
     pieces_for(split_algo, true, &pa);
     pieces_for(split_algo, false, &pb);
     auto blocks_for = [&](int64_t rows) {
-        int64_t n = ((rows + TR - 1) / TR) * ((pl.K + TKP - 1) / TKP);
+        int64_t n = ((rows + TR - 1) / TR) * ((Kb + TKP - 1) / TKP);
         return (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * 8));
     };
     if (t == DT_F32) {
         pack_pieces_kernel<float><<<blocks_for(pl.M), PT, 0, s>>>((const float *)Ab, rowA, kA, pl.M, pl.K,
-                                                                   a_row_fast, pa, Ap, ld);
+                                                                   Kb, a_row_fast, pa, Ap, ld);
         pack_pieces_kernel<float><<<blocks_for(pl.N), PT, 0, s>>>((const float *)Bb, colB, kB, pl.N, pl.K,
-                                                                   b_row_fast, pb, Bp, ld);
+                                                                   Kb, b_row_fast, pb, Bp, ld);
     } else {
         pack_pieces_kernel<uint16_t><<<blocks_for(pl.M), PT, 0, s>>>((const uint16_t *)Ab, rowA, kA, pl.M, pl.K,
-                                                                      a_row_fast, pa, Ap, ld);
+                                                                      Kb, a_row_fast, pa, Ap, ld);
         pack_pieces_kernel<uint16_t><<<blocks_for(pl.N), PT, 0, s>>>((const uint16_t *)Bb, colB, kB, pl.N, pl.K,
-                                                                      b_row_fast, pb, Bp, ld);
+                                                                      Kb, b_row_fast, pb, Bp, ld);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -175,6 +180,19 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
     p.M = pl.M;
     p.N = pl.N;
     p.K = Kp;
+    // one accumulation chunk per piece block (at most 1024 K): every piece
+    // product is summed in its own accumulator and the chunk sums are added
+    // in registers
+    {
+        const int64_t tiles = Kb / 64;
+        int kc = 1;
+        for (int d = 16; d >= 1; --d)
+            if (tiles % d == 0) {
+                kc = d;
+                break;
+            }
+        p.kc_tiles = kc;
+    }
     p.err = err;
     p.C = Cb;
     p.rowC = rowC;

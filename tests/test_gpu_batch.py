@@ -1,0 +1,122 @@
+"""GPU parity of the batched persistent launch: every problem's C against the
+oracle (fp32 arithmetic: element bound 2 (K+2) 2^-24 (|C0| + sum |A||B|)),
+plain and graph launches, every tile configuration, alias rejection."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_06770_gb300 import batch as gb
+from paper_2410_06770_gb300 import gett, synth
+from tests._gpu_util import abs_bound, download, problem_for, upload
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch_problems(n, seed, max_ext=12, pad_frac=0.25):
+    rng = np.random.default_rng(seed)
+    probs = []
+    for i in range(n):
+        k = int(rng.integers(0, 4))
+        ra = int(rng.integers(max(2, k), 6))
+        rb = int(rng.integers(max(2, k), 6))
+        sig = synth.random_signature(rng, rank_a=ra, rank_b=rb, conts=k, min_ext=2, max_ext=max_ext,
+                                     max_elems=1 << 16)
+        kinds = ("padded",) * 3 if rng.random() < pad_frac else ("contig",) * 3
+        p = synth.make_problem(sig, rng, np.float64, "uniform", kinds, "uniform")
+        prefix = "sb" if rng.integers(0, 2) else "s"
+        probs.append((prefix, problem_for(prefix, p)))
+    return probs
+
+
+def upload_all(probs):
+    dev = []
+    descs = []
+    for prefix, q in probs:
+        dA, dB, dC = upload(q.A), upload(q.B), upload(q.C)
+        dev.append((dA, dB, dC))
+        a = q.args()
+        descs.append(dict(dtype="bf16" if prefix == "sb" else "f32",
+                          EXTA=a["EXTA"], INCA=a["INCA"], EXTB=a["EXTB"], INCB=a["INCB"],
+                          CONTA=a["CONTA"], CONTB=a["CONTB"], PERM=a["PERM"], INCC=a["INCC"],
+                          A=dA.data_ptr() + q.la.off * dA.element_size(),
+                          B=dB.data_ptr() + q.lb.off * dB.element_size(),
+                          C=dC.data_ptr() + q.lc.off * dC.element_size()))
+    return dev, descs
+
+
+def check_all(probs, dev, times=1):
+    for (prefix, q), (_, _, dC) in zip(probs, dev):
+        got = download(dC, np.float32)
+        ref = oracle.widen(q.C).copy()
+        for _ in range(times):
+            ref = oracle.gett_problem(q, C=ref)
+        gaps = synth.gap_mask(q.lc)
+        assert np.array_equal(got[gaps], q.C[gaps])
+        g = synth.gather(q.lc, got).astype(np.float64)
+        r = synth.gather(q.lc, ref)
+        K = max(1, int(np.prod([q.sig.exta[m] for m in q.sig.conta], dtype=np.int64)))
+        bound = abs_bound(q) * times
+        assert np.all(np.abs(g - r) <= 2.0 * (K + 2) * times * 2.0 ** -24 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("select,config", [("heuristic", 0), ("fixed", 0), ("fixed", 1), ("fixed", 2), ("fixed", 3)])
+def test_batch_matches_oracle(select, config):
+    import torch
+    probs = make_batch_problems(150, 1 + config)
+    dev, descs = upload_all(probs)
+    b = gb.Batch(descs, select=select, config=config)
+    info = b.info()
+    assert info["n"] == 150 and info["tiles"] > 0
+    b.launch()
+    torch.cuda.synchronize()
+    check_all(probs, dev)
+    b.close()
+
+
+def test_batch_graph_replay_accumulates():
+    import torch
+    probs = make_batch_problems(100, 7)
+    dev, descs = upload_all(probs)
+    b = gb.Batch(descs)
+    b.launch(graph=True)
+    b.launch(graph=True)
+    torch.cuda.synchronize()
+    check_all(probs, dev, times=2)
+
+
+def test_batch_deterministic():
+    import torch
+    probs = make_batch_problems(80, 9)
+    outs = []
+    for _ in range(2):
+        dev, descs = upload_all(probs)
+        b = gb.Batch(descs)
+        b.launch()
+        torch.cuda.synchronize()
+        outs.append([download(dC, np.float32).copy() for (_, _, dC) in dev])
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
+
+
+def test_batch_rejects_overlapping_outputs():
+    import torch
+    probs = make_batch_problems(2, 11)
+    dev, descs = upload_all(probs)
+    descs[1]["C"] = descs[0]["C"]
+    with pytest.raises(gett.GettError) as ei:
+        gb.Batch(descs)
+    assert ei.value.status == gett.GETT_ERR_ALIAS
+
+
+def test_batch_table_selection_and_learned_fallback():
+    import torch
+    probs = make_batch_problems(60, 13)
+    dev, descs = upload_all(probs)
+    gb.clear_model()
+    b = gb.Batch(descs, select="learned")
+    assert b.info()["fallbacks"] == b.info()["nonempty"]  # no model: heuristic everywhere
+    cfgs = [i % gb.num_configs() for i in range(60)]
+    b2 = gb.Batch(descs, select="table", configs=cfgs)
+    b2.launch()
+    torch.cuda.synchronize()
+    check_all(probs, dev)

@@ -1,0 +1,71 @@
+"""GPU checks of the planner network's own kernels against the fp64 CPU
+reference: forward outputs, loss and every gradient (<= 1e-4 relative),
+training that lowers the loss, and installation as the batch planner."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle
+from paper_2410_06770_gb300 import batch as gb
+
+pytestmark = pytest.mark.gpu
+
+NF, H, NO = gb.NFEAT, 128, 4
+
+
+def data(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, NF)).astype(np.float32)
+    W = rng.standard_normal((NF, NO))
+    T = (np.tanh(X @ W) + 0.1 * rng.standard_normal((n, NO))).astype(np.float32)
+    M = (rng.random((n, NO)) < 0.9).astype(np.float32)
+    return X, T, M
+
+
+def test_forward_matches_reference():
+    m = gb.MLP(NF, H, NO, seed=1)
+    X, _, _ = data(64, 0)
+    y = m.predict(X)
+    ref, _ = mlp_oracle.forward(m.get_params(), X, NF, H, NO)
+    assert np.max(np.abs(y - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("n", [1, 37, 256])
+def test_gradients_match_reference(n):
+    m = gb.MLP(NF, H, NO, seed=2)
+    X, T, M = data(n, n)
+    loss, g = m.loss_grad(X, T, M)
+    rloss, rg = mlp_oracle.loss_grad(m.get_params(), X, T, M, NF, H, NO)
+    assert abs(loss - rloss) <= 1e-4 * max(1.0, abs(rloss))
+    assert np.linalg.norm(g - rg) <= 1e-4 * max(1e-6, np.linalg.norm(rg))
+    assert np.max(np.abs(g - rg)) <= 1e-4 * max(1e-6, np.max(np.abs(rg)))
+
+
+def test_training_reduces_loss_and_is_deterministic():
+    X, T, M = data(2000, 5)
+    losses = []
+    params = []
+    for _ in range(2):
+        m = gb.MLP(NF, H, NO, seed=3)
+        l0, _ = m.loss_grad(X[:512], T[:512], M[:512])
+        lf = m.fit(X, T, M, epochs=20, batch=128, lr=1e-3, seed=4)
+        losses.append((l0, lf))
+        params.append(m.get_params())
+    assert losses[0][1] < 0.5 * losses[0][0]
+    assert np.array_equal(params[0], params[1])
+
+
+def test_installed_model_drives_host_prediction():
+    m = gb.MLP(NF, H, NO, seed=6)
+    p = m.get_params()
+    mean = np.zeros(NF, dtype=np.float32)
+    std = np.ones(NF, dtype=np.float32)
+    gb.install_model(p, mean, std, H, NO)
+    X, _, _ = data(8, 1)
+    import ctypes
+    L = gb._bind()
+    ref, _ = mlp_oracle.forward(p, X, NF, H, NO)
+    for i in range(8):
+        out = np.zeros(NO, dtype=np.float32)
+        assert L.gett_learn_predict(gb._f(np.ascontiguousarray(X[i])), gb._f(out)) == 0
+        assert np.max(np.abs(out - ref[i])) <= 1e-4 * max(1.0, np.max(np.abs(ref[i])))
+    gb.clear_model()
