@@ -500,6 +500,49 @@ def cfg_stream(dtype=np.float64, a_ext=(256, 256, 64), b_ext=(64, 8), c_host=Tru
     return Problem(sig, la, lb, lc, A, B, np.zeros(1, dtype=dtype), "stream_outer", {"c_zero": True})
 
 
+def capped_signature(rng: np.random.Generator, ra: int, rb: int, k: int, min_ext: int, max_ext: int,
+                     cap: int) -> Signature:
+    """Random signature with ranks ra, rb and k contracted pairs, extents drawn
+    U{min_ext..max_ext}; while |A|, |B| or |C| exceeds `cap` elements, the
+    largest extent of the most oversized tensor is redrawn below its current
+    value (contracted extents stay paired), so the draw always terminates."""
+    exta = [int(rng.integers(min_ext, max_ext + 1)) for _ in range(ra)]
+    extb = [int(rng.integers(min_ext, max_ext + 1)) for _ in range(rb)]
+    conta = [int(x) for x in rng.choice(ra, size=k, replace=False)] if k else []
+    contb = [int(x) for x in rng.choice(rb, size=k, replace=False)] if k else []
+    for ma, mb in zip(conta, contb):
+        extb[mb] = exta[ma]
+    perm = [int(x) for x in rng.permutation(ra + rb - 2 * k)]
+    pair_b = dict(zip(conta, contb))
+    pair_a = dict(zip(contb, conta))
+    while True:
+        sig = Signature(tuple(exta), tuple(extb), tuple(conta), tuple(contb), tuple(perm))
+        sizes = [int(np.prod(exta, dtype=np.int64)), int(np.prod(extb, dtype=np.int64)),
+                 int(np.prod(sig.extc(), dtype=np.int64)) if sig.rank_c else 1]
+        worst = int(np.argmax(sizes))
+        if sizes[worst] <= cap:
+            return sig
+        if worst == 0:
+            modes = [(exta[m], 0, m) for m in range(ra)]
+        elif worst == 1:
+            modes = [(extb[m], 1, m) for m in range(rb)]
+        else:
+            modes = [(exta[m], 0, m) for m in range(ra) if m not in conta] + \
+                    [(extb[m], 1, m) for m in range(rb) if m not in contb]
+        e, t, m = max(modes)
+        if e <= min_ext:
+            return sig  # cannot shrink further
+        new = int(rng.integers(min_ext, e))
+        if t == 0:
+            exta[m] = new
+            if m in pair_b:
+                extb[pair_b[m]] = new
+        else:
+            extb[m] = new
+            if m in pair_a:
+                exta[pair_a[m]] = new
+
+
 def batched_signatures(n=4096, seed=7, min_ext=2, max_ext=64, cap=1 << 18,
                        pad_frac=0.25) -> List[dict]:
     """Signatures for the batched workload: CONTS ~ U{0..3}, each rank ~
@@ -513,17 +556,7 @@ def batched_signatures(n=4096, seed=7, min_ext=2, max_ext=64, cap=1 << 18,
         k = int(rng.integers(0, 4))
         ra = int(rng.integers(max(2, k), 6))
         rb = int(rng.integers(max(2, k), 6))
-        for _ in range(200):
-            try:
-                sig = random_signature(rng, rank_a=ra, rank_b=rb, conts=k, min_ext=min_ext,
-                                       max_ext=max_ext, max_elems=cap)
-                break
-            except RuntimeError:
-                sig = None
-        else:
-            sig = None
-        if sig is None:
-            continue
+        sig = capped_signature(rng, ra, rb, k, min_ext, max_ext, cap)
         padded = bool(rng.random() < pad_frac)
         dtype = "bf16" if rng.integers(0, 2) else "f32"
         pads = None

@@ -19,8 +19,7 @@ def make_batch_problems(n, seed, max_ext=12, pad_frac=0.25):
         k = int(rng.integers(0, 4))
         ra = int(rng.integers(max(2, k), 6))
         rb = int(rng.integers(max(2, k), 6))
-        sig = synth.random_signature(rng, rank_a=ra, rank_b=rb, conts=k, min_ext=2, max_ext=max_ext,
-                                     max_elems=1 << 16)
+        sig = synth.capped_signature(rng, ra, rb, k, 2, max_ext, 1 << 16)
         kinds = ("padded",) * 3 if rng.random() < pad_frac else ("contig",) * 3
         p = synth.make_problem(sig, rng, np.float64, "uniform", kinds, "uniform")
         prefix = "sb" if rng.integers(0, 2) else "s"
