@@ -6,10 +6,10 @@
  *
  *   C[o] <- C[o] + sum over contracted coordinates kappa of A[...] * B[...]
  *
- * (Sec. 2.2, the contraction equation; Sec. 5, Alg. 1 adds every product to
+ * (Sec. 2.2, the contraction equation; Sec. 6, Alg. 1 adds every product to
  * the value C already holds, so C is ACCUMULATED into, never overwritten).
  *
- * Argument order and meaning are those of the final interface (Sec. 4.7):
+ * Argument order and meaning are those of the final interface (Sec. 5.7):
  *
  *   xGETT(RANKA, EXTA, INCA, A,  RANKB, EXTB, INCB, B,
  *         CONTS, CONTA, CONTB, PERM,  INCC, C)
@@ -18,10 +18,10 @@
  *   EXTA, EXTB    extents, one per mode (>= 0).  Host arrays, read during
  *                 the call only; may be NULL when the rank is 0.
  *   INCA, INCB    increments in ELEMENTS (not bytes) between neighbours
- *                 along each mode; may be negative (Sec. 6, negative
+ *                 along each mode; may be negative (Sec. 7, negative
  *                 increment tests) or zero (broadcast).  Host arrays.
  *   A, B          DEVICE pointers to the element whose coordinates are all
- *                 zero (the "first used data point", Sec. 4.1); with a
+ *                 zero (the "first used data point", Sec. 5.1); with a
  *                 negative increment the other elements lie below it.
  *                 Read only; A and B may alias each other.
  *   CONTS         number of contracted mode pairs (0 <= CONTS <=
@@ -32,11 +32,11 @@
  *   PERM          length r_C = RANKA + RANKB - 2*CONTS.  The free indices
  *                 are A's non-contracted modes in ascending order followed
  *                 by B's; PERM[p] is the 0-based OUTPUT POSITION of free
- *                 index p (Sec. 4.6, the fourth encoding).  Must be a
+ *                 index p (Sec. 5.6, the fourth encoding).  Must be a
  *                 permutation of 0..r_C-1.  Host array.
  *   INCC          r_C increments of C in elements, indexed by output
- *                 position (the "array of two values" wording of Sec. 4.7 is
- *                 left over from the matrix stage; Sec. 4.4 generalises LD
+ *                 position (the "array of two values" wording of Sec. 5.7 is
+ *                 left over from the matrix stage; Sec. 5.4 generalises LD
  *                 to one increment per mode).  Host array.
  *   C             DEVICE pointer to C's coordinate-zero element; read and
  *                 written.  Elements outside the logical tensor (gaps of a
@@ -47,7 +47,7 @@
  * contracted extent adds an empty sum (C unchanged).
  *
  * Types: s = float, d = double, c = interleaved single complex, z =
- * interleaved double complex (Sec. 4, prefixes); complex products are not
+ * interleaved double complex (Sec. 5, prefixes); complex products are not
  * conjugated.  Extension: sbgett takes bfloat16 A and B and a float C.
  *
  * Errors.  Every entry point returns a gett_status.  GETT_ERR_ARG: an
@@ -95,7 +95,7 @@ typedef struct gett_complex_float { float re, im; } gett_complex_float;
 typedef struct gett_complex_double { double re, im; } gett_complex_double;
 
 /* ---------------------------------------------------------------------- */
-/* Plain xGETT (Sec. 4.7).  Synchronous.                                   */
+/* Plain xGETT (Sec. 5.7).  Synchronous.                                   */
 /* ---------------------------------------------------------------------- */
 int sgett(int RANKA, const int64_t *EXTA, const int64_t *INCA, const float *A,
           int RANKB, const int64_t *EXTB, const int64_t *INCB, const float *B,

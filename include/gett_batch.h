@@ -1,8 +1,8 @@
 /*
  * gett_batch.h -- many xGETT contractions in one persistent launch
- * (extension; the thesis defines single calls only, Sec. 4.7).
+ * (extension; the thesis defines single calls only, Sec. 5.7).
  *
- * Each problem is a full xGETT call (the 14 arguments of Sec. 4.7, same
+ * Each problem is a full xGETT call (the 14 arguments of Sec. 5.7, same
  * meaning as in gett.h) with float C and either float or bfloat16 A and B;
  * products are accumulated in float.  gett_batch_create validates and plans
  * every problem on the host, chooses a tile configuration per problem,

@@ -1,7 +1,7 @@
 /*
  * gett_learn.h -- the learned planner: a 3-layer MLP that maps a
  * contraction signature to predicted log run times of the batched kernel's
- * tile configurations (extension; the thesis has no planner, Sec. 5).
+ * tile configurations (extension; the thesis has no planner, Sec. 6).
  *
  * Features are computed from the planned problem (after squeezing, flips
  * and fusion): log2 of M, N, K and of the leading increments of A, B and C

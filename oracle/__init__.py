@@ -4,7 +4,7 @@ Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
 legs may import this package.  The CUDA library never calls it; the two share
 no code.
 
-`gett()` runs Alg. 1 of the thesis (Sec. 5) in plain C (gett_oracle.c) on
+`gett()` runs Alg. 1 of the thesis (Sec. 6) in plain C (gett_oracle.c) on
 numpy buffers.  Precisions:
   'f64'    -- products and sums in double, each product added to C in turn
               (exactly the loop of Alg. 1);

@@ -7,11 +7,11 @@
  * cpu_baseline / reference legs of bench.py may load this code.  The CUDA
  * library never calls it and shares no code, header or helper with it.
  *
- * What it computes (Sec. 2.2, the contraction equation; Sec. 5, Alg. 1):
+ * What it computes (Sec. 2.2, the contraction equation; Sec. 6, Alg. 1):
  *   for every output coordinate o:
  *     C[sum_q o_q INCC[q]] <- C[...] + sum_kappa A[...] * B[...]
  *   where the free modes are A's non-contracted modes in ascending order
- *   followed by B's (Sec. 4.6, option 4 of the PERM encodings), free index p
+ *   followed by B's (Sec. 5.6, option 4 of the PERM encodings), free index p
  *   is placed at output position PERM[p], and kappa runs over the contracted
  *   coordinates with the first contracted index fastest (Alg. 2).
  *
@@ -21,9 +21,9 @@
  * multiply-add is fused and the result is deterministic.
  *
  * Readings of the thesis taken here (all listed in the design notes):
- *  - PERM[p] is the OUTPUT POSITION of free index p (Sec. 4.6: "the integers
+ *  - PERM[p] is the OUTPUT POSITION of free index p (Sec. 5.6: "the integers
  *    written in each position ... represent the placement").
- *  - INCC has one entry per output mode (Sec. 4.4 generalises LD to INC; the
+ *  - INCC has one entry per output mode (Sec. 5.4 generalises LD to INC; the
  *    "array of two values" wording is left over from the matrix stage).
  *  - In Alg. 1 the contracted loop uses the contracted-mode increments
  *    IncContA/IncContB, and the two IncCoords calls take ExtContInd for the
@@ -37,7 +37,7 @@
  *
  * Parity pins: tests/test_oracle_pins.py (GEMM/GEMV/DOT/GER reductions against
  * numpy BLAS, integer-exact comparison with numpy.einsum, the coordinate
- * order printed in Sec. 5, the layout figures with increments [1,3,9] and
+ * order printed in Sec. 6, the layout figures with increments [1,3,9] and
  * [1,5,25], permutation/commutativity/stride invariance, brute force).
  */
 #include <stdint.h>
@@ -63,14 +63,14 @@ static void inc_coords(int num_of_ind, int64_t *coords, const int64_t *exts)
 }
 
 /* Exported so the tests can compare the visiting order with the sequence
- * printed in Sec. 5 ([0,0,0], [1,0,0], [2,0,0], [0,1,0], ...). */
+ * printed in Sec. 6 ([0,0,0], [1,0,0], [2,0,0], [0,1,0], ...). */
 void oracle_inc_coords(int num_of_ind, int64_t *coords, const int64_t *exts)
 {
     inc_coords(num_of_ind, coords, exts);
 }
 
 /* ---------------------------------------------------------------------- */
-/* Preprocessing of Sec. 5: the arrays Alg. 1 works on.                    */
+/* Preprocessing of Sec. 6: the arrays Alg. 1 works on.                    */
 /* ---------------------------------------------------------------------- */
 typedef struct {
     int num_free;          /* NumFreeInd  = RANKA + RANKB - 2*CONTS        */
@@ -128,7 +128,7 @@ static int prepare(prep_t *p,
         p->inc_cont_a[t] = INCA[ma];
         p->inc_cont_b[t] = INCB[mb];
     }
-    /* Free index p: A's free modes ascending, then B's (Sec. 4.6). */
+    /* Free index p: A's free modes ascending, then B's (Sec. 5.6). */
     int fp = 0;
     for (int tensor = 0; tensor < 2; ++tensor) {
         int rank = tensor == 0 ? RANKA : RANKB;

@@ -9,7 +9,7 @@
 
 namespace gett {
 
-// Interleaved complex values (Sec. 4: prefixes c and z).  Complex products
+// Interleaved complex values (Sec. 5: prefixes c and z).  Complex products
 // are not conjugated: (a + ib)(c + id) = (ac - bd) + i(ad + bc).
 struct cf {
     float re, im;

@@ -1,14 +1,14 @@
 // k_stream.cu -- HBM-streaming kernels for low-intensity contractions.
 //
 // OUTER: no contracted mode of extent > 1 (the thesis's "nothing
-// contraction", Sec. 6): C[m,n] += A[m] * B[n].  Every C element is read and
+// contraction", Sec. 7): C[m,n] += A[m] * B[n].  Every C element is read and
 // written once, so the kernel is bound by HBM bandwidth.  C is walked along
 // its smallest-increment mode (the first mode of whichever class holds it),
 // in runs of that mode; the operand that varies along the run is read along
 // the same index, the other operand is one value per run.
 //
 // REDUCE: few output elements and long sums (the "scalar contraction" of
-// Sec. 6 and its neighbours).  Pass 1 splits the flat contracted index
+// Sec. 7 and its neighbours).  Pass 1 splits the flat contracted index
 // space into a fixed number of contiguous ranges, one per CTA, and sums each
 // range with a fixed per-thread stride, warp shuffles and a fixed cross-warp
 // order; pass 2 adds the per-CTA partials in CTA order and accumulates into

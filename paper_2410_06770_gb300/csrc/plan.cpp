@@ -1,8 +1,8 @@
 // plan.cpp -- argument validation and the mode-classification planner.
 //
-// Validation follows the interface of Sec. 4.7: ranks, extents, increments,
+// Validation follows the interface of Sec. 5.7: ranks, extents, increments,
 // the contracted pairs CONTA/CONTB (distinct, in range, equal extents, Sec.
-// 4.5), PERM a permutation of the r_C output positions (Sec. 4.6), one INCC
+// 4.5), PERM a permutation of the r_C output positions (Sec. 5.6), one INCC
 // entry per output mode.
 //
 // The planner turns the 14 arguments into three mode classes -- A-free modes
@@ -155,7 +155,7 @@ int make_plan(const Args &a, Plan *p, int *bad_arg)
     if (rc > 0 && !a.INCC) BAD(13);
 #undef BAD
 
-    // Classify (free index p = A's free modes ascending, then B's; Sec. 4.6).
+    // Classify (free index p = A's free modes ascending, then B's; Sec. 5.6).
     Mode mm[GETT_MAX_RANK], nn[GETT_MAX_RANK], kk[GETT_MAX_RANK];
     int nm = 0, nn_ = 0, nk = 0, fp = 0;
     int64_t extc[2 * GETT_MAX_RANK];

@@ -5,7 +5,7 @@ This module holds no contraction arithmetic.  It only decides shapes,
 increments, buffer offsets and the values stored in buffers, so both the CUDA
 path and the CPU oracle can be fed the same inputs.
 
-Conventions (thesis Sec. 4.4-4.7 and Sec. 5):
+Conventions (thesis Sec. 5.4-5.7 and Sec. 6):
   * column-major, element-unit increments (the layout figures with increments
     [1, 3, 9] for a rank-3 tensor and [1, 5, 25] for a sub-tensor of a 5x5x5
     parent);
@@ -13,10 +13,10 @@ Conventions (thesis Sec. 4.4-4.7 and Sec. 5):
     negative increment the other elements sit at lower addresses, so such a
     tensor's coordinate-zero element has a positive offset into its buffer;
   * PERM[p] is the output position of free index p, where free indices are A's
-    non-contracted modes in ascending order followed by B's (Sec. 4.6).
+    non-contracted modes in ascending order followed by B's (Sec. 5.6).
 
 Random contraction generation follows the parameters the thesis lists for its
-generator (Sec. 6): minimum/maximum rank, minimum/maximum extent and the number
+generator (Sec. 7): minimum/maximum rank, minimum/maximum extent and the number
 of contracted modes; it always produces a valid contraction.
 """
 from __future__ import annotations
@@ -101,8 +101,8 @@ def layout_explicit(ext: Sequence[int], inc: Sequence[int]) -> Layout:
 def layout_padded(ext: Sequence[int], rng: np.random.Generator, pad_lo=1, pad_hi=5,
                   negative: bool = False) -> Layout:
     """Sub-tensor of the same rank, randomly placed in a parent whose extents are
-    pad_lo..pad_hi larger (thesis Sec. 6, "sub-tensor of same rank"); with
-    negative=True every increment is negated (Sec. 6, "sub-tensor negative
+    pad_lo..pad_hi larger (thesis Sec. 7, "sub-tensor of same rank"); with
+    negative=True every increment is negated (Sec. 7, "sub-tensor negative
     increment")."""
     ext = tuple(int(e) for e in ext)
     pads = [int(rng.integers(pad_lo, pad_hi + 1)) for _ in ext]
@@ -122,7 +122,7 @@ def layout_padded(ext: Sequence[int], rng: np.random.Generator, pad_lo=1, pad_hi
 
 
 def layout_negative(ext: Sequence[int]) -> Layout:
-    """Dense tensor read backwards in memory (thesis Sec. 6, "negative increment")."""
+    """Dense tensor read backwards in memory (thesis Sec. 7, "negative increment")."""
     ext = tuple(int(e) for e in ext)
     strides = colmajor_strides(ext)
     n = 1
@@ -134,7 +134,7 @@ def layout_negative(ext: Sequence[int]) -> Layout:
 
 def layout_lower_rank(ext: Sequence[int], rng: np.random.Generator) -> Layout:
     """Sub-tensor of a parent whose rank is 1..3 higher and whose extents are
-    1..3 larger (thesis Sec. 6, "sub-tensor of lower rank")."""
+    1..3 larger (thesis Sec. 7, "sub-tensor of lower rank")."""
     ext = tuple(int(e) for e in ext)
     extra = int(rng.integers(1, 4))
     prank = len(ext) + extra
@@ -210,7 +210,7 @@ def random_signature(rng: np.random.Generator, min_rank=1, max_rank=5, min_ext=1
                      conts: Optional[int] = None, min_conts=0, max_conts=4,
                      rank_a: Optional[int] = None, rank_b: Optional[int] = None,
                      equal_ext: Optional[int] = None, max_elems: Optional[int] = None) -> Signature:
-    """Random valid contraction (thesis Sec. 6 generator parameters)."""
+    """Random valid contraction (thesis Sec. 7 generator parameters)."""
     for _ in range(1000):
         ra = rank_a if rank_a is not None else int(rng.integers(min_rank, max_rank + 1))
         rb = rank_b if rank_b is not None else int(rng.integers(min_rank, max_rank + 1))
@@ -370,7 +370,7 @@ def make_problem(sig: Signature, rng: np.random.Generator, dtype=np.float64, dis
 
 
 # --------------------------------------------------------------------------
-# Thesis test families (Sec. 6).  Each returns a Problem; `dist` and `dtype`
+# Thesis test families (Sec. 7).  Each returns a Problem; `dist` and `dtype`
 # select the value distribution.
 # --------------------------------------------------------------------------
 THESIS_TESTS = (
@@ -425,7 +425,7 @@ def thesis_problem(name: str, seed: int, dtype=np.float64, dist="uniform", c_dis
 
 def swapped(p: Problem) -> Problem:
     """Same inputs with A and B exchanged and PERM rotated so the output layout
-    is unchanged (thesis Sec. 6, "commutativity")."""
+    is unchanged (thesis Sec. 7, "commutativity")."""
     s = p.sig
     na = len(s.exta) - s.conts
     nb = len(s.extb) - s.conts
@@ -436,7 +436,7 @@ def swapped(p: Problem) -> Problem:
 
 
 def rotated_output(p: Problem, n: int, rng: np.random.Generator) -> Problem:
-    """PERM shifted left n times (thesis Sec. 6, "permutations"): each free index
+    """PERM shifted left n times (thesis Sec. 7, "permutations"): each free index
     moves to a new output position; C gets a fresh contiguous layout for the new
     extents."""
     s = p.sig

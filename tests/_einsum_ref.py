@@ -1,6 +1,6 @@
 """Independent references for the oracle pins: numpy.einsum / BLAS on the
 logical tensors, written from the contraction's definition (thesis Sec. 2.2)
-and the PERM encoding (Sec. 4.6), not from the oracle's code."""
+and the PERM encoding (Sec. 5.6), not from the oracle's code."""
 import string
 
 import numpy as np

@@ -1,5 +1,5 @@
 """CPU-only checks of the C-ABI library: it loads, exports every symbol the
-public header declares, validates arguments (Sec. 4.7 rules) and plans
+public header declares, validates arguments (Sec. 5.7 rules) and plans
 correctly.  No device work is started: every call here fails validation or is
 the host-only planner."""
 import os

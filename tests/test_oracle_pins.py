@@ -2,7 +2,7 @@
 
 Each test names the passage it checks.  None of them compares the oracle with
 itself re-typed: the references are numpy BLAS / einsum on logical tensors,
-exact rational arithmetic, the coordinate order printed in Sec. 5 and the
+exact rational arithmetic, the coordinate order printed in Sec. 6 and the
 layout figures' increments.
 """
 import math
@@ -36,10 +36,10 @@ def run(p, precision="f64", nthreads=1):
 
 
 # --------------------------------------------------------------------------
-# Alg. 2 and the Sec. 5 figures
+# Alg. 2 and the Sec. 6 figures
 # --------------------------------------------------------------------------
 def test_inccoords_prints_paper_sequence():
-    """Sec. 5: IncCoords visits [0,0,0], [1,0,0], [2,0,0], [0,1,0], [1,1,0],
+    """Sec. 6: IncCoords visits [0,0,0], [1,0,0], [2,0,0], [0,1,0], [1,1,0],
     [2,1,0], ... for extents (3,3,3)."""
     want = _golden_numbers("inccoords_rank3.txt")
     c = [0, 0, 0]
@@ -69,7 +69,7 @@ def test_inccoords_full_cycle_and_rank0():
     ("layout_subtensor_inc_1_5_25.txt", 125, (1, 5, 25)),
 ])
 def test_layout_figures(fixture, parent, inc):
-    """Sec. 5 figures: a (3,3,3) tensor with increments [1,3,9] and a (3,3,3)
+    """Sec. 6 figures: a (3,3,3) tensor with increments [1,3,9] and a (3,3,3)
     sub-tensor with increments [1,5,25].  Contracting with the rank-0 tensor 1
     (CONTS=0) copies A into a contiguous C, so C lists A's memory index of each
     coordinate in IncCoords order."""
@@ -156,7 +156,7 @@ def test_ger_is_bit_exact(perm):
 
 
 # --------------------------------------------------------------------------
-# Integer-exact comparison with einsum over all thesis test families (Sec. 6)
+# Integer-exact comparison with einsum over all thesis test families (Sec. 7)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("family", synth.THESIS_TESTS)
 @pytest.mark.parametrize("seed", range(6))
@@ -176,7 +176,7 @@ def test_integer_exact_vs_einsum(family, seed):
 
 @pytest.mark.parametrize("seed", range(8))
 def test_complex_integer_exact_vs_einsum(seed):
-    """Complex double, no conjugation (Sec. 4 prefix z)."""
+    """Complex double, no conjugation (Sec. 5 prefix z)."""
     p = synth.thesis_problem("basic", 2000 + seed, np.complex128, "int", c_dist="int")
     ref = einsum_logical(p, np.complex128)
     got = synth.logical(p.lc, oracle.gett_problem(p, "z"))
@@ -193,7 +193,7 @@ def test_complex_no_conjugation():
 
 
 # --------------------------------------------------------------------------
-# Bit-identity invariants of the oracle (Sec. 6 permutation / commutativity /
+# Bit-identity invariants of the oracle (Sec. 7 permutation / commutativity /
 # sub-tensor tests): the contracted summation order does not depend on PERM,
 # operand order or layout.
 # --------------------------------------------------------------------------
@@ -310,7 +310,7 @@ def test_summation_order_first_contracted_index_fastest():
 # Special cases
 # --------------------------------------------------------------------------
 def test_rank_zero_operand_scales_elementwise():
-    """Sec. 6 "rank zero tensor": C = C0 + s*B, one rounding per element."""
+    """Sec. 7 "rank zero tensor": C = C0 + s*B, one rounding per element."""
     rng = np.random.default_rng(9)
     sig = synth.Signature((), (3, 4, 2), (), (), (2, 0, 1))
     p = synth.make_problem(sig, rng, np.float64, "uniform", ("contig", "padded", "padded"), "uniform")
@@ -321,7 +321,7 @@ def test_rank_zero_operand_scales_elementwise():
 
 
 def test_scalar_output_vs_fsum():
-    """Sec. 6 "scalar contraction": every mode contracted gives a rank-0 C."""
+    """Sec. 7 "scalar contraction": every mode contracted gives a rank-0 C."""
     rng = np.random.default_rng(10)
     sig = synth.Signature((3, 4, 5), (5, 3, 4), (0, 1, 2), (1, 2, 0), ())
     p = synth.make_problem(sig, rng, np.float64, "uniform")
