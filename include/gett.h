@@ -216,6 +216,32 @@ int sbgett_ex(int RANKA, const int64_t *EXTA, const int64_t *INCA, const uint16_
               const gett_options *opt, gett_report *rep, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Allocation-free double-precision form.  The thesis has no counterpart;  */
+/* this entry point exists for callers that must not allocate device       */
+/* memory while they run (a process that budgets all device memory up     */
+/* front, a latency-critical loop that cannot afford cudaFree's implicit   */
+/* device-wide synchronisation, a framework whose own allocator owns the   */
+/* device).  Same 14 arguments and semantics as dgett, stream-ordered on   */
+/* `stream` like dgett_async, computed by the dense CUDA-core kernel.  Its */
+/* scratch (16 * (M + N + K) bytes of offset tables, M, N, K = products of */
+/* the free-A, free-B and contracted extents) lives in one fixed 4 MiB     */
+/* device array of the library that every GPU loading the library holds    */
+/* until the process exits; problems with M + N + K greater than           */
+/* GETT_NOALLOC_MAX_INDEX_SUM are rejected with GETT_ERR_UNSUPPORTED and   */
+/* nothing is launched.  It calls no cudaMalloc or cudaFree.  The first    */
+/* call on a device (with that device current) looks up the array's device */
+/* address with cudaGetSymbolAddress; make that first call before any      */
+/* stream capture.  All calls share the array (it keeps the last call's    */
+/* contents, none of which needs to start at zero): calls whose work       */
+/* overlaps on the GPU race and must be ordered by the caller.             */
+/* ---------------------------------------------------------------------- */
+#define GETT_NOALLOC_MAX_INDEX_SUM 262144
+int dgett_noalloc(int RANKA, const int64_t *EXTA, const int64_t *INCA, const double *A,
+                  int RANKB, const int64_t *EXTB, const int64_t *INCB, const double *B,
+                  int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                  const int64_t *INCC, double *C, void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Planner inspection (host only, no device work).  Validates the 14       */
 /* arguments (pointers are not inspected) and describes the canonical      */
 /* problem: modes of each class after dropping extent-1 modes, flipping    */
