@@ -363,6 +363,7 @@ def gpu_arm(args, dist: Dist):
         del dA, dB, dC
         torch.cuda.empty_cache()
         result["forms"] = measure_forms(args.workload)
+        result["forms"].update(measure_split_forms())
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         v, cores, desc, dt = oracle_sample(p, args.cpu_seconds)
         result["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
@@ -440,6 +441,96 @@ def e2e_measure(p, flops, call_host, dA, dB, dC, a, stream, steps):
     bo = hOut.numel() * 8
     return {"value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": bi,
             "d2h_bytes_per_step": bo, "ms_per_step": ms, "steps": steps}
+
+
+def time_calls(call, reps, warm=2):
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        call()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return min(times), statistics.median(times)
+
+
+def measure_split_forms():
+    """Split-precision DGETT on the CC workload (sampled parity) and every
+    precision form on the small workload with log-uniform magnitudes (full
+    comparison with the long-double oracle)."""
+    import torch
+    import oracle
+    from paper_2410_06770_gb300 import gett, synth
+    out = {}
+    mp = measured_peaks()
+    bf16_peak = mp.get("bf16_tflops", 1900.0)
+    # CC at full size
+    p, desc = workload("cc")
+    a = p.args()
+    dA = torch.from_numpy(p.A).cuda()
+    dB = torch.from_numpy(p.B).cuda()
+    dC = torch.from_numpy(p.C).cuda()
+    stream = torch.cuda.current_stream()
+    opts = gett.options(algo="ozaki_bf16")
+
+    def call():
+        return gett.xgett("d", a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"], a["INCB"], dB,
+                          a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], dC,
+                          a_off=p.la.off, b_off=p.lb.off, c_off=p.lc.off, mode="ex", opts=opts,
+                          stream=stream.cuda_stream)
+    _, rep = call()
+    torch.cuda.synchronize()
+    parity = sampled_parity(p, dC.cpu().numpy(), nsamples=128)
+    best, med = time_calls(call, 5)
+    f = flops_of(p)
+    L = rep["moduli"]
+    out["cc_split_fp64"] = {
+        "workload": desc, "algo": "ozaki_bf16 (modular, bf16 tcgen05)", "moduli": L,
+        "ms": best, "ms_median": med, "tflops_effective": f / (best * 1e-3) / 1e12,
+        "slice_tflops": L * f / (best * 1e-3) / 1e12, "slice_frac_of_bf16_peak": L * f / (best * 1e-3) / 1e12 / bf16_peak,
+        "parity": parity}
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+    # small workload, log-uniform magnitudes: every form vs the long-double oracle
+    ps = synth.cfg_small_dgett(dist="logu")
+    ref = synth.gather(ps.lc, oracle.gett_problem(ps, "ld", nthreads=os.cpu_count() or 1))
+    forms = {}
+    for prefix, algo in (("d", "native"), ("d", "ozaki_bf16"), ("s", "native"), ("s", "bf16x3"), ("s", "bf16x6")):
+        q = ps.copy()
+        if prefix == "s":
+            q.A = ps.A.astype(np.float32)
+            q.B = ps.B.astype(np.float32)
+            q.C = ps.C.astype(np.float32)
+            refq = synth.gather(q.lc, oracle.gett_problem(q, "ld"))
+        else:
+            refq = ref
+        a = q.args()
+        dA, dB = torch.from_numpy(q.A).cuda(), torch.from_numpy(q.B).cuda()
+        dC = torch.from_numpy(q.C).cuda()
+        o = gett.options(algo=algo)
+
+        def c2():
+            return gett.xgett(prefix, a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"], a["INCB"], dB,
+                              a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], dC,
+                              a_off=q.la.off, b_off=q.lb.off, c_off=q.lc.off, mode="ex", opts=o,
+                              stream=stream.cuda_stream)
+        c2()
+        torch.cuda.synchronize()
+        got = synth.gather(q.lc, dC.cpu().numpy()).astype(np.float64)
+        err = float(np.linalg.norm(got - refq) / np.linalg.norm(refq))
+        dC.copy_(torch.from_numpy(q.C))
+        best, _ = time_calls(c2, 20)
+        forms[f"{prefix}gett/{algo}"] = {"normwise_err_vs_long_double": err, "ms": best,
+                                         "tflops": flops_of(q) / (best * 1e-3) / 1e12}
+    out["small_logu_forms"] = {"workload": "dgett_small shapes, 10^U(-8,8) magnitudes, random signs",
+                               "forms": forms}
+    return out
 
 
 def measure_forms(main_workload):
