@@ -364,6 +364,7 @@ def gpu_arm(args, dist: Dist):
         torch.cuda.empty_cache()
         result["forms"] = measure_forms(args.workload)
         result["forms"].update(measure_split_forms())
+        result["forms"]["batched"] = measure_batched()
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         v, cores, desc, dt = oracle_sample(p, args.cpu_seconds)
         result["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
@@ -530,6 +531,79 @@ def measure_split_forms():
                                          "tflops": flops_of(q) / (best * 1e-3) / 1e12}
     out["small_logu_forms"] = {"workload": "dgett_small shapes, 10^U(-8,8) magnitudes, random signs",
                                "forms": forms}
+    return out
+
+
+MODEL_PATH = os.path.join(ROOT, "paper_2410_06770_gb300", "models", "planner_mlp.npz")
+
+
+def measure_batched(n=4096):
+    """The batched workload: one persistent launch (CUDA graph replay) for all
+    contractions vs one plain call per contraction, with heuristic, tuned and
+    (if a trained model is committed) learned tile configurations."""
+    import torch
+    import oracle
+    from paper_2410_06770_gb300 import batch as gb
+    from paper_2410_06770_gb300 import gett, synth, tune
+    probs = tune.draw_problems(n, 7, 64)
+    total_flops = sum(tune.flops(p) for p in probs)
+    bufs = tune.DeviceBuffers(probs, values=True)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{n} contractions, seed 7, ranks 2-5, extents 2-64 (<= 2^18 elements), "
+                       "0-3 contracted, 25% padded, fp32/bf16 operands, fp32 C",
+           "gflop": total_flops / 1e9}
+
+    def per_call():
+        for pr, d in zip(probs, bufs.descs):
+            a = tune.args_of(pr)
+            gett.xgett("sb" if pr["dtype"] == "bf16" else "s", len(a["EXTA"]), a["EXTA"], a["INCA"], d["A"],
+                       len(a["EXTB"]), a["EXTB"], a["INCB"], d["B"], len(a["CONTA"]), a["CONTA"], a["CONTB"],
+                       a["PERM"], a["INCC"], d["C"], mode="async", stream=stream.cuda_stream)
+    per_call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    per_call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0))
+    out["per_call"] = {"ms": ms, "contractions_per_s": n / (ms * 1e-3), "tflops": total_flops / (ms * 1e-3) / 1e12}
+    # parity of one batched launch on fresh C for a sample of problems
+    sample = list(range(0, n, max(1, n // 64)))
+    for i in sample:
+        bufs.keep[i][2].zero_()
+    b = gb.Batch(bufs.descs)
+    b.launch(stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for i in sample:
+        pr = probs[i]
+        rng = np.random.default_rng(pr["seed"])
+        A = synth.fill(pr["la"], rng.uniform(-1, 1, pr["la"].numel), np.float32, 0.0)
+        B = synth.fill(pr["lb"], rng.uniform(-1, 1, pr["lb"].numel), np.float32, 0.0)
+        if pr["dtype"] == "bf16":
+            A = torch.from_numpy(A).to(torch.bfloat16).float().numpy()
+            B = torch.from_numpy(B).to(torch.bfloat16).float().numpy()
+        C = np.zeros(pr["lc"].size)
+        q = synth.Problem(pr["sig"], pr["la"], pr["lb"], pr["lc"], A.astype(np.float64), B.astype(np.float64), C)
+        ref = synth.gather(pr["lc"], oracle.gett_problem(q))
+        got = synth.gather(pr["lc"], bufs.keep[i][2].cpu().numpy()).astype(np.float64)
+        nr = np.linalg.norm(ref)
+        worst = max(worst, float(np.linalg.norm(got - ref) / (nr if nr else 1.0)))
+    out["parity"] = {"problems_checked": len(sample), "max_normwise_err": worst, "against": "oracle (fp64)"}
+    b.close()
+    del bufs
+    torch.cuda.empty_cache()
+    out["batched_heuristic"] = tune.throughput(probs, "heuristic")
+    T = tune.measure(probs, reps=2)
+    tuned = list(T.argmin(axis=1))
+    out["batched_tuned"] = tune.throughput(probs, "table", configs=tuned)
+    if os.path.exists(MODEL_PATH):
+        tune.install(tune.load_model(MODEL_PATH))
+        out["batched_learned"] = tune.throughput(probs, "learned")
+        gb.clear_model()
+    out["speedup_batched_vs_per_call"] = out["per_call"]["ms"] / out["batched_heuristic"]["ms"]
     return out
 
 

@@ -74,6 +74,13 @@ typedef struct gett_batch_info {
 int gett_batch_num_configs(void);
 int gett_batch_config_shape(int config, int *bm, int *bn);
 
+/* The fixed heuristic's tile configuration for one problem (14 xGETT
+ * arguments without pointers) -- the fallback of the other selectors. */
+int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const int64_t *INCA,
+                                int RANKB, const int64_t *EXTB, const int64_t *INCB,
+                                int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                                const int64_t *INCC, int *config);
+
 /* Returns GETT_OK or the first failing problem's status; *bad_index (may be
  * NULL) receives that problem's index and gett_last_error_arg() its
  * argument position. */
@@ -82,6 +89,12 @@ int gett_batch_create(int n, const gett_problem_desc *probs, const gett_batch_op
 int gett_batch_launch(gett_batch *b, void *stream);
 int gett_batch_launch_graph(gett_batch *b, void *stream);
 int gett_batch_get_info(const gett_batch *b, gett_batch_info *info);
+/* Autotuner measurement: times every problem of the batch alone (its own
+ * tiles, `reps` back-to-back launches of the persistent kernel between two
+ * CUDA events on an internal stream) and writes the mean milliseconds per
+ * launch to ms_out[i] (0 for problems with nothing to compute).
+ * Synchronous; the problems' C buffers are updated reps times each. */
+int gett_batch_profile(gett_batch *b, int reps, float *ms_out);
 int gett_batch_destroy(gett_batch *b);
 
 #ifdef __cplusplus

@@ -50,7 +50,11 @@ def _bind():
         getattr(L, n).restype = ctypes.c_int
     L.gett_batch_get_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(BatchInfo)]
     L.gett_batch_destroy.argtypes = [ctypes.c_void_p]
+    L.gett_batch_profile.argtypes = [ctypes.c_void_p, ctypes.c_int, _fp]
+    L.gett_batch_profile.restype = ctypes.c_int
     L.gett_batch_num_configs.restype = ctypes.c_int
+    L.gett_batch_heuristic_config.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
+                                              ctypes.c_int, _ip, _ip, _ip, _i64p, _ip]
     L.gett_batch_config_shape.argtypes = [ctypes.c_int, _ip, _ip]
     L.gett_problem_features.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
                                         ctypes.c_int, _ip, _ip, _ip, _i64p, ctypes.c_int, _fp]
@@ -113,11 +117,18 @@ class Batch:
         if st != 0:
             raise gett.GettError(st, f"gett_batch_create failed at problem {bad.value}", L.gett_last_error_arg())
         self.h = h
+        self.n = n
 
     def launch(self, stream=0, graph=False):
         L = _bind()
         fn = L.gett_batch_launch_graph if graph else L.gett_batch_launch
         gett.check(fn(self.h, ctypes.c_void_p(int(stream or 0))))
+
+    def profile(self, reps=3) -> np.ndarray:
+        """Mean ms per launch of each problem run alone (0 for empty ones)."""
+        out = np.zeros(max(self.n, 1), dtype=np.float32)
+        gett.check(_bind().gett_batch_profile(self.h, int(reps), _f(out)))
+        return out[: self.n]
 
     def info(self) -> dict:
         L = _bind()
@@ -140,6 +151,16 @@ class Batch:
 
 def num_configs() -> int:
     return _bind().gett_batch_num_configs()
+
+
+def heuristic_config(args: dict) -> int:
+    L = _bind()
+    c = ctypes.c_int(0)
+    gett.check(L.gett_batch_heuristic_config(len(args["EXTA"]), gett._i64(args["EXTA"]), gett._i64(args["INCA"]),
+                                             len(args["EXTB"]), gett._i64(args["EXTB"]), gett._i64(args["INCB"]),
+                                             len(args["CONTA"]), gett._i32(args["CONTA"]), gett._i32(args["CONTB"]),
+                                             gett._i32(args["PERM"]), gett._i64(args["INCC"]), ctypes.byref(c)))
+    return c.value
 
 
 def features(args: dict, dtype) -> np.ndarray:

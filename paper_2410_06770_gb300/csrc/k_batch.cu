@@ -168,6 +168,8 @@ struct gett_batch {
     uint2 *d_work = nullptr;
     int64_t *d_tables = nullptr;
     unsigned long long *d_counter = nullptr;
+    uint2 *d_work_by_problem = nullptr;  // work items grouped by problem
+    std::vector<int64_t> prob_start, prob_count;  // per user index (count 0: empty)
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap = nullptr;
@@ -182,6 +184,21 @@ extern "C" int gett_batch_config_shape(int config, int *bm, int *bn)
     if (config < 0 || config >= NCFG) return GETT_ERR_ARG;
     if (bm) *bm = kB[config].bm;
     if (bn) *bn = kB[config].bn;
+    return GETT_OK;
+}
+
+extern "C" int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const int64_t *INCA, int RANKB,
+                                           const int64_t *EXTB, const int64_t *INCB, int CONTS, const int *CONTA,
+                                           const int *CONTB, const int *PERM, const int64_t *INCC, int *config)
+{
+    if (!config) return GETT_ERR_ARG;
+    Args a{RANKA, EXTA, INCA, RANKB, EXTB, INCB, CONTS, CONTA, CONTB, PERM, INCC};
+    Plan p;
+    int bad = 0;
+    int rc = make_plan(a, &p, &bad);
+    set_last_error_arg(bad);
+    if (rc != GETT_OK) return rc;
+    *config = p.empty ? 0 : batch_heuristic_config(p.M, p.N, p.K);
     return GETT_OK;
 }
 
@@ -308,6 +325,17 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
             cost.push_back((double)kB[pr.cfg].bm * kB[pr.cfg].bn * (double)p.K);
         }
     }
+    b->prob_start.assign(n, 0);
+    b->prob_count.assign(n, 0);
+    {
+        int64_t pos = 0;
+        for (size_t j = 0; j < hp.size(); ++j) {
+            const int nt = hp[j].tiles_m * hp[j].tiles_n;
+            b->prob_start[hp_index[j]] = pos;
+            b->prob_count[hp_index[j]] = nt;
+            pos += nt;
+        }
+    }
     // longest tiles first
     std::vector<size_t> order(work.size());
     std::iota(order.begin(), order.end(), 0);
@@ -324,6 +352,9 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
     if (e == cudaSuccess) e = cudaMalloc(&b->d_work, sizeof(uint2) * std::max<size_t>(sorted.size(), 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tables, sizeof(int64_t) * tables.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_work_by_problem, sizeof(uint2) * std::max<size_t>(work.size(), 1));
+    if (e == cudaSuccess && !work.empty())
+        e = cudaMemcpy(b->d_work_by_problem, work.data(), sizeof(uint2) * work.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !hp.empty())
         e = cudaMemcpy(b->d_probs, hp.data(), sizeof(BatchProb) * hp.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !sorted.empty())
@@ -380,6 +411,47 @@ extern "C" int gett_batch_launch_graph(gett_batch *b, void *stream)
     return GETT_OK;
 }
 
+extern "C" int gett_batch_profile(gett_batch *b, int reps, float *ms_out)
+{
+    if (!b || reps <= 0 || !ms_out) return GETT_ERR_ARG;
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+        ms_out[i] = 0.f;
+        const int64_t cnt = b->prob_count[i];
+        if (cnt == 0) continue;
+        const uint2 *w = b->d_work_by_problem + b->prob_start[i];
+        const int ctas = (int)std::min<int64_t>(b->ctas, cnt);
+        auto one = [&] {
+            cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
+            batch_kernel<<<ctas, BT, 0, s>>>(b->d_probs, w, cnt, b->d_tables, b->d_counter);
+        };
+        one();  // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r) one();
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        ms_out[i] = ms / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    return GETT_OK;
+}
+
 extern "C" int gett_batch_get_info(const gett_batch *b, gett_batch_info *info)
 {
     if (!b || !info) return GETT_ERR_ARG;
@@ -403,6 +475,7 @@ extern "C" int gett_batch_destroy(gett_batch *b)
     if (b->d_work) cudaFree(b->d_work);
     if (b->d_tables) cudaFree(b->d_tables);
     if (b->d_counter) cudaFree(b->d_counter);
+    if (b->d_work_by_problem) cudaFree(b->d_work_by_problem);
     delete b;
     return GETT_OK;
 }

@@ -104,8 +104,11 @@ __global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict
         }
         if (threadIdx.x < TKP) sk[threadIdx.x] = k0 + threadIdx.x < K ? kT[k0 + threadIdx.x] : 0;
         __syncthreads();
-        unsigned long long local[TR * TKP / PT];
-        int lr[TR * TKP / PT];
+        // each thread's elements of one row are reduced in registers first:
+        // row-fast mapping -> all of a thread's elements share one row;
+        // k-fast mapping -> a warp covers 32 k of one row per step
+        unsigned long long mine = 0;
+        int myrow = 0;
 #pragma unroll
         for (int j = 0; j < TR * TKP / PT; ++j) {
             int e = threadIdx.x + j * PT;
@@ -116,20 +119,29 @@ __global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict
             if (r0 + r < rows && k0 + k < K)
                 b = (unsigned long long)__double_as_longlong(__ldg(src + srow[r] + sk[k])) & 0x7FFFFFFFFFFFFFFFull;
             if ((b >> 52) == 0x7FF) b = 0;
-            local[j] = b;
-            lr[j] = r;
-        }
+            if (ROW_FAST) {
+                mine = b > mine ? b : mine;
+                myrow = r;
+            } else {
 #pragma unroll
-        for (int j = 0; j < TR * TKP / PT; ++j)
-            if (local[j]) atomicMax(&smax[lr[j]], local[j]);
+                for (int d = 16; d > 0; d >>= 1) {
+                    const unsigned long long o = __shfl_down_sync(0xffffffffu, b, d);
+                    b = o > b ? o : b;
+                }
+                if ((threadIdx.x & 31) == 0 && b) atomicMax(&smax[r], b);
+            }
+        }
+        if (ROW_FAST && mine) atomicMax(&smax[myrow], mine);
         __syncthreads();
         if (threadIdx.x < TR && r0 + threadIdx.x < rows && smax[threadIdx.x])
             atomicMax(&maxbits[r0 + threadIdx.x], smax[threadIdx.x]);
     }
 }
 
-// residues of round(x * 2^shift) for every modulus, packed [L][rows][ld] bf16
-template <int ROW_FAST>
+// residues of round(x * 2^shift) for every modulus, packed [L][rows][ld] bf16.
+// Each thread converts two neighbouring k of one row and stores both bf16
+// residues of a modulus with one 32-bit store (ld is even, k0 multiple of 64).
+template <int ROW_FAST, int L>
 __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict__ src,
                                                        const int64_t *__restrict__ rowT,
                                                        const int64_t *__restrict__ kT, int64_t rows, int64_t K,
@@ -140,6 +152,14 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
     __shared__ int64_t srow[TR];
     __shared__ int sshift[TR];
     __shared__ int64_t sk[TKP];
+    float pf[L], ip[L], c21[L], c42[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        pf[l] = c.pf[l];
+        ip[l] = c.invp[l];
+        c21[l] = c.c21[l];
+        c42[l] = c.c42[l];
+    }
     const int64_t tiles_k = (K + TKP - 1) / TKP;
     const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
     const int64_t plane = rows * ld;
@@ -159,36 +179,65 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
             int r, k;
             if (ROW_FAST) { r = e % TR; k = e / TR; }
             else { k = e % TKP; r = e / TKP; }
-            uint64_t b = 0;
-            if (r0 + r < rows && k0 + k < K) b = (uint64_t)__double_as_longlong(__ldg(src + srow[r] + sk[k]));
-            tile[r][k] = b;
+            uint64_t bits = 0;
+            if (r0 + r < rows && k0 + k < K) bits = (uint64_t)__double_as_longlong(__ldg(src + srow[r] + sk[k]));
+            tile[r][k] = bits;
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < TR * TKP / PT; ++j) {
-            int e = threadIdx.x + j * PT;
-            int k = e % TKP, r = e / TKP;
+        for (int j = 0; j < TR * TKP / (2 * PT); ++j) {
+            const int e = threadIdx.x + j * PT;
+            const int kp = e % (TKP / 2), r = e / (TKP / 2);
+            const int k = 2 * kp;
             if (r0 + r >= rows || k0 + k >= K) continue;
-            const uint64_t bits = tile[r][k];
-            const bool neg = (bits >> 63) != 0;
-            const uint64_t v = scaled_int(bits & 0x7FFFFFFFFFFFFFFFull, sshift[r]);
-            const float lo = (float)(uint32_t)(v & 0x1FFFFF);
-            const float mid = (float)(uint32_t)((v >> 21) & 0x1FFFFF);
-            const float hi = (float)(uint32_t)(v >> 42);
-            uint16_t *o = out + (r0 + r) * ld + k0 + k;
-            for (int l = 0; l < c.L; ++l) {
-                const float pf = c.pf[l], ip = c.invp[l];
-                const float lr = fmaf(-rintf(lo * ip), pf, lo);
-                const float mr = fmaf(-rintf(mid * ip), pf, mid);
-                const float s = fmaf(hi, c.c42[l], fmaf(mr, c.c21[l], lr));
-                float x = fmaf(-rintf(s * ip), pf, s);
-                const float half = 0.5f * (pf - 1.f);
-                x = x > half ? x - pf : x;
-                x = x < -half ? x + pf : x;
-                o[l * plane] = f2bf_bits(neg ? -x : x);
+            float lo[2], mid[2], hi[2];
+            bool neg[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const uint64_t bits = tile[r][k + u];
+                neg[u] = (bits >> 63) != 0;
+                const uint64_t v = scaled_int(bits & 0x7FFFFFFFFFFFFFFFull, sshift[r]);
+                lo[u] = (float)(uint32_t)(v & 0x1FFFFF);
+                mid[u] = (float)(uint32_t)((v >> 21) & 0x1FFFFF);
+                hi[u] = (float)(uint32_t)(v >> 42);
+            }
+            uint32_t *o = reinterpret_cast<uint32_t *>(out + (r0 + r) * ld + k0 + k);
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                uint32_t packed = 0;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const float lr = fmaf(-rintf(lo[u] * ip[l]), pf[l], lo[u]);
+                    const float mr = fmaf(-rintf(mid[u] * ip[l]), pf[l], mid[u]);
+                    const float sum = fmaf(hi[u], c42[l], fmaf(mr, c21[l], lr));
+                    float x = fmaf(-rintf(sum * ip[l]), pf[l], sum);
+                    const float half = 0.5f * (pf[l] - 1.f);
+                    x = x > half ? x - pf[l] : x;
+                    x = x < -half ? x + pf[l] : x;
+                    packed |= (uint32_t)f2bf_bits(neg[u] ? -x : x) << (16 * u);
+                }
+                o[(l * plane) / 2] = packed;
             }
         }
     }
+}
+
+template <int ROW_FAST>
+cudaError_t launch_residues(const double *src, const int64_t *rowT, const int64_t *kT, int64_t rows, int64_t K,
+                            const unsigned long long *maxbits, int kbits, const OzConsts &c, uint16_t *out,
+                            int64_t ld, int blocks, cudaStream_t s)
+{
+#define CASE(LL)                                                                                    \
+    case LL:                                                                                        \
+        oz_residue_kernel<ROW_FAST, LL><<<blocks, PT, 0, s>>>(src, rowT, kT, rows, K, maxbits, kbits, c, out, ld); \
+        break;
+    switch (c.L) {
+        CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
+        CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20)
+    default: return cudaErrorInvalidValue;
+    }
+#undef CASE
+    return cudaGetLastError();
 }
 
 template <int L>
@@ -457,15 +506,11 @@ cudaError_t launch_ozaki(const Plan &pl, int L_req, const void *A, const void *B
     else oz_maxbits_kernel<0><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA);
     if (b_row_fast) oz_maxbits_kernel<1><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB);
     else oz_maxbits_kernel<0><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB);
-    if (a_row_fast)
-        oz_residue_kernel<1><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA, c.ka, c, o.RA, o.ld);
-    else
-        oz_residue_kernel<0><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA, c.ka, c, o.RA, o.ld);
-    if (b_row_fast)
-        oz_residue_kernel<1><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB, c.kb, c, o.RB, o.ld);
-    else
-        oz_residue_kernel<0><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB, c.kb, c, o.RB, o.ld);
-    e = cudaGetLastError();
+    e = a_row_fast ? launch_residues<1>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA, c.ka, c, o.RA, o.ld, blocks_for(pl.M), s)
+                   : launch_residues<0>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA, c.ka, c, o.RA, o.ld, blocks_for(pl.M), s);
+    if (e != cudaSuccess) return e;
+    e = b_row_fast ? launch_residues<1>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB, c.kb, c, o.RB, o.ld, blocks_for(pl.N), s)
+                   : launch_residues<0>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB, c.kb, c, o.RB, o.ld, blocks_for(pl.N), s);
     if (e != cudaSuccess) return e;
     TcGemmParams p{};
     p.M = pl.M;

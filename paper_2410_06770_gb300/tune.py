@@ -1,0 +1,236 @@
+"""Autotuner and learned-planner training for the batched path.
+
+    python -m paper_2410_06770_gb300.tune --train 20000 --test 2000 \\
+        --model OUT.npz --report OUT.json
+
+1. Draws contraction signatures from the batched workload's distribution
+   (ranks 2-5, extents up to --max-ext, 0-3 contracted modes, 25 % padded,
+   fp32/bf16 operands, <= 2^18 elements per tensor).
+2. Autotuner: times every problem alone with every tile configuration of the
+   batched kernel (gett_batch_profile: CUDA events around back-to-back
+   launches) -> a table of times; the exhaustive best configuration is the
+   tuned choice.
+3. Learned planner: features of each signature (gett_problem_features) ->
+   MLP predicting normalised log times of all configurations, trained on the
+   GPU by the library's own kernels (gett_mlp_fit).
+4. Held-out evaluation: regret of the network's choice against exhaustive
+   tuning (geometric mean of t_pred / t_best - 1, share above 10 %), the same
+   for the fixed heuristic, fallback rate, and end-to-end throughput of one
+   persistent launch with learned vs heuristic vs tuned configurations.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import batch as gb
+from . import synth
+
+
+def draw_problems(n, seed, max_ext):
+    sigs = synth.batched_signatures(n=n, seed=seed, max_ext=max_ext)
+    probs = []
+    for d in sigs:
+        s = d["sig"]
+        pads = d["pads"]
+        la = synth.layout_with_pads(s.exta, pads[0] if pads else None)
+        lb = synth.layout_with_pads(s.extb, pads[1] if pads else None)
+        lc = synth.layout_with_pads(s.extc(), pads[2] if pads else None)
+        probs.append(dict(sig=s, la=la, lb=lb, lc=lc, dtype=d["dtype"], seed=d["value_seed"]))
+    return probs
+
+
+def args_of(pr):
+    s = pr["sig"]
+    return dict(EXTA=s.exta, INCA=pr["la"].inc, EXTB=s.extb, INCB=pr["lb"].inc, CONTA=s.conta,
+                CONTB=s.contb, PERM=s.perm, INCC=pr["lc"].inc)
+
+
+def flops(pr):
+    s = pr["sig"]
+    K = int(np.prod([s.exta[m] for m in s.conta], dtype=np.int64)) if s.conta else 1
+    return 2.0 * int(np.prod(s.extc(), dtype=np.int64)) * K
+
+
+class DeviceBuffers:
+    """Device buffers for a list of problems (values from each problem's seed
+    when `values`, zeros otherwise: run times do not depend on values)."""
+
+    def __init__(self, probs, values=False):
+        import torch
+        self.keep = []
+        self.descs = []
+        for pr in probs:
+            bf = pr["dtype"] == "bf16"
+            if values:
+                rng = np.random.default_rng(pr["seed"])
+                A = synth.fill(pr["la"], rng.uniform(-1, 1, pr["la"].numel), np.float32, 0.0)
+                B = synth.fill(pr["lb"], rng.uniform(-1, 1, pr["lb"].numel), np.float32, 0.0)
+                C = synth.fill(pr["lc"], rng.uniform(-1, 1, pr["lc"].numel), np.float32, 0.0)
+                tA = torch.from_numpy(A)
+                tB = torch.from_numpy(B)
+                if bf:
+                    tA = tA.to(torch.bfloat16)
+                    tB = tB.to(torch.bfloat16)
+                dA, dB, dC = tA.cuda(), tB.cuda(), torch.from_numpy(C).cuda()
+            else:
+                dt = torch.bfloat16 if bf else torch.float32
+                dA = torch.zeros(pr["la"].size, dtype=dt, device="cuda")
+                dB = torch.zeros(pr["lb"].size, dtype=dt, device="cuda")
+                dC = torch.zeros(pr["lc"].size, dtype=torch.float32, device="cuda")
+            self.keep.append((dA, dB, dC))
+            d = args_of(pr)
+            d.update(dtype=pr["dtype"], A=dA.data_ptr() + pr["la"].off * dA.element_size(),
+                     B=dB.data_ptr() + pr["lb"].off * dB.element_size(),
+                     C=dC.data_ptr() + pr["lc"].off * 4)
+            self.descs.append(d)
+
+
+def measure(probs, reps=3, chunk=1024, log=None):
+    """times[i][c]: mean ms of problem i alone with tile configuration c."""
+    import torch
+    nc = gb.num_configs()
+    T = np.zeros((len(probs), nc), dtype=np.float64)
+    for s in range(0, len(probs), chunk):
+        part = probs[s:s + chunk]
+        bufs = DeviceBuffers(part)
+        for c in range(nc):
+            b = gb.Batch(bufs.descs, select="fixed", config=c)
+            T[s:s + len(part), c] = b.profile(reps)
+            b.close()
+        del bufs
+        torch.cuda.empty_cache()
+        if log:
+            log(f"measured {min(s + chunk, len(probs))}/{len(probs)}")
+    return T
+
+
+def featurize(probs):
+    return np.stack([gb.features(args_of(pr), pr["dtype"]) for pr in probs]).astype(np.float32)
+
+
+def train(X, T, hidden=128, epochs=60, batch=256, lr=1e-3, seed=0):
+    mean = X.mean(0)
+    std = X.std(0)
+    std[std == 0] = 1.0
+    Xn = (X - mean) / std
+    Y = np.log(np.maximum(T, 1e-6))
+    mu, sd = Y.mean(), Y.std() if Y.std() > 0 else 1.0
+    Yn = ((Y - mu) / sd).astype(np.float32)
+    M = np.ones_like(Yn, dtype=np.float32)
+    net = gb.MLP(X.shape[1], hidden, T.shape[1], seed=seed)
+    loss = net.fit(Xn.astype(np.float32), Yn, M, epochs=epochs, batch=batch, lr=lr, seed=seed + 1)
+    return dict(params=net.get_params(), mean=mean.astype(np.float32), std=std.astype(np.float32),
+                hidden=hidden, nout=T.shape[1], final_loss=loss, y_mean=mu, y_std=sd)
+
+
+def predict_configs(model, X):
+    net = gb.MLP(X.shape[1], model["hidden"], model["nout"], seed=0)
+    net.set_params(model["params"])
+    Y = net.predict(((X - model["mean"]) / model["std"]).astype(np.float32))
+    finite = np.all(np.isfinite(Y), axis=1)
+    return np.argmin(Y, axis=1), finite
+
+
+def regret(choice, T):
+    best = T.min(axis=1)
+    r = T[np.arange(len(T)), choice] / best
+    return {"geomean_regret": float(np.exp(np.mean(np.log(r))) - 1.0),
+            "share_above_10pct": float(np.mean(r > 1.10)),
+            "mean_ratio": float(np.mean(r))}
+
+
+def save_model(path, model):
+    np.savez(path, **{k: np.asarray(v) for k, v in model.items()})
+
+
+def load_model(path):
+    z = np.load(path)
+    m = {k: z[k] for k in z.files}
+    m["hidden"] = int(m["hidden"])
+    m["nout"] = int(m["nout"])
+    return m
+
+
+def install(model):
+    gb.install_model(model["params"], model["mean"], model["std"], model["hidden"], model["nout"])
+
+
+def throughput(probs, select, configs=None, reps=10):
+    """Contractions/s and TFLOP/s of one persistent launch (graph replay)."""
+    import torch
+    bufs = DeviceBuffers(probs)
+    b = gb.Batch(bufs.descs, select=select, configs=configs)
+    info = b.info()
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        b.launch(stream=stream.cuda_stream, graph=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        b.launch(stream=stream.cuda_stream, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    b.close()
+    del bufs
+    return {"ms": ms, "contractions_per_s": len(probs) / (ms * 1e-3),
+            "tflops": info["flops"] / (ms * 1e-3) / 1e12, "fallbacks": info["fallbacks"],
+            "config_count": info["config_count"][:gb.num_configs()]}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=20000)
+    ap.add_argument("--test", type=int, default=2000)
+    ap.add_argument("--max-ext", type=int, default=256)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--model", default=None)
+    ap.add_argument("--report", default=None)
+    args = ap.parse_args(argv)
+    import torch
+    t0 = time.time()
+    log = lambda m: print(f"[{time.time() - t0:7.1f}s] {m}", file=sys.stderr, flush=True)
+    tr = draw_problems(args.train, 11, args.max_ext)
+    te = draw_problems(args.test, 12, args.max_ext)
+    log("signatures drawn")
+    Ttr = measure(tr, args.reps, log=log)
+    Tte = measure(te, args.reps, log=log)
+    Xtr, Xte = featurize(tr), featurize(te)
+    log("features done")
+    model = train(Xtr, Ttr, epochs=args.epochs)
+    log(f"trained, final loss {model['final_loss']:.4f}")
+    pred, finite = predict_configs(model, Xte)
+    heur = np.array([gb.heuristic_config(args_of(pr)) for pr in te])
+    tuned = T_best = Tte.argmin(axis=1)
+    pred_used = np.where(finite, pred, heur)
+    rep = {
+        "train": args.train, "test": args.test, "max_ext": args.max_ext, "epochs": args.epochs,
+        "configs": gb.num_configs(), "final_train_loss": model["final_loss"],
+        "learned": regret(pred_used, Tte), "heuristic": regret(heur, Tte),
+        "fallback_rate": float(np.mean(~finite)),
+        "learned_matches_best": float(np.mean(pred_used == tuned)),
+    }
+    install(model)
+    rep["throughput_learned"] = throughput(te, "learned")
+    rep["throughput_heuristic"] = throughput(te, "heuristic")
+    rep["throughput_tuned"] = throughput(te, "table", configs=list(tuned))
+    rep["elapsed_s"] = time.time() - t0
+    log(json.dumps(rep))
+    if args.model:
+        save_model(args.model, model)
+    if args.report:
+        with open(args.report, "w") as f:
+            json.dump(rep, f, indent=1)
+    print(json.dumps(rep))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
