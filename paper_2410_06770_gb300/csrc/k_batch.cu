@@ -8,11 +8,15 @@
 // tile cost so long tiles start first.  The persistent kernel runs
 // ctas_per_sm CTAs per SM; each CTA takes the next work item from an atomic
 // counter and computes that tile with the shared CUDA-core tile routine
-// (float arithmetic; bf16 operands are widened on load).  Every tile is
-// computed by exactly one CTA, so results do not depend on scheduling.
+// (float arithmetic; bf16 operands are widened on load).  Tiles whose K
+// extent would make them far longer than a CTA's average share are split
+// into K slices; slices write partial tiles that a second kernel adds into C
+// in slice order.  Every output element is therefore summed in a fixed order
+// and results do not depend on scheduling.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <numeric>
@@ -44,13 +48,17 @@ struct BatchProb {
     int tiles_m, tiles_n;
     int cfg, dtype;
     int a_m_fast, b_n_fast, c_m_fast;
+    int splits;       // K slices (1: the tile is added into C directly)
+    int64_t kps;      // K per slice (multiple of the tile's BK)
+    float *partial;   // splits > 1: [splits][M*N] partial tiles
 };
 
 template <class T, int CFG>
-__device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tables, int tile, float *smem_f,
+__device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tables, int item, float *smem_f,
                                          int64_t *smem_i)
 {
     constexpr BCfg c = kB[CFG];
+    const int tile = item / pr.splits, split = item % pr.splits;
     const int tm = tile / pr.tiles_n, tn = tile % pr.tiles_n;
     TileArgs a;
     a.A = pr.A;
@@ -67,12 +75,12 @@ __device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tab
     a.N = pr.N;
     a.m0 = (int64_t)tm * c.bm;
     a.n0 = (int64_t)tn * c.bn;
-    a.kbeg = 0;
-    a.kend = pr.K;
+    a.kbeg = split * pr.kps;
+    a.kend = min(pr.K, a.kbeg + pr.kps);
     a.a_m_fast = pr.a_m_fast;
     a.b_n_fast = pr.b_n_fast;
     a.c_m_fast = pr.c_m_fast;
-    a.partial = nullptr;
+    a.partial = pr.splits > 1 ? pr.partial + (int64_t)split * pr.M * pr.N : nullptr;
     dense_tile<T, c.bm, c.bn, c.bk, c.tm, c.tn>(a, smem_f, smem_f + 2 * c.bk * c.bm, smem_i, smem_i + c.bm);
 }
 
@@ -118,6 +126,30 @@ __global__ void __launch_bounds__(BT) batch_kernel(const BatchProb *__restrict__
         default: break;
         }
         __syncthreads();
+    }
+}
+
+// Adds the K-slice partial tiles of every split problem into C, slices in
+// order (deterministic).  One CTA per listed problem at a time.
+__global__ void __launch_bounds__(256) batch_reduce_kernel(const BatchProb *__restrict__ probs,
+                                                           const int *__restrict__ list, int nlist,
+                                                           const int64_t *__restrict__ tables)
+{
+    for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+        const BatchProb pr = probs[list[li]];
+        const int64_t *t = tables + pr.tab;
+        const int64_t *rowC = t + pr.M;
+        const int64_t *colC = t + 2 * pr.M + pr.N;
+        const int64_t MN = pr.M * pr.N;
+        for (int64_t i = threadIdx.x; i < MN; i += blockDim.x) {
+            int64_t m, n;
+            if (pr.c_m_fast) { m = i % pr.M; n = i / pr.M; }
+            else { n = i % pr.N; m = i / pr.N; }
+            float sum = pr.partial[i];
+            for (int sp = 1; sp < pr.splits; ++sp) sum += pr.partial[(int64_t)sp * MN + i];
+            float *dst = pr.C + rowC[m] + colC[n];
+            *dst = *dst + sum;
+        }
     }
 }
 
@@ -169,6 +201,10 @@ struct gett_batch {
     int64_t *d_tables = nullptr;
     unsigned long long *d_counter = nullptr;
     uint2 *d_work_by_problem = nullptr;  // work items grouped by problem
+    float *d_partial = nullptr;          // K-slice partial tiles of split problems
+    int *d_reduce = nullptr;             // indices (into the descriptor table) of split problems
+    int nreduce = 0;
+    std::vector<int> reduce_of;          // per user index: descriptor index if split, else -1
     std::vector<int64_t> prob_start, prob_count;  // per user index (count 0: empty)
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -303,6 +339,44 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
         }
     }
 
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    const int ctas = sms * (o.ctas_per_sm > 0 ? o.ctas_per_sm : 2);
+
+    // K slices: a tile whose work is far above the average share of a CTA is
+    // split along K so the longest work item stays short (tail effects);
+    // slices of one tile are added into C in slice order by a second kernel.
+    double total_cost = 0;
+    for (const BatchProb &pr : hp)
+        total_cost += (double)pr.tiles_m * pr.tiles_n * kB[pr.cfg].bm * kB[pr.cfg].bn * (double)pr.K;
+    const double target = std::max(total_cost / (2.0 * ctas), 1.0);
+    int64_t partial_floats = 0;
+    std::vector<int64_t> partial_off(hp.size(), -1);
+    for (size_t j = 0; j < hp.size(); ++j) {
+        BatchProb &pr = hp[j];
+        const int bk = kB[pr.cfg].bk;
+        const double tile_cost = (double)kB[pr.cfg].bm * kB[pr.cfg].bn * (double)pr.K;
+        int64_t S = (int64_t)std::ceil(tile_cost / target);
+        S = std::min<int64_t>(S, 64);
+        S = std::min<int64_t>(S, std::max<int64_t>(1, pr.K / 128));
+        if (S < 1) S = 1;
+        int64_t kps = (pr.K + S - 1) / S;
+        kps = (kps + bk - 1) / bk * bk;
+        S = (pr.K + kps - 1) / kps;
+        if (S > 1 && partial_floats + S * pr.M * pr.N > (int64_t)(1 << 28)) S = 1, kps = pr.K;
+        pr.splits = (int)S;
+        pr.kps = S > 1 ? kps : pr.K;
+        if (S > 1) {
+            partial_off[j] = partial_floats;
+            partial_floats += S * pr.M * pr.N;
+        }
+    }
+
     gett_batch *b = new gett_batch();
     b->n = n;
     b->nonempty = (int)hp.size();
@@ -320,17 +394,25 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
         b->flops += 2.0 * (double)p.M * (double)p.N * (double)p.K;
         b->config_count[pr.cfg]++;
         const int nt = pr.tiles_m * pr.tiles_n;
-        for (int tt = 0; tt < nt; ++tt) {
+        for (int tt = 0; tt < nt * pr.splits; ++tt) {
             work.push_back(make_uint2((unsigned)j, (unsigned)tt));
-            cost.push_back((double)kB[pr.cfg].bm * kB[pr.cfg].bn * (double)p.K);
+            cost.push_back((double)kB[pr.cfg].bm * kB[pr.cfg].bn * (double)pr.kps);
         }
     }
     b->prob_start.assign(n, 0);
     b->prob_count.assign(n, 0);
+    b->reduce_of.assign(n, -1);
+    std::vector<int> reduce_list;
+    for (size_t j = 0; j < hp.size(); ++j)
+        if (hp[j].splits > 1) {
+            b->reduce_of[hp_index[j]] = (int)reduce_list.size();
+            reduce_list.push_back((int)j);
+        }
+    b->nreduce = (int)reduce_list.size();
     {
         int64_t pos = 0;
         for (size_t j = 0; j < hp.size(); ++j) {
-            const int nt = hp[j].tiles_m * hp[j].tiles_n;
+            const int nt = hp[j].tiles_m * hp[j].tiles_n * hp[j].splits;
             b->prob_start[hp_index[j]] = pos;
             b->prob_count[hp_index[j]] = nt;
             pos += nt;
@@ -344,10 +426,14 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = work[order[i]];
     b->nwork = (int64_t)sorted.size();
 
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->ctas = sms * (o.ctas_per_sm > 0 ? o.ctas_per_sm : 2);
+    b->ctas = ctas;
+    e = cudaMalloc(&b->d_partial, sizeof(float) * (size_t)std::max<int64_t>(partial_floats, 1));
+    if (e == cudaSuccess)
+        for (size_t j = 0; j < hp.size(); ++j)
+            hp[j].partial = partial_off[j] >= 0 ? b->d_partial + partial_off[j] : nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_reduce, sizeof(int) * std::max<size_t>(reduce_list.size(), 1));
+    if (e == cudaSuccess && !reduce_list.empty())
+        e = cudaMemcpy(b->d_reduce, reduce_list.data(), sizeof(int) * reduce_list.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, sizeof(BatchProb) * std::max<size_t>(hp.size(), 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_work, sizeof(uint2) * std::max<size_t>(sorted.size(), 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tables, sizeof(int64_t) * tables.size());
@@ -375,6 +461,9 @@ static cudaError_t enqueue(gett_batch *b, cudaStream_t s)
     if (e != cudaSuccess || b->nwork == 0) return e;
     const int ctas = (int)std::min<int64_t>(b->ctas, b->nwork);
     batch_kernel<<<ctas, BT, 0, s>>>(b->d_probs, b->d_work, b->nwork, b->d_tables, b->d_counter);
+    if (b->nreduce > 0)
+        batch_reduce_kernel<<<std::min(b->nreduce, b->ctas), 256, 0, s>>>(b->d_probs, b->d_reduce, b->nreduce,
+                                                                          b->d_tables);
     return cudaGetLastError();
 }
 
@@ -429,9 +518,11 @@ extern "C" int gett_batch_profile(gett_batch *b, int reps, float *ms_out)
         if (cnt == 0) continue;
         const uint2 *w = b->d_work_by_problem + b->prob_start[i];
         const int ctas = (int)std::min<int64_t>(b->ctas, cnt);
+        const int red = b->reduce_of[i];
         auto one = [&] {
             cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
             batch_kernel<<<ctas, BT, 0, s>>>(b->d_probs, w, cnt, b->d_tables, b->d_counter);
+            if (red >= 0) batch_reduce_kernel<<<1, 256, 0, s>>>(b->d_probs, b->d_reduce + red, 1, b->d_tables);
         };
         one();  // warm-up
         cudaEventRecord(e0, s);
@@ -476,6 +567,8 @@ extern "C" int gett_batch_destroy(gett_batch *b)
     if (b->d_tables) cudaFree(b->d_tables);
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_work_by_problem) cudaFree(b->d_work_by_problem);
+    if (b->d_partial) cudaFree(b->d_partial);
+    if (b->d_reduce) cudaFree(b->d_reduce);
     delete b;
     return GETT_OK;
 }

@@ -46,13 +46,25 @@ struct OzConsts {
     float invp[OZ_MAX_L];
     float c21[OZ_MAX_L], c42[OZ_MAX_L];     // 2^21 mod p, 2^42 mod p
     int inv[OZ_MAX_L][OZ_MAX_L];            // inv[i][j] = p_j^{-1} mod p_i (j < i)
+    float invf[OZ_MAX_L][OZ_MAX_L];         // the same as floats
     int half[OZ_MAX_L];                     // mixed-radix digits of (P-1)/2
+    float halff[OZ_MAX_L];
 };
 
 __device__ __forceinline__ uint16_t f2bf_bits(float x)
 {
     __nv_bfloat16 b = __float2bfloat16_rn(x);
     return *reinterpret_cast<uint16_t *>(&b);
+}
+
+// Nearest integer of x * r for |x * r| < 2^22, with two full-rate fp32 ops:
+// adding 1.5 * 2^23 leaves no fraction bits, so the fused multiply-add rounds
+// the product to an integer (round to nearest even), and subtracting the
+// constant again is exact.  Replaces rintf, which runs on a slower pipe.
+__device__ __forceinline__ float round_mul(float x, float r)
+{
+    const float magic = 12582912.0f;  // 1.5 * 2^23
+    return __fadd_rn(__fmaf_rn(x, r, magic), -magic);
 }
 
 // floor(log2(v)) of a positive finite double given its bit pattern
@@ -207,10 +219,10 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
                 uint32_t packed = 0;
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const float lr = fmaf(-rintf(lo[u] * ip[l]), pf[l], lo[u]);
-                    const float mr = fmaf(-rintf(mid[u] * ip[l]), pf[l], mid[u]);
+                    const float lr = fmaf(-round_mul(lo[u], ip[l]), pf[l], lo[u]);
+                    const float mr = fmaf(-round_mul(mid[u], ip[l]), pf[l], mid[u]);
                     const float sum = fmaf(hi[u], c42[l], fmaf(mr, c21[l], lr));
-                    float x = fmaf(-rintf(sum * ip[l]), pf[l], sum);
+                    float x = fmaf(-round_mul(sum, ip[l]), pf[l], sum);
                     const float half = 0.5f * (pf[l] - 1.f);
                     x = x > half ? x - pf[l] : x;
                     x = x < -half ? x + pf[l] : x;
@@ -251,27 +263,28 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
     const int64_t MN = M * N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t m = i % M, n = i / M;
-        int v[L];
+        // Garner's mixed-radix digits, in fp32 holding exact small integers
+        // (every intermediate is an integer below 2^17)
+        float v[L];
 #pragma unroll
         for (int l = 0; l < L; ++l) {
-            int r = R[(int64_t)l * MN + i];
-            v[l] = r < 0 ? r + c.p[l] : r;
+            // int8 -> float without a conversion instruction: r + 128 in [1, 255]
+            // placed in the mantissa of 2^23
+            const int r = (int)R[(int64_t)l * MN + i];
+            const float rf = __int_as_float(0x4B000000 | (r + 128)) - 8388736.0f;
+            v[l] = rf < 0.f ? rf + c.pf[l] : rf;
         }
-        // Garner: v[i] becomes the i-th mixed-radix digit
 #pragma unroll
         for (int a = 1; a < L; ++a) {
-            int t = v[a];
-            const int pa = c.p[a];
+            float t = v[a];
+            const float pa = c.pf[a];
             const float ipa = c.invp[a];
 #pragma unroll
             for (int b = 0; b < a; ++b) {
-                const int d = t - v[b] + 2 * pa;
-                const int x = d * c.inv[a][b];
-                int q = (int)((float)x * ipa);
-                int r = x - q * pa;
-                r = r < 0 ? r + pa : r;
-                r = r >= pa ? r - pa : r;
-                t = r;
+                const float d = t - v[b] + 2.f * pa;           // in (0, 3 pa)
+                const float x = d * c.invf[a][b];               // < 2^17, exact
+                float r = fmaf(-round_mul(x, ipa), pa, x);      // x mod pa, in (-pa, pa)
+                t = r < 0.f ? r + pa : r;
             }
             v[a] = t;
         }
@@ -279,7 +292,7 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
         int cmp = 0;
 #pragma unroll
         for (int a = L - 1; a >= 0; --a)
-            if (cmp == 0) cmp = v[a] > c.half[a] ? 1 : (v[a] < c.half[a] ? -1 : 0);
+            if (cmp == 0) cmp = v[a] > c.halff[a] ? 1 : (v[a] < c.halff[a] ? -1 : 0);
         const bool negv = cmp > 0;
         // exact Horner evaluation of the mixed-radix digits in three 64-bit
         // limbs (|X| < P < 2^160), then one correctly rounded conversion
@@ -287,7 +300,9 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
 #pragma unroll
         for (int a = L - 1; a >= 0; --a) {
             const uint64_t pa = (uint64_t)c.p[a];
-            const uint64_t d = (uint64_t)(negv ? (c.p[a] - 1 - v[a]) : v[a]);
+            // exact small non-negative integer float -> integer via the 2^23 mantissa
+            const float df = negv ? (c.pf[a] - 1.f - v[a]) : v[a];
+            const uint64_t d = (uint64_t)(__float_as_int(df + 8388608.0f) & 0x7FFFFF);
             const uint64_t l0 = h0 * pa, c0 = __umul64hi(h0, pa);
             const uint64_t l1 = h1 * pa, c1 = __umul64hi(h1, pa);
             h2 = h2 * pa + c1;
@@ -384,13 +399,17 @@ void oz_setup(int64_t K, int want_L, OzConsts *c)
         long long m21 = (1LL << 21) % p;
         c->c21[i] = (float)m21;
         c->c42[i] = (float)((m21 * m21) % p);
-        for (int j = 0; j < OZ_MAX_L; ++j) c->inv[i][j] = (j < i) ? modinv(kOzModuli[j] % p, p) : 0;
+        for (int j = 0; j < OZ_MAX_L; ++j) {
+            c->inv[i][j] = (j < i) ? modinv(kOzModuli[j] % p, p) : 0;
+            c->invf[i][j] = (float)c->inv[i][j];
+        }
     }
     // digits of (P-1)/2: long division of the digits (p_i - 1) by 2 from the top
     int carry = 0;
     for (int i = L - 1; i >= 0; --i) {
         const int cur = carry * c->p[i] + (c->p[i] - 1);
         c->half[i] = cur / 2;
+        c->halff[i] = (float)c->half[i];
         carry = cur % 2;
     }
 }

@@ -184,8 +184,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 for (int i = 0; i < 32; ++i) {
                     const float x = res[cb * 32 + i] + __uint_as_float(v[i]);
                     if (MODE == TC_MODE_MOD) {
-                        // exact: |res| <= p/2 + 3 and |chunk sum| < 2^24 - 2^8
-                        const float qq = rintf(x * inv);
+                        // exact: |res| <= p/2 + 3 and |chunk sum| < 2^24 - 2^8;
+                        // q = nearest integer of x / p via the 1.5 * 2^23 constant
+                        const float qq = __fadd_rn(__fmaf_rn(x, inv, 12582912.0f), -12582912.0f);
                         res[cb * 32 + i] = fmaf(-qq, pm, x);
                     } else {
                         res[cb * 32 + i] = x;
