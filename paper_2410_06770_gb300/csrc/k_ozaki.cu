@@ -44,7 +44,7 @@ struct OzConsts {
     int p[OZ_MAX_L];
     float pf[OZ_MAX_L];
     float invp[OZ_MAX_L];
-    float c21[OZ_MAX_L], c42[OZ_MAX_L];     // 2^21 mod p, 2^42 mod p
+    float c13[OZ_MAX_L], c26[OZ_MAX_L], c39[OZ_MAX_L];  // 2^13, 2^26, 2^39 mod p, symmetric
     int inv[OZ_MAX_L][OZ_MAX_L];            // inv[i][j] = p_j^{-1} mod p_i (j < i)
     float invf[OZ_MAX_L][OZ_MAX_L];         // the same as floats
     int half[OZ_MAX_L];                     // mixed-radix digits of (P-1)/2
@@ -164,14 +164,6 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
     __shared__ int64_t srow[TR];
     __shared__ int sshift[TR];
     __shared__ int64_t sk[TKP];
-    float pf[L], ip[L], c21[L], c42[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-        pf[l] = c.pf[l];
-        ip[l] = c.invp[l];
-        c21[l] = c.c21[l];
-        c42[l] = c.c42[l];
-    }
     const int64_t tiles_k = (K + TKP - 1) / TKP;
     const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
     const int64_t plane = rows * ld;
@@ -202,33 +194,33 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
             const int kp = e % (TKP / 2), r = e / (TKP / 2);
             const int k = 2 * kp;
             if (r0 + r >= rows || k0 + k >= K) continue;
-            float lo[2], mid[2], hi[2];
-            bool neg[2];
+            // four 13-bit limbs of the scaled integer, sign applied to the limbs,
+            // converted to float through the 2^23 mantissa (no conversion op)
+            float l0[2], l1[2], l2[2], l3[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const uint64_t bits = tile[r][k + u];
-                neg[u] = (bits >> 63) != 0;
                 const uint64_t v = scaled_int(bits & 0x7FFFFFFFFFFFFFFFull, sshift[r]);
-                lo[u] = (float)(uint32_t)(v & 0x1FFFFF);
-                mid[u] = (float)(uint32_t)((v >> 21) & 0x1FFFFF);
-                hi[u] = (float)(uint32_t)(v >> 42);
+                const float sg = (bits >> 63) ? -1.f : 1.f;
+                l0[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)(v & 0x1FFF)) - 8388608.0f);
+                l1[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)((v >> 13) & 0x1FFF)) - 8388608.0f);
+                l2[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)((v >> 26) & 0x1FFF)) - 8388608.0f);
+                l3[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)(v >> 39)) - 8388608.0f);
             }
             uint32_t *o = reinterpret_cast<uint32_t *>(out + (r0 + r) * ld + k0 + k);
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                uint32_t packed = 0;
+                float x[2];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const float lr = fmaf(-round_mul(lo[u], ip[l]), pf[l], lo[u]);
-                    const float mr = fmaf(-round_mul(mid[u], ip[l]), pf[l], mid[u]);
-                    const float sum = fmaf(hi[u], c42[l], fmaf(mr, c21[l], lr));
-                    float x = fmaf(-round_mul(sum, ip[l]), pf[l], sum);
-                    const float half = 0.5f * (pf[l] - 1.f);
-                    x = x > half ? x - pf[l] : x;
-                    x = x < -half ? x + pf[l] : x;
-                    packed |= (uint32_t)f2bf_bits(neg[u] ? -x : x) << (16 * u);
+                    // |s| <= 127 * 3 * 8191 + 8191 < 2^22: exact; nearest rounding of
+                    // s / p is exact for odd p, so the residue lies in [-(p-1)/2, (p-1)/2]
+                    const float sum = fmaf(l3[u], c.c39[l], fmaf(l2[u], c.c26[l], fmaf(l1[u], c.c13[l], l0[u])));
+                    x[u] = fmaf(-round_mul(sum, c.invp[l]), c.pf[l], sum);
                 }
-                o[(l * plane) / 2] = packed;
+                // |x| <= 127 has at most 7 significant bits: its bf16 pattern is the
+                // upper half of the fp32 pattern; pack both upper halves at once
+                o[(l * plane) / 2] = __byte_perm(__float_as_uint(x[0]), __float_as_uint(x[1]), 0x7632);
             }
         }
     }
@@ -396,9 +388,11 @@ void oz_setup(int64_t K, int want_L, OzConsts *c)
         c->p[i] = p;
         c->pf[i] = (float)p;
         c->invp[i] = 1.0f / (float)p;
-        long long m21 = (1LL << 21) % p;
-        c->c21[i] = (float)m21;
-        c->c42[i] = (float)((m21 * m21) % p);
+        auto sym = [p](long long r) { r %= p; return (float)(r > (p - 1) / 2 ? r - p : r); };
+        const long long m13 = (1LL << 13) % p;
+        c->c13[i] = sym(m13);
+        c->c26[i] = sym(m13 * m13);
+        c->c39[i] = sym(m13 * m13 % p * m13);
         for (int j = 0; j < OZ_MAX_L; ++j) {
             c->inv[i][j] = (j < i) ? modinv(kOzModuli[j] % p, p) : 0;
             c->invf[i][j] = (float)c->inv[i][j];

@@ -3,7 +3,8 @@
     python -m paper_2410_06770_gb300.profile_case WORKLOAD [SCALE] [--calls N] [--algo A]
 
 WORKLOAD: cc, cc_perm_transA (extents a..d = SCALE, i,j = SCALE/4), stream
-(A(SCALE, SCALE, 64) x B(64, 8)), small.  Inputs are generated on the host,
+(A(SCALE, SCALE, 64) x B(64, 8)), small, batched (SCALE contractions of the
+batched workload, one persistent launch per call).  Inputs are generated on the host,
 copied once, then the call is made N times (default 2) and synchronised.
 """
 import argparse
@@ -24,6 +25,17 @@ def main(argv=None):
 
     from . import build, gett, synth
     build.build()
+    if args.workload == "batched":
+        from . import batch as gb
+        from . import tune
+        probs = tune.draw_problems(args.scale, 7, 64)
+        bufs = tune.DeviceBuffers(probs)
+        b = gb.Batch(bufs.descs)
+        for _ in range(args.calls):
+            b.launch()
+        torch.cuda.synchronize()
+        print(b.info())
+        return 0
     if args.workload == "cc":
         p = synth.cfg_cc("plain", scale=args.scale, small_ij=max(1, args.scale // 4))
     elif args.workload == "cc_perm_transA":
