@@ -37,7 +37,11 @@ constexpr int NCFG = 4;
 struct BCfg {
     int bm, bn, bk, tm, tn;
 };
-constexpr BCfg kB[NCFG] = {{128, 64, 8, 8, 4}, {64, 64, 16, 4, 4}, {32, 32, 16, 2, 2}, {64, 32, 16, 4, 2}};
+// Tile shapes (all 256 threads, at most 4x4 accumulators a thread, so two
+// CTAs fit on an SM without spills: the gathers are latency bound and need
+// warps in flight).
+constexpr BCfg kB[NCFG] = {{64, 64, 16, 4, 4}, {32, 64, 16, 2, 4}, {32, 32, 16, 2, 2}, {64, 32, 16, 4, 2}};
+constexpr int kCtasPerSm = 2;
 
 struct BatchProb {
     const void *A;
@@ -98,7 +102,7 @@ constexpr int smem_ints()
     return m;
 }
 
-__global__ void __launch_bounds__(BT) batch_kernel(const BatchProb *__restrict__ probs, const uint2 *__restrict__ work,
+__global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *__restrict__ probs, const uint2 *__restrict__ work,
                                                    int64_t nwork, const int64_t *__restrict__ tables,
                                                    unsigned long long *counter)
 {
@@ -180,8 +184,8 @@ int64_t first_abs(const ModeList &L, const int64_t *s) { return L.n ? (s[0] < 0 
 int batch_heuristic_config(int64_t M, int64_t N, int64_t K)
 {
     (void)K;
-    if (M >= 128 && N >= 64) return 0;
-    if (M >= 64 && N >= 64) return 1;
+    if (M >= 64 && N >= 64) return 0;
+    if (M < 64 && N >= 64) return 1;
     if (M >= 64 && N < 64) return 3;
     return 2;
 }
@@ -346,7 +350,7 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
         set_last_cuda_error(e);
         return GETT_ERR_CUDA;
     }
-    const int ctas = sms * (o.ctas_per_sm > 0 ? o.ctas_per_sm : 2);
+    const int ctas = sms * (o.ctas_per_sm > 0 ? o.ctas_per_sm : kCtasPerSm);
 
     // K slices: a tile whose work is far above the average share of a CTA is
     // split along K so the longest work item stays short (tail effects);
