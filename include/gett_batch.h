@@ -89,12 +89,14 @@ int gett_batch_create(int n, const gett_problem_desc *probs, const gett_batch_op
 int gett_batch_launch(gett_batch *b, void *stream);
 int gett_batch_launch_graph(gett_batch *b, void *stream);
 int gett_batch_get_info(const gett_batch *b, gett_batch_info *info);
-/* Autotuner measurement: times every problem of the batch alone (its own
- * tiles, `reps` back-to-back launches of the persistent kernel between two
- * CUDA events on an internal stream) and writes the mean milliseconds per
- * launch to ms_out[i] (0 for problems with nothing to compute).
- * Synchronous; the problems' C buffers are updated reps times each. */
-int gett_batch_profile(gett_batch *b, int reps, float *ms_out);
+/* Autotuner measurement: times every problem of the batch on its own
+ * (`reps` back-to-back launches of the persistent kernel between two CUDA
+ * events on an internal stream) and writes the mean milliseconds to
+ * ms_out[i] (0 for problems with nothing to compute).  mode 0: the problem's
+ * tiles alone (latency).  mode 1: the problem's tiles repeated until every
+ * persistent CTA gets several, time divided by the repeat count (its cost
+ * inside a full batch).  Synchronous; C buffers are updated each run. */
+int gett_batch_profile(gett_batch *b, int reps, int mode, float *ms_out);
 int gett_batch_destroy(gett_batch *b);
 
 #ifdef __cplusplus

@@ -50,7 +50,7 @@ def _bind():
         getattr(L, n).restype = ctypes.c_int
     L.gett_batch_get_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(BatchInfo)]
     L.gett_batch_destroy.argtypes = [ctypes.c_void_p]
-    L.gett_batch_profile.argtypes = [ctypes.c_void_p, ctypes.c_int, _fp]
+    L.gett_batch_profile.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _fp]
     L.gett_batch_profile.restype = ctypes.c_int
     L.gett_batch_num_configs.restype = ctypes.c_int
     L.gett_batch_heuristic_config.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
@@ -124,10 +124,11 @@ class Batch:
         fn = L.gett_batch_launch_graph if graph else L.gett_batch_launch
         gett.check(fn(self.h, ctypes.c_void_p(int(stream or 0))))
 
-    def profile(self, reps=3) -> np.ndarray:
-        """Mean ms per launch of each problem run alone (0 for empty ones)."""
+    def profile(self, reps=3, throughput=True) -> np.ndarray:
+        """Mean ms of each problem on its own (0 for empty ones): its cost in
+        a full GPU (throughput=True) or its latency alone."""
         out = np.zeros(max(self.n, 1), dtype=np.float32)
-        gett.check(_bind().gett_batch_profile(self.h, int(reps), _f(out)))
+        gett.check(_bind().gett_batch_profile(self.h, int(reps), 1 if throughput else 0, _f(out)))
         return out[: self.n]
 
     def info(self) -> dict:

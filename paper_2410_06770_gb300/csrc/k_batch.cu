@@ -102,8 +102,10 @@ constexpr int smem_ints()
     return m;
 }
 
+// Work item i is work[i % wrap]; normal launches pass wrap == nwork, the
+// autotuner's throughput mode replicates one problem's items to fill the GPU.
 __global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *__restrict__ probs, const uint2 *__restrict__ work,
-                                                   int64_t nwork, const int64_t *__restrict__ tables,
+                                                   int64_t nwork, int64_t wrap, const int64_t *__restrict__ tables,
                                                    unsigned long long *counter)
 {
     __shared__ float smem_f[smem_floats()];
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *
         const unsigned long long it = s_item;
         __syncthreads();
         if (it >= (unsigned long long)nwork) break;
-        const uint2 w = work[it];
+        const uint2 w = work[it % (unsigned long long)wrap];
         const BatchProb pr = probs[w.x];
         const int key = pr.cfg * 2 + pr.dtype;
         switch (key) {
@@ -464,7 +466,7 @@ static cudaError_t enqueue(gett_batch *b, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess || b->nwork == 0) return e;
     const int ctas = (int)std::min<int64_t>(b->ctas, b->nwork);
-    batch_kernel<<<ctas, BT, 0, s>>>(b->d_probs, b->d_work, b->nwork, b->d_tables, b->d_counter);
+    batch_kernel<<<ctas, BT, 0, s>>>(b->d_probs, b->d_work, b->nwork, b->nwork, b->d_tables, b->d_counter);
     if (b->nreduce > 0)
         batch_reduce_kernel<<<std::min(b->nreduce, b->ctas), 256, 0, s>>>(b->d_probs, b->d_reduce, b->nreduce,
                                                                           b->d_tables);
@@ -504,9 +506,9 @@ extern "C" int gett_batch_launch_graph(gett_batch *b, void *stream)
     return GETT_OK;
 }
 
-extern "C" int gett_batch_profile(gett_batch *b, int reps, float *ms_out)
+extern "C" int gett_batch_profile(gett_batch *b, int reps, int mode, float *ms_out)
 {
-    if (!b || reps <= 0 || !ms_out) return GETT_ERR_ARG;
+    if (!b || reps <= 0 || !ms_out || (mode != 0 && mode != 1)) return GETT_ERR_ARG;
     cudaStream_t s;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -521,11 +523,15 @@ extern "C" int gett_batch_profile(gett_batch *b, int reps, float *ms_out)
         const int64_t cnt = b->prob_count[i];
         if (cnt == 0) continue;
         const uint2 *w = b->d_work_by_problem + b->prob_start[i];
-        const int ctas = (int)std::min<int64_t>(b->ctas, cnt);
+        // throughput mode: enough copies of the problem's items to give every
+        // persistent CTA several, so the time reflects its cost in a full GPU
+        const int64_t copies = mode == 1 ? std::min<int64_t>(64, std::max<int64_t>(1, (4LL * b->ctas + cnt - 1) / cnt)) : 1;
+        const int64_t items = cnt * copies;
+        const int ctas = (int)std::min<int64_t>(b->ctas, items);
         const int red = b->reduce_of[i];
         auto one = [&] {
             cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
-            batch_kernel<<<ctas, BT, 0, s>>>(b->d_probs, w, cnt, b->d_tables, b->d_counter);
+            batch_kernel<<<ctas, BT, 0, s>>>(b->d_probs, w, items, cnt, b->d_tables, b->d_counter);
             if (red >= 0) batch_reduce_kernel<<<1, 256, 0, s>>>(b->d_probs, b->d_reduce + red, 1, b->d_tables);
         };
         one();  // warm-up
@@ -535,7 +541,7 @@ extern "C" int gett_batch_profile(gett_batch *b, int reps, float *ms_out)
         e = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        ms_out[i] = ms / reps;
+        ms_out[i] = ms / reps / (float)copies;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -6,10 +6,11 @@
 1. Draws contraction signatures from the batched workload's distribution
    (ranks 2-5, extents up to --max-ext, 0-3 contracted modes, 25 % padded,
    fp32/bf16 operands, <= 2^18 elements per tensor).
-2. Autotuner: times every problem alone with every tile configuration of the
-   batched kernel (gett_batch_profile: CUDA events around back-to-back
-   launches) -> a table of times; the exhaustive best configuration is the
-   tuned choice.
+2. Autotuner: times every problem with every tile configuration of the
+   batched kernel (gett_batch_profile in throughput mode: the problem's tiles
+   repeated until the GPU is full, CUDA events around back-to-back launches,
+   time per copy) -> a table of costs; the exhaustive best configuration is
+   the tuned choice.
 3. Learned planner: features of each signature (gett_problem_features) ->
    MLP predicting normalised log times of all configurations, trained on the
    GPU by the library's own kernels (gett_mlp_fit).
