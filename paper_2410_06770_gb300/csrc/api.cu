@@ -82,6 +82,7 @@ cudaError_t run_family(const Plan &p, DType t, const Choice &ch, const void *A, 
     size_t ws_bytes = 0;
     if (ch.family == GETT_FAMILY_DENSE) ws_bytes = dense_workspace_bytes(p, t, ch.config, ch.split_k);
     else if (ch.family == GETT_FAMILY_REDUCE) ws_bytes = reduce_workspace_bytes(p, t, st.sms);
+    else if (ch.family == GETT_FAMILY_SKINNY) ws_bytes = skinny_workspace_bytes(p);
     else if (ch.family == GETT_FAMILY_TC)
         ws_bytes = ch.algo == GETT_ALGO_OZAKI_BF16 ? ozaki_workspace_bytes(p, ch.moduli)
                                                    : tc_split_workspace_bytes(p, ch.algo);
@@ -95,6 +96,7 @@ cudaError_t run_family(const Plan &p, DType t, const Choice &ch, const void *A, 
     case GETT_FAMILY_DENSE: e = launch_dense(p, t, A, B, C, ch.config, ch.split_k, ws, s); break;
     case GETT_FAMILY_OUTER: e = launch_outer(p, t, A, B, C, st.sms, s); break;
     case GETT_FAMILY_REDUCE: e = launch_reduce(p, t, A, B, C, st.sms, ws, s); break;
+    case GETT_FAMILY_SKINNY: e = launch_skinny(p, t, A, B, C, st.sms, ws, s); break;
     case GETT_FAMILY_TC:
         e = ch.algo == GETT_ALGO_OZAKI_BF16 ? launch_ozaki(p, ch.moduli, A, B, C, ws, st.sms, st.err, s)
                                             : launch_tc_split(p, t, ch.algo, A, B, C, ws, st.sms, st.err, s);

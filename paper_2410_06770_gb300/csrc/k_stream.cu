@@ -1,11 +1,19 @@
 // k_stream.cu -- HBM-streaming kernels for low-intensity contractions.
 //
 // OUTER: no contracted mode of extent > 1 (the thesis's "nothing
-// contraction", Sec. 7): C[m,n] += A[m] * B[n].  Every C element is read and
-// written once, so the kernel is bound by HBM bandwidth.  C is walked along
-// its smallest-increment mode (the first mode of whichever class holds it),
-// in runs of that mode; the operand that varies along the run is read along
-// the same index, the other operand is one value per run.
+// contraction", Sec. 7): C[m,n] += A[m] * B[n]; also short sums (K <= 8):
+// C[m,n] += sum_k A[m,k] B[k,n].  Every C element is read and written once,
+// so the kernel is bound by HBM bandwidth.  C is walked along its
+// smallest-increment mode (the first mode of whichever class holds it), in
+// runs of that mode; the operand that varies along the run is read along the
+// same index (once per k), the other operand is K values per run held in
+// registers.
+//
+// SKINNY: one free class of at most 8 indices and a long sum (matrix-vector
+// like).  Each of the (up to 8) short-class outputs of a long-class row is
+// accumulated in registers; when the long operand's contracted index has the
+// smaller increment a warp reduces one row (lanes along k, warp shuffles),
+// otherwise each thread reduces one row (threads along the row index).
 //
 // REDUCE: few output elements and long sums (the "scalar contraction" of
 // Sec. 7 and its neighbours).  Pass 1 splits the flat contracted index
@@ -24,6 +32,8 @@ namespace gett {
 
 namespace {
 
+constexpr int OUTER_MAX_K = 8;
+
 struct OuterParams {
     const void *X;  // operand varying along the run
     const void *Y;  // operand fixed along the run
@@ -33,6 +43,9 @@ struct OuterParams {
     int64_t e0, sx0, sc0;
     int64_t nxr, ny;
     int64_t chunk, nchunks, items;
+    int nk;                       // contracted length (1 for a pure outer product)
+    int64_t kx[OUTER_MAX_K];      // offsets of contracted index k in X
+    int64_t ky[OUTER_MAX_K];      // and in Y
 };
 
 template <class T, int NT>
@@ -53,30 +66,113 @@ __global__ void __launch_bounds__(NT) outer_kernel(OuterParams p)
         int64_t ox, ocx, oy, ocy;
         decode2(p.xr, ixr, ox, ocx);
         decode2(p.y, iy, oy, ocy);
-        const Acc yv = R::load(Y + oy);
+        Acc yv[OUTER_MAX_K];
+#pragma unroll
+        for (int k = 0; k < OUTER_MAX_K; ++k) yv[k] = k < p.nk ? R::load(Y + oy + p.ky[k]) : R::zero();
         const T *xb = X + ox;
         Out *cb = C + ocx + ocy;
         const int64_t x0 = c * p.chunk;
         const int64_t x1 = min(p.e0, x0 + p.chunk);
         for (int64_t x = x0 + threadIdx.x; x < x1; x += U * NT) {
-            Acc xv[U], cv[U];
+            Acc cv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 int64_t xx = x + u * NT;
-                if (xx < x1) {
-                    xv[u] = R::load(xb + xx * p.sx0);
-                    cv[u] = R::load_c(cb + xx * p.sc0);
+                if (xx < x1) cv[u] = R::load_c(cb + xx * p.sc0);
+            }
+            for (int k = 0; k < p.nk; ++k) {
+                Acc xv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    int64_t xx = x + u * NT;
+                    if (xx < x1) xv[u] = R::load(xb + xx * p.sx0 + p.kx[k]);
                 }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (x + u * NT < x1) R::mac(cv[u], xv[u], yv[k]);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 int64_t xx = x + u * NT;
-                if (xx < x1) {
-                    R::mac(cv[u], xv[u], yv);
-                    R::store_c(cb + xx * p.sc0, cv[u]);
-                }
+                if (xx < x1) R::store_c(cb + xx * p.sc0, cv[u]);
             }
         }
+    }
+}
+
+constexpr int SKINNY_MAX_S = 8;
+
+struct SkinnyParams {
+    const void *X;  // operand of the long free class (R rows)
+    const void *Y;  // operand of the short class (S <= 8 columns)
+    void *C;
+    const int64_t *rowX, *rowC;   // [R] offsets of the long class in X and C
+    const int64_t *kX, *kY;       // [K] offsets of the contracted class
+    int64_t colY[SKINNY_MAX_S], colC[SKINNY_MAX_S];
+    int64_t R, K;
+    int S;
+};
+
+// one warp per row: lanes stride over k
+template <class T>
+__global__ void __launch_bounds__(256) skinny_warp_kernel(SkinnyParams p)
+{
+    using Rt = Tr<T>;
+    using Acc = typename Rt::Acc;
+    using Out = typename Rt::Out;
+    const T *X = static_cast<const T *>(p.X);
+    const T *Y = static_cast<const T *>(p.Y);
+    Out *C = static_cast<Out *>(p.C);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < p.R; r += nwarps) {
+        Acc acc[SKINNY_MAX_S];
+#pragma unroll
+        for (int s = 0; s < SKINNY_MAX_S; ++s) acc[s] = Rt::zero();
+        const T *xr = X + p.rowX[r];
+        for (int64_t k = lane; k < p.K; k += 32) {
+            const Acc xv = Rt::load(xr + p.kX[k]);
+            const int64_t yk = p.kY[k];
+#pragma unroll
+            for (int s = 0; s < SKINNY_MAX_S; ++s)
+                if (s < p.S) Rt::mac(acc[s], xv, Rt::load(Y + p.colY[s] + yk));
+        }
+#pragma unroll
+        for (int s = 0; s < SKINNY_MAX_S; ++s) {
+            if (s >= p.S) break;
+            Acc v = acc[s];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v = Rt::add(v, shfl_down(v, d));
+            if (lane == 0) Rt::store_add(C + p.rowC[r] + p.colC[s], v);
+        }
+    }
+}
+
+// one thread per row: threads stride over rows, each loops over k
+template <class T>
+__global__ void __launch_bounds__(256) skinny_thread_kernel(SkinnyParams p)
+{
+    using Rt = Tr<T>;
+    using Acc = typename Rt::Acc;
+    const T *X = static_cast<const T *>(p.X);
+    const T *Y = static_cast<const T *>(p.Y);
+    typename Rt::Out *C = static_cast<typename Rt::Out *>(p.C);
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < p.R; r += (int64_t)gridDim.x * blockDim.x) {
+        Acc acc[SKINNY_MAX_S];
+#pragma unroll
+        for (int s = 0; s < SKINNY_MAX_S; ++s) acc[s] = Rt::zero();
+        const T *xr = X + p.rowX[r];
+        for (int64_t k = 0; k < p.K; ++k) {
+            const Acc xv = Rt::load(xr + p.kX[k]);
+            const int64_t yk = p.kY[k];
+#pragma unroll
+            for (int s = 0; s < SKINNY_MAX_S; ++s)
+                if (s < p.S) Rt::mac(acc[s], xv, Rt::load(Y + p.colY[s] + yk));
+        }
+#pragma unroll
+        for (int s = 0; s < SKINNY_MAX_S; ++s)
+            if (s < p.S) Rt::store_add(C + p.rowC[r] + p.colC[s], acc[s]);
     }
 }
 
@@ -245,6 +341,20 @@ cudaError_t launch_outer(const Plan &pl, DType t, const void *A, const void *B, 
         p.xr.n = 0;
     }
     p.y = oth;
+    // contracted offsets (first mode fastest), at most OUTER_MAX_K of them
+    if (pl.K > OUTER_MAX_K) return cudaErrorInvalidValue;
+    p.nk = (int)pl.K;
+    for (int64_t k = 0; k < pl.K; ++k) {
+        int64_t r = k, oa = 0, ob = 0;
+        for (int i = 0; i < pl.k.n; ++i) {
+            const int64_t x = r % pl.k.ext[i];
+            r /= pl.k.ext[i];
+            oa += x * pl.k.s0[i];
+            ob += x * pl.k.s1[i];
+        }
+        p.kx[k] = run_in_m ? oa : ob;
+        p.ky[k] = run_in_m ? ob : oa;
+    }
     p.nxr = prod(p.xr);
     p.ny = prod(p.y);
     p.chunk = 8192;
@@ -256,6 +366,92 @@ cudaError_t launch_outer(const Plan &pl, DType t, const void *A, const void *B, 
     case DT_C32: return outer_typed<cf>(p, num_sms, s);
     case DT_C64: return outer_typed<zd>(p, num_sms, s);
     case DT_BF16: return outer_typed<uint16_t>(p, num_sms, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+size_t skinny_workspace_bytes(const Plan &p)
+{
+    return sizeof(int64_t) * 2 * (size_t)(p.M + p.N + p.K) + 256;
+}
+
+bool skinny_applicable(const Plan &p)
+{
+    return std::min(p.M, p.N) <= SKINNY_MAX_S && p.K > 1;
+}
+
+template <class T>
+cudaError_t skinny_typed(const SkinnyParams &p, bool warp_per_row, int num_sms, cudaStream_t s)
+{
+    if (warp_per_row) {
+        int64_t blocks = std::min<int64_t>((p.R + 7) / 8, (int64_t)num_sms * 8);
+        skinny_warp_kernel<T><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(p);
+    } else {
+        int64_t blocks = std::min<int64_t>((p.R + 255) / 256, (int64_t)num_sms * 8);
+        skinny_thread_kernel<T><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_skinny(const Plan &pl, DType t, const void *A, const void *B, void *C, int num_sms, void *ws,
+                          cudaStream_t s)
+{
+    if (!skinny_applicable(pl)) return cudaErrorInvalidValue;
+    int64_t *tab = static_cast<int64_t *>(ws);
+    int64_t *rowA = tab, *rowC = rowA + pl.M, *colB = rowC + pl.M, *colC = colB + pl.N;
+    int64_t *kA = colC + pl.N, *kB = kA + pl.K;
+    cudaError_t e = launch_build_tables(pl, rowA, rowC, colB, colC, kA, kB, s);
+    if (e != cudaSuccess) return e;
+    const size_t esz = dtype_size(t);
+    const char *Ab = static_cast<const char *>(A) + pl.offA * (int64_t)esz;
+    const char *Bb = static_cast<const char *>(B) + pl.offB * (int64_t)esz;
+    SkinnyParams p{};
+    p.C = static_cast<char *>(C) + pl.offC * (int64_t)out_size(t);
+    p.K = pl.K;
+    // the short class becomes the register-held columns
+    const bool short_is_n = pl.N <= pl.M;
+    const ModeList &sh = short_is_n ? pl.n : pl.m;
+    p.S = (int)(short_is_n ? pl.N : pl.M);
+    for (int64_t j = 0; j < p.S; ++j) {
+        int64_t r = j, a = 0, c = 0;
+        for (int i = 0; i < sh.n; ++i) {
+            const int64_t x = r % sh.ext[i];
+            r /= sh.ext[i];
+            a += x * sh.s0[i];
+            c += x * sh.s1[i];
+        }
+        p.colY[j] = a;
+        p.colC[j] = c;
+    }
+    if (short_is_n) {
+        p.X = Ab;
+        p.Y = Bb;
+        p.rowX = rowA;
+        p.rowC = rowC;
+        p.kX = kA;
+        p.kY = kB;
+        p.R = pl.M;
+    } else {
+        p.X = Bb;
+        p.Y = Ab;
+        p.rowX = colB;
+        p.rowC = colC;
+        p.kX = kB;
+        p.kY = kA;
+        p.R = pl.N;
+    }
+    // lanes along k when the long operand is contiguous along k
+    const ModeList &lg = short_is_n ? pl.m : pl.n;
+    const int64_t s_row = lg.n ? (lg.s0[0] < 0 ? -lg.s0[0] : lg.s0[0]) : 0;
+    const int64_t s_k = pl.k.n ? (short_is_n ? pl.k.s0[0] : pl.k.s1[0]) : 0;
+    const int64_t sk = s_k < 0 ? -s_k : s_k;
+    const bool warp_per_row = s_row == 0 || (sk != 0 && sk < s_row);
+    switch (t) {
+    case DT_F32: return skinny_typed<float>(p, warp_per_row, num_sms, s);
+    case DT_F64: return skinny_typed<double>(p, warp_per_row, num_sms, s);
+    case DT_C32: return skinny_typed<cf>(p, warp_per_row, num_sms, s);
+    case DT_C64: return skinny_typed<zd>(p, warp_per_row, num_sms, s);
+    case DT_BF16: return skinny_typed<uint16_t>(p, warp_per_row, num_sms, s);
     }
     return cudaErrorInvalidValue;
 }

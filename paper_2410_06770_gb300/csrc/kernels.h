@@ -21,9 +21,16 @@ cudaError_t launch_build_tables(const Plan &p, int64_t *rowA, int64_t *rowC, int
                                 int64_t *kA, int64_t *kB, cudaStream_t s);
 
 // ---- streaming kernels (k_stream.cu) ----
-// OUTER: no contracted mode of extent > 1 (K == 1).
+// OUTER: no contracted mode of extent > 1 (K == 1), or a short sum.
 cudaError_t launch_outer(const Plan &p, DType t, const void *A, const void *B, void *C, int num_sms,
                          cudaStream_t s);
+// OUTER also covers short sums: K <= OUTER_MAX_SUM.
+constexpr int OUTER_MAX_SUM = 8;
+// SKINNY: one free class of at most 8 indices, K > 1.
+bool skinny_applicable(const Plan &p);
+size_t skinny_workspace_bytes(const Plan &p);
+cudaError_t launch_skinny(const Plan &p, DType t, const void *A, const void *B, void *C, int num_sms, void *ws,
+                          cudaStream_t s);
 // REDUCE: few outputs (M*N small), long sums; deterministic two-pass.
 size_t reduce_workspace_bytes(const Plan &p, DType t, int num_sms);
 cudaError_t launch_reduce(const Plan &p, DType t, const void *A, const void *B, void *C, int num_sms,

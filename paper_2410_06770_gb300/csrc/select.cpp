@@ -3,6 +3,8 @@
 // Heuristic (the fixed planner every other selector falls back to):
 //  * K == 1 (no contracted extent > 1): OUTER streaming kernel;
 //  * at most 32 outputs and K >= 8192: REDUCE streaming kernel;
+//  * K <= 8 with at least 2^16 outputs: OUTER (short sums);
+//  * one free class of at most 8 indices: SKINNY streaming kernel;
 //  * otherwise the DENSE tiled kernel with the largest tile that still gives
 //    at least one tile per SM, else the smallest tile plus split-K so the
 //    grid covers the SMs.
@@ -28,6 +30,16 @@ Choice heuristic_choice(const Plan &p, DType t, int num_sms)
     const int64_t O = p.M * p.N;
     if (O <= 32 && p.K >= 8192) {
         c.family = GETT_FAMILY_REDUCE;
+        return c;
+    }
+    // short sums over a large output stream C at HBM speed
+    if (p.K <= OUTER_MAX_SUM && O >= (1 << 16)) {
+        c.family = GETT_FAMILY_OUTER;
+        return c;
+    }
+    // matrix-vector like: one free class of at most 8 indices
+    if (skinny_applicable(p) && std::max(p.M, p.N) * p.K >= (1 << 16)) {
+        c.family = GETT_FAMILY_SKINNY;
         return c;
     }
     if (t == DT_BF16 && p.M >= 128 && p.N >= 128 && p.K >= 64) {
@@ -102,7 +114,8 @@ int choose(const Plan &p, DType t, const gett_options *opt, int num_sms, Choice 
             bool ok = false;
             switch (f.family) {
             case GETT_FAMILY_DENSE: ok = dense_config_valid(t, f.config); break;
-            case GETT_FAMILY_OUTER: ok = p.K == 1; break;
+            case GETT_FAMILY_OUTER: ok = p.K <= OUTER_MAX_SUM; break;
+            case GETT_FAMILY_SKINNY: ok = skinny_applicable(p); break;
             case GETT_FAMILY_REDUCE: ok = p.M * p.N <= 4096; break;
             default: ok = false;
             }

@@ -141,3 +141,31 @@ def test_empty_and_degenerate():
     p = synth.make_problem(sig, np.random.default_rng(2), np.float64, "int", c_dist="int")
     got, _ = run_gpu("d", p)
     assert np.array_equal(got, p.C)
+
+
+STREAM_SHAPES = {
+    # short sum (K = 3) over a large output: OUTER with a register-held K
+    "short_sum": (synth.Signature((300, 3, 40), (3, 25), (1,), (0,), (0, 2, 1)), ("contig", "padded", "contig")),
+    # matrix-vector with the long operand contiguous along the row index
+    "gemv_rows": (synth.Signature((3000, 45), (45, 3), (1,), (0,), (0, 1)), ("contig", "negative", "padded")),
+    # matrix-vector with the long operand contiguous along k (warp per row)
+    "gemv_k": (synth.Signature((3000, 45), (45, 1), (1,), (0,), (0, 1)), ("rowmajor", "contig", "contig")),
+    # short class on the A side, two contracted modes
+    "left_skinny": (synth.Signature((2, 9, 7), (7, 9, 900), (1, 2), (1, 0), (1, 0)), ("padded", "rowmajor", "negative")),
+}
+
+
+@pytest.mark.parametrize("prefix", ("d", "s", "z", "c", "sb"))
+@pytest.mark.parametrize("name", sorted(STREAM_SHAPES))
+def test_streaming_short_sums_and_skinny(prefix, name):
+    sig, kinds = STREAM_SHAPES[name]
+    rng = np.random.default_rng(sum(map(ord, name)))
+    dtype = np.complex128 if prefix in ("z", "c") else np.float64
+    p = synth.make_problem(sig, rng, dtype, "uniform", kinds, "uniform")
+    q = problem_for(prefix, p)
+    family = "outer" if name == "short_sum" else "skinny"
+    got, rep = run_gpu(prefix, q, mode="ex", opts=gett.options(family=family))
+    assert rep["family_name"] == family
+    compare(prefix, q, got, oracle_ref(q))
+    got2, rep2 = run_gpu(prefix, q)  # the selector's own choice
+    compare(prefix, q, got2, oracle_ref(q))
