@@ -150,7 +150,18 @@ __global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict
     }
 }
 
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // residues of round(x * 2^shift) for every modulus, packed [L][rows][ld] bf16.
+// Tiles of 32 rows x 64 k are gathered with cp.async into a double buffer, so
+// the next tile's loads are in flight while the current one is converted.
 // Each thread converts two neighbouring k of one row and stores both bf16
 // residues of a modulus with one 32-bit store (ld is even, k0 multiple of 64).
 template <int ROW_FAST, int L>
@@ -160,34 +171,37 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
                                                        const unsigned long long *__restrict__ maxbits, int kbits,
                                                        OzConsts c, uint16_t *__restrict__ out, int64_t ld)
 {
-    __shared__ uint64_t tile[TR][TKP + 1];
-    __shared__ int64_t srow[TR];
-    __shared__ int sshift[TR];
-    __shared__ int64_t sk[TKP];
+    __shared__ uint64_t tile[2][TR][TKP + 1];
+    __shared__ int sshift[2][TR];
     const int64_t tiles_k = (K + TKP - 1) / TKP;
     const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
     const int64_t plane = rows * ld;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    auto issue = [&](int64_t t, int buf) {
         const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
-        __syncthreads();
-        if (threadIdx.x < TR) {
-            const bool in = r0 + threadIdx.x < rows;
-            srow[threadIdx.x] = in ? rowT[r0 + threadIdx.x] : 0;
-            sshift[threadIdx.x] = in ? shift_for(maxbits[r0 + threadIdx.x], kbits) : 0;
-        }
-        if (threadIdx.x < TKP) sk[threadIdx.x] = k0 + threadIdx.x < K ? kT[k0 + threadIdx.x] : 0;
-        __syncthreads();
+        if (threadIdx.x < TR)
+            sshift[buf][threadIdx.x] = r0 + threadIdx.x < rows ? shift_for(maxbits[r0 + threadIdx.x], kbits) : 0;
 #pragma unroll
         for (int j = 0; j < TR * TKP / PT; ++j) {
-            int e = threadIdx.x + j * PT;
+            const int e = threadIdx.x + j * PT;
             int r, k;
             if (ROW_FAST) { r = e % TR; k = e / TR; }
             else { k = e % TKP; r = e / TKP; }
-            uint64_t bits = 0;
-            if (r0 + r < rows && k0 + k < K) bits = (uint64_t)__double_as_longlong(__ldg(src + srow[r] + sk[k]));
-            tile[r][k] = bits;
+            const bool valid = r0 + r < rows && k0 + k < K;
+            const double *g = valid ? src + rowT[r0 + r] + kT[k0 + k] : src;
+            cp_async8(&tile[buf][r][k], g, valid);
         }
+        cp_async_commit();
+    };
+    int buf = 0;
+    int64_t t = blockIdx.x;
+    if (t < ntiles) issue(t, 0);
+    for (; t < ntiles; t += gridDim.x) {
+        const int64_t tn = t + gridDim.x;
+        if (tn < ntiles) issue(tn, buf ^ 1);
+        else cp_async_commit();  // empty group keeps the group count uniform
+        cp_async_wait1();
         __syncthreads();
+        const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
 #pragma unroll
         for (int j = 0; j < TR * TKP / (2 * PT); ++j) {
             const int e = threadIdx.x + j * PT;
@@ -199,8 +213,8 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
             float l0[2], l1[2], l2[2], l3[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const uint64_t bits = tile[r][k + u];
-                const uint64_t v = scaled_int(bits & 0x7FFFFFFFFFFFFFFFull, sshift[r]);
+                const uint64_t bits = tile[buf][r][k + u];
+                const uint64_t v = scaled_int(bits & 0x7FFFFFFFFFFFFFFFull, sshift[buf][r]);
                 const float sg = (bits >> 63) ? -1.f : 1.f;
                 l0[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)(v & 0x1FFF)) - 8388608.0f);
                 l1[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)((v >> 13) & 0x1FFF)) - 8388608.0f);
@@ -213,7 +227,7 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
                 float x[2];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    // |s| <= 127 * 3 * 8191 + 8191 < 2^22: exact; nearest rounding of
+                    // |s| <= 127 * 3 * 8191 + 8192 < 2^22: exact; nearest rounding of
                     // s / p is exact for odd p, so the residue lies in [-(p-1)/2, (p-1)/2]
                     const float sum = fmaf(l3[u], c.c39[l], fmaf(l2[u], c.c26[l], fmaf(l1[u], c.c13[l], l0[u])));
                     x[u] = fmaf(-round_mul(sum, c.invp[l]), c.pf[l], sum);
@@ -223,6 +237,8 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
                 o[(l * plane) / 2] = __byte_perm(__float_as_uint(x[0]), __float_as_uint(x[1]), 0x7632);
             }
         }
+        __syncthreads();
+        buf ^= 1;
     }
 }
 
