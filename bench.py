@@ -364,6 +364,7 @@ def gpu_arm(args, dist: Dist):
         torch.cuda.empty_cache()
         result["forms"] = measure_forms(args.workload)
         result["forms"].update(measure_split_forms())
+        result["forms"].update(measure_streaming_forms())
         result["forms"]["batched"] = measure_batched()
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         v, cores, desc, dt = oracle_sample(p, args.cpu_seconds)
@@ -604,6 +605,45 @@ def measure_batched(n=4096):
         out["batched_learned"] = tune.throughput(probs, "learned")
         gb.clear_model()
     out["speedup_batched_vs_per_call"] = out["per_call"]["ms"] / out["batched_heuristic"]["ms"]
+    return out
+
+
+def measure_streaming_forms():
+    """HBM-bound kernels beyond the outer product: a full inner product of two
+    128^4 tensors (REDUCE, 4.3 GB read) and a matrix-vector contraction
+    A(16384, 16384) x B(16384, 2) (SKINNY, 2.1 GB read)."""
+    import torch
+    from paper_2410_06770_gb300 import gett, synth
+    mp = measured_peaks()
+    bw = mp.get("hbm_gbs", 6800.0)
+    out = {}
+    stream = torch.cuda.current_stream()
+    cases = {
+        "inner_product": (synth.Signature((128,) * 4, (128,) * 4, (0, 1, 2, 3), (0, 1, 2, 3), ()), "reduce"),
+        "gemv": (synth.Signature((16384, 16384), (16384, 2), (1,), (0,), (0, 1)), "skinny"),
+    }
+    for name, (sig, fam) in cases.items():
+        la, lb, lc = synth.layout_contiguous(sig.exta), synth.layout_contiguous(sig.extb), synth.layout_contiguous(sig.extc())
+        g = torch.Generator(device="cuda")
+        g.manual_seed(9)
+        dA = torch.rand(la.size, dtype=torch.float64, device="cuda", generator=g)
+        dB = torch.rand(lb.size, dtype=torch.float64, device="cuda", generator=g)
+        dC = torch.zeros(lc.size, dtype=torch.float64, device="cuda")
+        a = dict(RANKA=len(sig.exta), EXTA=sig.exta, INCA=la.inc, RANKB=len(sig.extb), EXTB=sig.extb,
+                 INCB=lb.inc, CONTS=sig.conts, CONTA=sig.conta, CONTB=sig.contb, PERM=sig.perm, INCC=lc.inc)
+
+        def call():
+            return gett.xgett("d", a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"], a["INCB"], dB,
+                              a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], dC, mode="ex",
+                              stream=stream.cuda_stream)
+        _, rep = call()
+        best, _ = time_calls(call, 5)
+        nbytes = 8.0 * (la.numel + lb.numel + 2 * lc.numel)
+        out[name] = {"family": rep["family_name"], "ms": best, "gbs": nbytes / (best * 1e-3) / 1e9,
+                     "hbm_frac": nbytes / (best * 1e-3) / 1e9 / bw,
+                     "shape": f"A{sig.exta} x B{sig.extb}, CONTS={sig.conts}"}
+        del dA, dB, dC
+        torch.cuda.empty_cache()
     return out
 
 
