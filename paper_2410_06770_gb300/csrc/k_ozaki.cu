@@ -45,8 +45,8 @@ struct OzConsts {
     float pf[OZ_MAX_L];
     float invp[OZ_MAX_L];
     float c13[OZ_MAX_L], c26[OZ_MAX_L], c39[OZ_MAX_L];  // 2^13, 2^26, 2^39 mod p, symmetric
-    int inv[OZ_MAX_L][OZ_MAX_L];            // inv[i][j] = p_j^{-1} mod p_i (j < i)
-    float invf[OZ_MAX_L][OZ_MAX_L];         // the same as floats
+    float wpre[OZ_MAX_L][OZ_MAX_L];         // (p_0 ... p_{j-1}) mod p_i, symmetric (j < i)
+    float ipre[OZ_MAX_L];                   // (p_0 ... p_{i-1})^{-1} mod p_i
     int half[OZ_MAX_L];                     // mixed-radix digits of (P-1)/2
     float halff[OZ_MAX_L];
 };
@@ -96,41 +96,65 @@ __device__ __forceinline__ uint64_t scaled_int(uint64_t bits, int s)
     return (mant + (1ull << (rs - 1))) >> rs;
 }
 
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Row maxima of |x| (as bit patterns) over K, for the scaling.  Tiles of 32
+// rows x 64 k are gathered with cp.async into a double buffer; each warp
+// reduces its values in registers / with shuffles before one shared atomic.
 template <int ROW_FAST>
 __global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict__ src,
                                                        const int64_t *__restrict__ rowT,
                                                        const int64_t *__restrict__ kT, int64_t rows, int64_t K,
                                                        unsigned long long *__restrict__ maxbits)
 {
+    __shared__ uint64_t tile[2][TR][TKP + 1];
     __shared__ unsigned long long smax[TR];
-    __shared__ int64_t srow[TR];
-    __shared__ int64_t sk[TKP];
     const int64_t tiles_k = (K + TKP - 1) / TKP;
     const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    auto issue = [&](int64_t t, int buf) {
         const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
-        __syncthreads();
-        if (threadIdx.x < TR) {
-            srow[threadIdx.x] = r0 + threadIdx.x < rows ? rowT[r0 + threadIdx.x] : 0;
-            smax[threadIdx.x] = 0;
+#pragma unroll
+        for (int j = 0; j < TR * TKP / PT; ++j) {
+            const int e = threadIdx.x + j * PT;
+            int r, k;
+            if (ROW_FAST) { r = e % TR; k = e / TR; }
+            else { k = e % TKP; r = e / TKP; }
+            const bool valid = r0 + r < rows && k0 + k < K;
+            const double *g = valid ? src + rowT[r0 + r] + kT[k0 + k] : src;
+            cp_async8(&tile[buf][r][k], g, valid);
         }
-        if (threadIdx.x < TKP) sk[threadIdx.x] = k0 + threadIdx.x < K ? kT[k0 + threadIdx.x] : 0;
+        cp_async_commit();
+    };
+    int buf = 0;
+    int64_t t = blockIdx.x;
+    if (t < ntiles) issue(t, 0);
+    for (; t < ntiles; t += gridDim.x) {
+        const int64_t tn = t + gridDim.x;
+        if (tn < ntiles) issue(tn, buf ^ 1);
+        else cp_async_commit();
+        if (threadIdx.x < TR) smax[threadIdx.x] = 0;
+        cp_async_wait1();
         __syncthreads();
-        // each thread's elements of one row are reduced in registers first:
-        // row-fast mapping -> all of a thread's elements share one row;
-        // k-fast mapping -> a warp covers 32 k of one row per step
+        const int64_t r0 = (t / tiles_k) * TR;
+        // row-fast mapping: a thread's elements share one row; otherwise a warp
+        // covers 32 k of one row per step
         unsigned long long mine = 0;
         int myrow = 0;
 #pragma unroll
         for (int j = 0; j < TR * TKP / PT; ++j) {
-            int e = threadIdx.x + j * PT;
+            const int e = threadIdx.x + j * PT;
             int r, k;
             if (ROW_FAST) { r = e % TR; k = e / TR; }
             else { k = e % TKP; r = e / TKP; }
-            unsigned long long b = 0;
-            if (r0 + r < rows && k0 + k < K)
-                b = (unsigned long long)__double_as_longlong(__ldg(src + srow[r] + sk[k])) & 0x7FFFFFFFFFFFFFFFull;
-            if ((b >> 52) == 0x7FF) b = 0;
+            unsigned long long b = tile[buf][r][k] & 0x7FFFFFFFFFFFFFFFull;
+            if ((b >> 52) == 0x7FF) b = 0;  // inf / nan do not set the scale
             if (ROW_FAST) {
                 mine = b > mine ? b : mine;
                 myrow = r;
@@ -147,17 +171,10 @@ __global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict
         __syncthreads();
         if (threadIdx.x < TR && r0 + threadIdx.x < rows && smax[threadIdx.x])
             atomicMax(&maxbits[r0 + threadIdx.x], smax[threadIdx.x]);
+        __syncthreads();
+        buf ^= 1;
     }
 }
-
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
-{
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem), "r"(valid ? 8 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // residues of round(x * 2^shift) for every modulus, packed [L][rows][ld] bf16.
 // Tiles of 32 rows x 64 k are gathered with cp.async into a double buffer, so
@@ -271,30 +288,29 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
     const int64_t MN = M * N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t m = i % M, n = i / M;
-        // Garner's mixed-radix digits, in fp32 holding exact small integers
-        // (every intermediate is an integer below 2^17)
+        // Garner's mixed-radix digits: X = v_0 + p_0 v_1 + p_0 p_1 v_2 + ...,
+        // v_a = (r_a - sum_{b<a} v_b (p_0..p_{b-1} mod p_a)) (p_0..p_{a-1})^{-1} mod p_a.
+        // fp32 holds every intermediate exactly: the prefix sum is at most
+        // 19 * 254 * 127 < 2^24, the reduced values are below 2^15.
         float v[L];
 #pragma unroll
         for (int l = 0; l < L; ++l) {
             // int8 -> float without a conversion instruction: r + 128 in [1, 255]
             // placed in the mantissa of 2^23
             const int r = (int)R[(int64_t)l * MN + i];
-            const float rf = __int_as_float(0x4B000000 | (r + 128)) - 8388736.0f;
-            v[l] = rf < 0.f ? rf + c.pf[l] : rf;
+            v[l] = __int_as_float(0x4B000000 | (r + 128)) - 8388736.0f;
         }
+        v[0] = v[0] < 0.f ? v[0] + c.pf[0] : v[0];
 #pragma unroll
         for (int a = 1; a < L; ++a) {
-            float t = v[a];
-            const float pa = c.pf[a];
-            const float ipa = c.invp[a];
+            float sum = v[a];
 #pragma unroll
-            for (int b = 0; b < a; ++b) {
-                const float d = t - v[b] + 2.f * pa;           // in (0, 3 pa)
-                const float x = d * c.invf[a][b];               // < 2^17, exact
-                float r = fmaf(-round_mul(x, ipa), pa, x);      // x mod pa, in (-pa, pa)
-                t = r < 0.f ? r + pa : r;
-            }
-            v[a] = t;
+            for (int b = 0; b < a; ++b) sum = fmaf(-v[b], c.wpre[a][b], sum);
+            const float pa = c.pf[a], ipa = c.invp[a];
+            const float t = fmaf(-round_mul(sum, ipa), pa, sum);      // in [-(pa-1)/2, (pa-1)/2]
+            const float x = t * c.ipre[a];                             // |x| < 2^15, exact
+            float d = fmaf(-round_mul(x, ipa), pa, x);
+            v[a] = d < 0.f ? d + pa : d;
         }
         // sign: compare with (P-1)/2 from the most significant digit
         int cmp = 0;
@@ -409,9 +425,12 @@ void oz_setup(int64_t K, int want_L, OzConsts *c)
         c->c13[i] = sym(m13);
         c->c26[i] = sym(m13 * m13);
         c->c39[i] = sym(m13 * m13 % p * m13);
+        long long pre = 1;  // (p_0 ... p_{j-1}) mod p
         for (int j = 0; j < OZ_MAX_L; ++j) {
-            c->inv[i][j] = (j < i) ? modinv(kOzModuli[j] % p, p) : 0;
-            c->invf[i][j] = (float)c->inv[i][j];
+            long long w = pre % p;
+            c->wpre[i][j] = (j < i) ? (float)(w > (p - 1) / 2 ? w - p : w) : 0.f;
+            if (j == i) c->ipre[i] = (float)(i == 0 ? 1 : modinv((int)pre, p));
+            if (j < i) pre = pre * (kOzModuli[j] % p) % p;
         }
     }
     // digits of (P-1)/2: long division of the digits (p_i - 1) by 2 from the top
