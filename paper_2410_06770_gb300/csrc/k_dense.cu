@@ -60,9 +60,11 @@ dense_kernel(DenseParams p)
     __shared__ Acc sB[2 * BK * BN];
     __shared__ int64_t sRowA[BM];
     __shared__ int64_t sColB[BN];
+    // column tiles fastest: the CTAs that share one row block of A run
+    // together, so A is fetched from DRAM about once
     const int tile = blockIdx.x;
-    const int tile_m = tile % p.tiles_m;
-    const int tile_n = tile / p.tiles_m;
+    const int tile_n = tile % p.tiles_n;
+    const int tile_m = tile / p.tiles_n;
     const int split = blockIdx.y;
     TileArgs a;
     a.A = p.A;
