@@ -272,6 +272,13 @@ const char *gett_status_string(int status);
  * wait gives up; synchronises the device.  GETT_OK or GETT_ERR_TIMEOUT. */
 int gett_device_status(void);
 int gett_version(void);              /* major*10000 + minor*100 + patch      */
+/* Failure-detection check (no counterpart in the thesis): launches one
+ * thread that waits, with a limit of `limit_cycles` SM clock cycles, on a
+ * device barrier that nothing completes.  The bounded wait gives up, records
+ * its code in the device error word and the kernel returns; the call then
+ * reads the word like gett_device_status and returns GETT_ERR_TIMEOUT, with
+ * the CUDA context still usable.  Synchronous. */
+int gett_check_wait_timeout(long long limit_cycles);
 
 #ifdef __cplusplus
 }

@@ -10,6 +10,7 @@
 #include "internal.h"
 #include "kernels.h"
 #include "select.h"
+#include "tc_gemm.h"
 
 namespace gett {
 
@@ -255,6 +256,21 @@ extern "C" int gett_device_status(void)
         return GETT_ERR_TIMEOUT;
     }
     return GETT_OK;
+}
+
+extern "C" int gett_check_wait_timeout(long long limit_cycles)
+{
+    gett::DevState *st = nullptr;
+    int rc = gett::dev_state(&st);
+    if (rc != GETT_OK) return rc;
+    if (limit_cycles <= 0) return GETT_ERR_ARG;
+    cudaError_t e = gett::launch_wait_timeout_probe(st->err, limit_cycles, (cudaStream_t)0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)0);
+    if (e != cudaSuccess) {
+        gett::set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    return gett_device_status();
 }
 
 extern "C" int gett_version(void) { return 100; }

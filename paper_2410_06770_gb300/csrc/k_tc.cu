@@ -229,6 +229,21 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
 }
 
+// Failure-detection check: one thread waits on an mbarrier whose phase
+// nothing completes (count 2, a single arrival), with a short limit; the
+// bounded wait gives up, records ERR_WAIT_FULL in the error word and the
+// kernel returns normally.  No fault, no trap, no endless loop.
+__global__ void wait_timeout_probe_kernel(int *err, long long limit)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 2);
+        tc::fence_barrier_init();
+        tc::mbar_arrive(&bar);  // one of the two expected arrivals: phase 0 never completes
+        tc::mbar_wait(&bar, 0, err, tc::ERR_WAIT_FULL, limit);
+    }
+}
+
 // ---- tensor maps ---------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -299,4 +314,12 @@ cudaError_t launch_tc_gemm(int mode, const void *Ap, const void *Bp, int64_t Z, 
     return cudaGetLastError();
 }
 
+}  // namespace gett
+
+namespace gett {
+cudaError_t launch_wait_timeout_probe(int *err, long long limit_cycles, cudaStream_t s)
+{
+    wait_timeout_probe_kernel<<<1, 32, 0, s>>>(err, limit_cycles);
+    return cudaGetLastError();
+}
 }  // namespace gett

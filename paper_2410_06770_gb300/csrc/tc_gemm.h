@@ -37,4 +37,7 @@ int64_t tc_ld(int64_t K);
 cudaError_t launch_tc_gemm(int mode, const void *Ap, const void *Bp, int64_t Z, const TcGemmParams &p,
                            cudaStream_t s);
 
+// Failure-detection check (see gett_check_wait_timeout).
+cudaError_t launch_wait_timeout_probe(int *err, long long limit_cycles, cudaStream_t s);
+
 }  // namespace gett
