@@ -151,7 +151,8 @@ typedef enum gett_algo {
     GETT_ALGO_DEFAULT = 0,    /* library's choice (native arithmetic)      */
     GETT_ALGO_NATIVE = 1,     /* arithmetic in the operand type            */
     GETT_ALGO_OZAKI_BF16 = 2, /* d/z: split-precision modular form on bf16 */
-                              /* tensor cores, fp64 recombination          */
+                              /* tensor cores, fp64 recombination (z: the  */
+                              /* real 2x2 block form of the complex sum)   */
     GETT_ALGO_BF16X3 = 3,     /* s/c: fp32 split into 2 bf16 pieces, 3     */
                               /* products on tensor cores                  */
     GETT_ALGO_BF16X6 = 4      /* s/c: 3 bf16 pieces, 6 products            */

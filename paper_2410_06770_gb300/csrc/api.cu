@@ -85,8 +85,8 @@ cudaError_t run_family(const Plan &p, DType t, const Choice &ch, const void *A, 
     else if (ch.family == GETT_FAMILY_REDUCE) ws_bytes = reduce_workspace_bytes(p, t, st.sms);
     else if (ch.family == GETT_FAMILY_SKINNY) ws_bytes = skinny_workspace_bytes(p);
     else if (ch.family == GETT_FAMILY_TC)
-        ws_bytes = ch.algo == GETT_ALGO_OZAKI_BF16 ? ozaki_workspace_bytes(p, ch.moduli)
-                                                   : tc_split_workspace_bytes(p, ch.algo);
+        ws_bytes = ch.algo != GETT_ALGO_OZAKI_BF16 ? tc_split_workspace_bytes(p, ch.algo)
+                   : (t == DT_C64 ? ozaki_complex_workspace_bytes(p, ch.moduli) : ozaki_workspace_bytes(p, ch.moduli));
     void *ws = nullptr;
     cudaError_t e = cudaSuccess;
     if (ws_bytes) {
@@ -99,8 +99,9 @@ cudaError_t run_family(const Plan &p, DType t, const Choice &ch, const void *A, 
     case GETT_FAMILY_REDUCE: e = launch_reduce(p, t, A, B, C, st.sms, ws, s); break;
     case GETT_FAMILY_SKINNY: e = launch_skinny(p, t, A, B, C, st.sms, ws, s); break;
     case GETT_FAMILY_TC:
-        e = ch.algo == GETT_ALGO_OZAKI_BF16 ? launch_ozaki(p, ch.moduli, A, B, C, ws, st.sms, st.err, s)
-                                            : launch_tc_split(p, t, ch.algo, A, B, C, ws, st.sms, st.err, s);
+        if (ch.algo != GETT_ALGO_OZAKI_BF16) e = launch_tc_split(p, t, ch.algo, A, B, C, ws, st.sms, st.err, s);
+        else if (t == DT_C64) e = launch_ozaki_complex(p, ch.moduli, A, B, C, ws, st.sms, st.err, s);
+        else e = launch_ozaki(p, ch.moduli, A, B, C, ws, st.sms, st.err, s);
         break;
     default: e = cudaErrorInvalidValue; break;
     }

@@ -186,13 +186,13 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
                                                        const int64_t *__restrict__ rowT,
                                                        const int64_t *__restrict__ kT, int64_t rows, int64_t K,
                                                        const unsigned long long *__restrict__ maxbits, int kbits,
-                                                       OzConsts c, uint16_t *__restrict__ out, int64_t ld)
+                                                       OzConsts c, uint16_t *__restrict__ out, int64_t ld,
+                                                       int64_t plane, int64_t neg_from)
 {
     __shared__ uint64_t tile[2][TR][TKP + 1];
     __shared__ int sshift[2][TR];
     const int64_t tiles_k = (K + TKP - 1) / TKP;
     const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
-    const int64_t plane = rows * ld;
     auto issue = [&](int64_t t, int buf) {
         const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
         if (threadIdx.x < TR)
@@ -232,7 +232,10 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
             for (int u = 0; u < 2; ++u) {
                 const uint64_t bits = tile[buf][r][k + u];
                 const uint64_t v = scaled_int(bits & 0x7FFFFFFFFFFFFFFFull, sshift[buf][r]);
-                const float sg = (bits >> 63) ? -1.f : 1.f;
+                // k >= neg_from: the value enters negated (the -Im block of the
+                // real form of a complex matrix)
+                const bool neg = ((bits >> 63) != 0) != (k0 + k + u >= neg_from);
+                const float sg = neg ? -1.f : 1.f;
                 l0[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)(v & 0x1FFF)) - 8388608.0f);
                 l1[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)((v >> 13) & 0x1FFF)) - 8388608.0f);
                 l2[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)((v >> 26) & 0x1FFF)) - 8388608.0f);
@@ -262,11 +265,14 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
 template <int ROW_FAST>
 cudaError_t launch_residues(const double *src, const int64_t *rowT, const int64_t *kT, int64_t rows, int64_t K,
                             const unsigned long long *maxbits, int kbits, const OzConsts &c, uint16_t *out,
-                            int64_t ld, int blocks, cudaStream_t s)
+                            int64_t ld, int blocks, cudaStream_t s, int64_t plane = -1, int64_t neg_from = -1)
 {
+    if (plane < 0) plane = rows * ld;
+    if (neg_from < 0) neg_from = K;
 #define CASE(LL)                                                                                    \
     case LL:                                                                                        \
-        oz_residue_kernel<ROW_FAST, LL><<<blocks, PT, 0, s>>>(src, rowT, kT, rows, K, maxbits, kbits, c, out, ld); \
+        oz_residue_kernel<ROW_FAST, LL><<<blocks, PT, 0, s>>>(src, rowT, kT, rows, K, maxbits, kbits, c, out, ld, \
+                                                              plane, neg_from);                     \
         break;
     switch (c.L) {
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
                                                     const unsigned long long *__restrict__ maxB,
                                                     const int64_t *__restrict__ rowC,
                                                     const int64_t *__restrict__ colC, double *__restrict__ C,
-                                                    OzConsts c)
+                                                    OzConsts c, int64_t shift_rows)
 {
     const int64_t MN = M * N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
             drop = 0;
         }
         const double mag = __ull2double_rn(top);
-        const int e = drop - (shift_for(maxA[m], c.ka) + shift_for(maxB[n], c.kb));
+        const int e = drop - (shift_for(maxA[m % shift_rows], c.ka) + shift_for(maxB[n], c.kb));
         // mag * 2^e in two exact power-of-two steps (no overflow of the factors)
         const int e1 = e / 2, e2 = e - e1;
         const double f1 = __longlong_as_double((long long)(e1 + 1023) << 52);
@@ -372,6 +378,36 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
         const double val = negv ? -((mag * f1) * f2) : (mag * f1) * f2;
         double *dst = C + rowC[m] + colC[n];
         *dst = *dst + val;
+    }
+}
+
+// Offset tables (in doubles) of the real form of a complex contraction:
+//   [C_re; C_im] = [[A_re, -A_im], [A_im, A_re]] [B_re; B_im]
+// rows r < M of the real A are re-rows, r >= M im-rows; k' < K selects the
+// first block of columns.  Complex element offsets o become 2 o (+1 for the
+// imaginary part).
+__global__ void oz_complex_tables_kernel(const int64_t *rowA, const int64_t *rowC, const int64_t *colB,
+                                         const int64_t *colC, const int64_t *kA, const int64_t *kB, int64_t M,
+                                         int64_t N, int64_t K, int64_t *rowA2, int64_t *kAre, int64_t *kAim,
+                                         int64_t *colB2, int64_t *kB2, int64_t *rowC2, int64_t *colC2)
+{
+    const int64_t n_all = max(max(2 * M, 2 * K), N);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_all; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < 2 * M) {
+            const int64_t m = i % M, im = i >= M ? 1 : 0;
+            rowA2[i] = 2 * rowA[m] + im;
+            rowC2[i] = 2 * rowC[m] + im;
+        }
+        if (i < 2 * K) {
+            const int64_t k = i % K, hi = i >= K ? 1 : 0;
+            kAre[i] = 2 * kA[k] + hi;   // re-rows: Re then Im (the Im block enters negated)
+            kAim[i] = 2 * kA[k] - hi;   // im-rows (offset +1 in rowA2): Im then Re
+            kB2[i] = 2 * kB[k] + hi;    // B: Re block over Im block
+        }
+        if (i < N) {
+            colB2[i] = 2 * colB[i];
+            colC2[i] = 2 * colC[i];
+        }
     }
 }
 
@@ -446,20 +482,21 @@ void oz_setup(int64_t K, int want_L, OzConsts *c)
 template <int L>
 void launch_crt_t(const int8_t *R, int64_t M, int64_t N, const unsigned long long *maxA,
                   const unsigned long long *maxB, const int64_t *rowC, const int64_t *colC, double *C,
-                  const OzConsts &c, int num_sms, cudaStream_t s)
+                  const OzConsts &c, int num_sms, cudaStream_t s, int64_t shift_rows)
 {
     const int64_t MN = M * N;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((MN + 255) / 256, (int64_t)num_sms * 16));
-    oz_crt_kernel<L><<<blocks, 256, 0, s>>>(R, M, N, maxA, maxB, rowC, colC, C, c);
+    oz_crt_kernel<L><<<blocks, 256, 0, s>>>(R, M, N, maxA, maxB, rowC, colC, C, c, shift_rows);
 }
 
 cudaError_t launch_crt(const int8_t *R, int64_t M, int64_t N, const unsigned long long *maxA,
                        const unsigned long long *maxB, const int64_t *rowC, const int64_t *colC, double *C,
-                       const OzConsts &c, int num_sms, cudaStream_t s)
+                       const OzConsts &c, int num_sms, cudaStream_t s, int64_t shift_rows = -1)
 {
+    if (shift_rows <= 0) shift_rows = M;
 #define CASE(L)                                                                       \
     case L:                                                                           \
-        launch_crt_t<L>(R, M, N, maxA, maxB, rowC, colC, C, c, num_sms, s);           \
+        launch_crt_t<L>(R, M, N, maxA, maxB, rowC, colC, C, c, num_sms, s, shift_rows); \
         break;
     switch (c.L) {
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
@@ -570,6 +607,114 @@ cudaError_t launch_ozaki(const Plan &pl, int L_req, const void *A, const void *B
     e = launch_tc_gemm(TC_MODE_MOD, o.RA, o.RB, c.L, p, s);
     if (e != cudaSuccess) return e;
     return launch_crt(o.R, pl.M, pl.N, o.maxA, o.maxB, o.rowC, o.colC, Cb, c, num_sms, s);
+}
+
+namespace {
+
+struct OzComplexLayout {
+    int64_t *rowA, *rowC, *colB, *colC, *kA, *kB;              // complex element units
+    int64_t *rowA2, *kAre, *kAim, *colB2, *kB2, *rowC2, *colC2;  // doubles, real form
+    unsigned long long *maxA, *maxB;
+    uint16_t *RA, *RB;
+    int8_t *R;
+    int64_t ld;
+    size_t total;
+};
+
+OzComplexLayout oz_complex_layout(const Plan &p, int L, void *ws)
+{
+    OzComplexLayout o{};
+    char *w = static_cast<char *>(ws);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *r = w ? w + off : nullptr;
+        off += a256(bytes);
+        return r;
+    };
+    const int64_t M2 = 2 * p.M, K2 = 2 * p.K;
+    o.ld = tc_ld(K2);
+    auto t64 = [&](int64_t n) { return reinterpret_cast<int64_t *>(take(8 * (size_t)n)); };
+    o.rowA = t64(p.M); o.rowC = t64(p.M); o.colB = t64(p.N); o.colC = t64(p.N); o.kA = t64(p.K); o.kB = t64(p.K);
+    o.rowA2 = t64(M2); o.kAre = t64(K2); o.kAim = t64(K2); o.colB2 = t64(p.N); o.kB2 = t64(K2);
+    o.rowC2 = t64(M2); o.colC2 = t64(p.N);
+    o.maxA = reinterpret_cast<unsigned long long *>(take(8 * (size_t)p.M));
+    o.maxB = reinterpret_cast<unsigned long long *>(take(8 * (size_t)p.N));
+    o.RA = reinterpret_cast<uint16_t *>(take(2 * (size_t)L * M2 * o.ld));
+    o.RB = reinterpret_cast<uint16_t *>(take(2 * (size_t)L * p.N * o.ld));
+    o.R = reinterpret_cast<int8_t *>(take((size_t)L * M2 * p.N));
+    o.total = off;
+    return o;
+}
+
+}  // namespace
+
+size_t ozaki_complex_workspace_bytes(const Plan &p, int L)
+{
+    return oz_complex_layout(p, L, nullptr).total;
+}
+
+// Complex double (z) split precision: the same scaling, residue, slice-GEMM and
+// recombination kernels applied to the real form of the contraction (2M rows,
+// 2K contracted indices), reading the interleaved complex buffers in place
+// through the real-form offset tables.
+cudaError_t launch_ozaki_complex(const Plan &pl, int L_req, const void *A, const void *B, void *C, void *ws,
+                                 int num_sms, int *err, cudaStream_t s)
+{
+    const int64_t M2 = 2 * pl.M, K2 = 2 * pl.K;
+    OzConsts c;
+    oz_setup(K2, L_req, &c);
+    OzComplexLayout o = oz_complex_layout(pl, c.L, ws);
+    cudaError_t e = launch_build_tables(pl, o.rowA, o.rowC, o.colB, o.colC, o.kA, o.kB, s);
+    if (e != cudaSuccess) return e;
+    {
+        const int64_t n_all = std::max(std::max(M2, K2), pl.N);
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n_all + 255) / 256, 4096));
+        oz_complex_tables_kernel<<<blocks, 256, 0, s>>>(o.rowA, o.rowC, o.colB, o.colC, o.kA, o.kB, pl.M, pl.N, pl.K,
+                                                        o.rowA2, o.kAre, o.kAim, o.colB2, o.kB2, o.rowC2, o.colC2);
+    }
+    e = cudaMemsetAsync(o.maxA, 0, 8 * (size_t)pl.M, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o.maxB, 0, 8 * (size_t)pl.N, s);
+    if (e != cudaSuccess) return e;
+    const double *Ab = static_cast<const double *>(A) + 2 * pl.offA;
+    const double *Bb = static_cast<const double *>(B) + 2 * pl.offB;
+    double *Cb = static_cast<double *>(C) + 2 * pl.offC;
+    auto first = [](const ModeList &Lm, const int64_t *st) { return Lm.n ? (st[0] < 0 ? -st[0] : st[0]) : 0; };
+    const bool a_row_fast = first(pl.m, pl.m.s0) != 0 && first(pl.m, pl.m.s0) <= first(pl.k, pl.k.s0);
+    const bool b_row_fast = first(pl.n, pl.n.s0) != 0 && first(pl.n, pl.n.s0) <= first(pl.k, pl.k.s1);
+    auto blocks_for = [&](int64_t rows) {
+        int64_t n = ((rows + TR - 1) / TR) * ((K2 + TKP - 1) / TKP);
+        return (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * 8));
+    };
+    // scales: a complex row's maximum over both parts (its re-row covers both)
+    if (a_row_fast) oz_maxbits_kernel<1><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA2, o.kAre, pl.M, K2, o.maxA);
+    else oz_maxbits_kernel<0><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA2, o.kAre, pl.M, K2, o.maxA);
+    if (b_row_fast) oz_maxbits_kernel<1><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB2, o.kB2, pl.N, K2, o.maxB);
+    else oz_maxbits_kernel<0><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB2, o.kB2, pl.N, K2, o.maxB);
+    const int64_t planeA = M2 * o.ld;
+    // re-rows: [Re | -Im], im-rows: [Im | Re]
+    e = a_row_fast ? launch_residues<1>(Ab, o.rowA2, o.kAre, pl.M, K2, o.maxA, c.ka, c, o.RA, o.ld, blocks_for(pl.M), s,
+                                        planeA, pl.K)
+                   : launch_residues<0>(Ab, o.rowA2, o.kAre, pl.M, K2, o.maxA, c.ka, c, o.RA, o.ld, blocks_for(pl.M), s,
+                                        planeA, pl.K);
+    if (e != cudaSuccess) return e;
+    e = a_row_fast ? launch_residues<1>(Ab, o.rowA2 + pl.M, o.kAim, pl.M, K2, o.maxA, c.ka, c, o.RA + pl.M * o.ld,
+                                        o.ld, blocks_for(pl.M), s, planeA, K2)
+                   : launch_residues<0>(Ab, o.rowA2 + pl.M, o.kAim, pl.M, K2, o.maxA, c.ka, c, o.RA + pl.M * o.ld,
+                                        o.ld, blocks_for(pl.M), s, planeA, K2);
+    if (e != cudaSuccess) return e;
+    e = b_row_fast ? launch_residues<1>(Bb, o.colB2, o.kB2, pl.N, K2, o.maxB, c.kb, c, o.RB, o.ld, blocks_for(pl.N), s)
+                   : launch_residues<0>(Bb, o.colB2, o.kB2, pl.N, K2, o.maxB, c.kb, c, o.RB, o.ld, blocks_for(pl.N), s);
+    if (e != cudaSuccess) return e;
+    TcGemmParams p{};
+    p.M = M2;
+    p.N = pl.N;
+    p.K = K2;
+    p.err = err;
+    p.kc_tiles = OZ_CHUNK_K / 64;
+    p.R = o.R;
+    e = launch_tc_gemm(TC_MODE_MOD, o.RA, o.RB, c.L, p, s);
+    if (e != cudaSuccess) return e;
+    return launch_crt(o.R, M2, pl.N, o.maxA, o.maxB, o.rowC2, o.colC2, Cb, c, num_sms, s, pl.M);
 }
 
 }  // namespace gett

@@ -48,5 +48,9 @@ int ozaki_bits_for(int64_t K, int L);
 size_t ozaki_workspace_bytes(const Plan &p, int L);
 cudaError_t launch_ozaki(const Plan &p, int L, const void *A, const void *B, void *C, void *ws, int num_sms,
                          int *err, cudaStream_t s);
+// z: the same on the real form of the complex contraction (2M rows, 2K sums)
+size_t ozaki_complex_workspace_bytes(const Plan &p, int L);
+cudaError_t launch_ozaki_complex(const Plan &p, int L, const void *A, const void *B, void *C, void *ws,
+                                 int num_sms, int *err, cudaStream_t s);
 
 }  // namespace gett

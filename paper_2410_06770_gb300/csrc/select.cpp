@@ -74,11 +74,12 @@ int choose(const Plan &p, DType t, const gett_options *opt, int num_sms, Choice 
 {
     Choice c = heuristic_choice(p, t, num_sms);
     if (opt && opt->algo == GETT_ALGO_OZAKI_BF16) {
-        if (t != DT_F64) return GETT_ERR_UNSUPPORTED;
+        if (t != DT_F64 && t != DT_C64) return GETT_ERR_UNSUPPORTED;
         c = Choice{};
         c.family = GETT_FAMILY_TC;
         c.algo = GETT_ALGO_OZAKI_BF16;
-        c.moduli = ozaki_moduli_for(p.K, opt->moduli);
+        // the complex form sums 2K real products per element
+        c.moduli = ozaki_moduli_for(t == DT_C64 ? 2 * p.K : p.K, opt->moduli);
         c.selector = 3;
         *out = c;
         return GETT_OK;

@@ -141,3 +141,35 @@ def test_ozaki_moduli_counts(L):
     lp = sum(np.log2(moduli[:L]))
     bits = min(52, int(np.floor((lp - 1 - np.log2(480) - 1e-6) / 2)))
     assert rel <= 2.0 ** (-bits + 6), (rel, bits)
+
+
+@pytest.mark.parametrize("idx", range(len(SHAPES)))
+@pytest.mark.parametrize("dist", ["int", "uniform", "logu"])
+def test_ozaki_complex(idx, dist):
+    """zgett with the split-precision form: the real 2x2 block form of the
+    complex contraction on bf16 tensor cores.  Integer data bit-exact, float
+    data normwise within 1e-13 of the complex-double oracle."""
+    rng = np.random.default_rng(70 + idx)
+    p = synth.make_problem(SHAPES[idx], rng, np.complex128, dist, ("padded", "negative", "contig"),
+                           "int" if dist == "int" else "uniform")
+    got, rep = run_gpu("z", p, mode="ex", opts=gett.options(algo="ozaki_bf16"))
+    assert rep["family_name"] == "tc"
+    ref = oracle_ref(p)
+    if dist == "int":
+        compare("z", p, got, ref, exact=True)
+    else:
+        g = synth.gather(p.lc, got)
+        r = synth.gather(p.lc, ref)
+        assert np.linalg.norm(g - r) <= 1e-13 * np.linalg.norm(r)
+        gaps = synth.gap_mask(p.lc)
+        assert np.array_equal(got[gaps], p.C[gaps])
+
+
+@pytest.mark.parametrize("family", ["basic", "subtensor_negative", "rank_zero", "scalar", "nothing"])
+def test_ozaki_complex_thesis_families(family):
+    p = synth.thesis_problem(family, 61, np.complex128, "uniform", c_dist="uniform")
+    got, _ = run_gpu("z", p, mode="ex", opts=gett.options(algo="ozaki_bf16"))
+    g = synth.gather(p.lc, got)
+    r = synth.gather(p.lc, oracle_ref(p))
+    nr = np.linalg.norm(r)
+    assert np.linalg.norm(g - r) <= 1e-13 * (nr if nr else 1.0)
