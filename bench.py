@@ -244,12 +244,13 @@ def traffic_entry(kernel_key: str):
     e = entries.get(kernel_key)
     if not e:
         return None
-    src = os.path.join(ROOT, e["source"])
+    h = hashlib.sha256()
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for src in e["sources"]:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
     except Exception:
         return None
-    if sha != e.get("source_sha"):
+    if h.hexdigest()[:16] != e.get("source_sha"):
         return None
     return e
 
@@ -374,19 +375,19 @@ def gpu_arm(args, dist: Dist):
 
 
 def sampled_parity(p, Cbuf, nsamples=128):
-    """Max elementwise relative error of sampled output elements against the
-    oracle evaluated one element at a time (the sub-problem with every free
-    mode fixed)."""
+    """Sampled output elements against the oracle evaluated one element at a
+    time (the sub-problem with every free index fixed): the largest
+    element-wise relative error and the normwise error over the sample."""
     import oracle
-    from paper_2410_06770_gb300 import synth
     s = p.sig
+    cplx = np.iscomplexobj(p.A)
+    prec = "z" if cplx else "f64"
     rng = np.random.default_rng(1234)
     extc = s.extc()
     fps = s.free_modes()
-    errs = []
+    errs, diffs, refs = [], [], []
     for _ in range(nsamples):
         o = [int(rng.integers(0, e)) for e in extc]
-        # fix free coordinates: A and B offsets move to the chosen element
         offa, offb = p.la.off, p.lb.off
         for pidx, (t, m) in enumerate(fps):
             x = o[s.perm[pidx]]
@@ -397,9 +398,9 @@ def sampled_parity(p, Cbuf, nsamples=128):
         exta = [s.exta[m] for m in s.conta]
         inca = [p.la.inc[m] for m in s.conta]
         incb = [p.lb.inc[m] for m in s.contb]
-        c = np.zeros(1)
+        c = np.zeros(1, dtype=np.complex128 if cplx else np.float64)
         r = len(exta)
-        rc = oracle.gett_raw("f64", r, exta, inca, p.A, offa, r, exta, incb, p.B, offb, r,
+        rc = oracle.gett_raw(prec, r, exta, inca, p.A, offa, r, exta, incb, p.B, offb, r,
                              list(range(r)), list(range(r)), [], [], c, 0)
         assert rc == 0
         offc = p.lc.off + sum(x * i for x, i in zip(o, p.lc.inc))
@@ -407,7 +408,10 @@ def sampled_parity(p, Cbuf, nsamples=128):
         got = Cbuf[offc]
         bound = abs(ref) if ref != 0 else 1.0
         errs.append(abs(got - ref) / bound)
+        diffs.append(abs(got - ref))
+        refs.append(abs(ref))
     return {"samples": nsamples, "max_rel_err": float(max(errs)), "median_rel_err": float(np.median(errs)),
+            "normwise_err_over_sample": float(np.linalg.norm(diffs) / np.linalg.norm(refs)),
             "against": "oracle (Alg. 1) per sampled output element"}
 
 
@@ -532,6 +536,29 @@ def measure_split_forms():
                                          "tflops": flops_of(q) / (best * 1e-3) / 1e12}
     out["small_logu_forms"] = {"workload": "dgett_small shapes, 10^U(-8,8) magnitudes, random signs",
                                "forms": forms}
+    # complex double: the CC contraction at a..d = 64, i,j = 16, native vs split
+    pz = synth.cfg_cc("plain", dtype=np.complex128, scale=64, small_ij=16)
+    a = pz.args()
+    zf = {}
+    for algo in ("native", "ozaki_bf16"):
+        dA, dB = torch.from_numpy(pz.A).cuda(), torch.from_numpy(pz.B).cuda()
+        dC = torch.from_numpy(pz.C).cuda()
+        o = gett.options(algo=algo)
+
+        def cz():
+            return gett.xgett("z", a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"], a["INCB"], dB,
+                              a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], dC, mode="ex", opts=o,
+                              stream=stream.cuda_stream)
+        _, rep = cz()
+        torch.cuda.synchronize()
+        par = sampled_parity(pz, dC.cpu().numpy(), nsamples=32)
+        best, _ = time_calls(cz, 3)
+        fz = 4 * flops_of(pz)
+        zf[f"zgett/{algo}"] = {"ms": best, "tflops": fz / (best * 1e-3) / 1e12, "moduli": rep["moduli"],
+                               "parity": par}
+        del dA, dB, dC
+    out["cc64_complex_forms"] = {"workload": "complex CC, a..d=64, i,j=16 (8 real flops per complex MAC)",
+                                 "forms": zf}
     return out
 
 
