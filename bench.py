@@ -365,7 +365,7 @@ def gpu_arm(args, dist: Dist):
         torch.cuda.empty_cache()
         result["forms"] = measure_forms(args.workload)
         result["forms"].update(measure_split_forms())
-        result["forms"].update(measure_streaming_forms())
+        result["forms"].update(measure_streaming_forms(pk.get("dfma_tflops")))
         result["forms"]["batched"] = measure_batched()
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         v, cores, desc, dt = oracle_sample(p, args.cpu_seconds)
@@ -635,10 +635,13 @@ def measure_batched(n=4096):
     return out
 
 
-def measure_streaming_forms():
-    """HBM-bound kernels beyond the outer product: a full inner product of two
-    128^4 tensors (REDUCE, 4.3 GB read) and a matrix-vector contraction
-    A(16384, 16384) x B(16384, 2) (SKINNY, 2.1 GB read)."""
+def measure_streaming_forms(dfma_tflops=None):
+    """Low-intensity kernels beyond the outer product: a full inner product of
+    two 128^4 tensors (REDUCE, 4.3 GB read) and a matrix-vector contraction
+    A(16384, 16384) x B(16384, 2) (SKINNY, 2.1 GB read).  Each is bounded by
+    HBM or, in FP64 on this GPU, by the FMA rate (2 flops per element and
+    short-class column): both fractions are given, and `bound` names the
+    larger floor."""
     import torch
     from paper_2410_06770_gb300 import gett, synth
     mp = measured_peaks()
@@ -666,9 +669,19 @@ def measure_streaming_forms():
         _, rep = call()
         best, _ = time_calls(call, 5)
         nbytes = 8.0 * (la.numel + lb.numel + 2 * lc.numel)
-        out[name] = {"family": rep["family_name"], "ms": best, "gbs": nbytes / (best * 1e-3) / 1e9,
-                     "hbm_frac": nbytes / (best * 1e-3) / 1e9 / bw,
-                     "shape": f"A{sig.exta} x B{sig.extb}, CONTS={sig.conts}"}
+        flops = 2.0 * rep["M"] * rep["N"] * rep["K"]
+        ent = {"family": rep["family_name"], "ms": best, "gbs": nbytes / (best * 1e-3) / 1e9,
+               "hbm_frac": nbytes / (best * 1e-3) / 1e9 / bw,
+               "tflops": flops / (best * 1e-3) / 1e12,
+               "shape": f"A{sig.exta} x B{sig.extb}, CONTS={sig.conts}"}
+        if dfma_tflops:
+            ent["dfma_frac"] = ent["tflops"] / dfma_tflops
+            hbm_floor = nbytes / (bw * 1e9)
+            alu_floor = flops / (dfma_tflops * 1e12)
+            ent["bound"] = "hbm" if hbm_floor >= alu_floor else "alu"
+            ent["floor_ms"] = max(hbm_floor, alu_floor) * 1e3
+            ent["floor_frac"] = ent["floor_ms"] / best
+        out[name] = ent
         del dA, dB, dC
         torch.cuda.empty_cache()
     return out

@@ -83,7 +83,7 @@ cudaError_t run_family(const Plan &p, DType t, const Choice &ch, const void *A, 
     size_t ws_bytes = 0;
     if (ch.family == GETT_FAMILY_DENSE) ws_bytes = dense_workspace_bytes(p, t, ch.config, ch.split_k);
     else if (ch.family == GETT_FAMILY_REDUCE) ws_bytes = reduce_workspace_bytes(p, t, st.sms);
-    else if (ch.family == GETT_FAMILY_SKINNY) ws_bytes = skinny_workspace_bytes(p);
+    else if (ch.family == GETT_FAMILY_SKINNY) ws_bytes = skinny_workspace_bytes(p, t, st.sms);
     else if (ch.family == GETT_FAMILY_TC)
         ws_bytes = ch.algo != GETT_ALGO_OZAKI_BF16 ? tc_split_workspace_bytes(p, ch.algo)
                    : (t == DT_C64 ? ozaki_complex_workspace_bytes(p, ch.moduli) : ozaki_workspace_bytes(p, ch.moduli));

@@ -11,9 +11,16 @@
 //
 // SKINNY: one free class of at most 8 indices and a long sum (matrix-vector
 // like).  Each of the (up to 8) short-class outputs of a long-class row is
-// accumulated in registers; when the long operand's contracted index has the
-// smaller increment a warp reduces one row (lanes along k, warp shuffles),
-// otherwise each thread reduces one row (threads along the row index).
+// accumulated in registers.  When the long operand's contracted index has the
+// smaller increment a warp reduces one row (lanes along k, warp shuffles);
+// otherwise a CTA owns 32 consecutive rows (lanes along the row index) and its
+// warps split the K range.  The CTA stages each chunk of its K range (the
+// long operand's offsets and the short operand's values) in shared memory,
+// so the inner loop's only global loads are the long operand's, several in
+// flight per thread.  The grid also splits K into slices so that about
+// sixteen CTAs per SM stream the long operand; slice partials are added into
+// C in slice order by a second kernel.  In FP64 on this GPU the kernel is
+// bound by the FP64 FMA rate once S >= 2 (2 S flops per 8-byte element).
 //
 // REDUCE: few output elements and long sums (the "scalar contraction" of
 // Sec. 7 and its neighbours).  Pass 1 splits the flat contracted index
@@ -111,68 +118,184 @@ struct SkinnyParams {
     int64_t colY[SKINNY_MAX_S], colC[SKINNY_MAX_S];
     int64_t R, K;
     int S;
+    int splits;                   // K slices (grid.y)
+    int64_t kps;                  // K per slice
+    void *partial;                // splits > 1: Acc[splits][S][R]
 };
 
-// one warp per row: lanes stride over k
-template <class T>
-__global__ void __launch_bounds__(256) skinny_warp_kernel(SkinnyParams p)
+template <class Rt>
+__device__ __forceinline__ void skinny_emit(const SkinnyParams &p, int64_t r, int s, typename Rt::Acc v)
+{
+    using Acc = typename Rt::Acc;
+    if (p.splits > 1)
+        static_cast<Acc *>(p.partial)[((int64_t)blockIdx.y * p.S + s) * p.R + r] = v;
+    else
+        Rt::store_add(static_cast<typename Rt::Out *>(p.C) + p.rowC[r] + p.colC[s], v);
+}
+
+// K chunk staged in shared memory by each SKINNY CTA: 2 KB of Acc values
+// per short-class column (256 doubles).
+template <class Acc>
+__host__ __device__ constexpr int skinny_kc()
+{
+    return (int)(2048 / sizeof(Acc));
+}
+
+template <class Acc, int SM>
+__host__ __device__ constexpr size_t skinny_smem_bytes(bool with_red)
+{
+    return (size_t)skinny_kc<Acc>() * (sizeof(int64_t) + SM * sizeof(Acc)) > (with_red ? 8 * SM * 32 * sizeof(Acc) : 0)
+               ? (size_t)skinny_kc<Acc>() * (sizeof(int64_t) + SM * sizeof(Acc))
+               : 8 * SM * 32 * sizeof(Acc);
+}
+
+// Stage k = kc .. kc+n-1 of the slice: koff[i] = offset of k in X, yv[i][s] =
+// Y element of short-class column s at k.  The whole CTA loads (coalesced
+// reads of the tables), so the inner loops read only X from global memory.
+template <class T, int SM>
+__device__ __forceinline__ void skinny_stage(const SkinnyParams &p, int64_t kc, int n, int64_t *koff,
+                                             typename Tr<T>::Acc *yv)
+{
+    using Rt = Tr<T>;
+    const T *Y = static_cast<const T *>(p.Y);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        koff[i] = p.kX[kc + i];
+        const int64_t yk = p.kY[kc + i];
+#pragma unroll
+        for (int s = 0; s < SM; ++s)
+            if (s < p.S) yv[i * SM + s] = Rt::load(Y + p.colY[s] + yk);
+    }
+}
+
+// Rows contiguous in X: a CTA owns 32 rows (lane = row); its 8 warps take
+// interleaved k of each staged chunk of the CTA's K slice, then add their
+// sums in warp order.  SM >= S bounds the register-held columns.
+template <class T, int SM>
+__global__ void __launch_bounds__(256) skinny_rows_kernel(SkinnyParams p)
 {
     using Rt = Tr<T>;
     using Acc = typename Rt::Acc;
-    using Out = typename Rt::Out;
+    constexpr int KC = skinny_kc<Acc>();
+    __shared__ __align__(16) unsigned char sbuf[skinny_smem_bytes<Acc, SM>(true)];
+    int64_t *koff = reinterpret_cast<int64_t *>(sbuf);
+    Acc *yv = reinterpret_cast<Acc *>(sbuf + KC * sizeof(int64_t));
     const T *X = static_cast<const T *>(p.X);
-    const T *Y = static_cast<const T *>(p.Y);
-    Out *C = static_cast<Out *>(p.C);
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = warp; r < p.R; r += nwarps) {
-        Acc acc[SKINNY_MAX_S];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 32 + lane;
+    const bool ok = r < p.R;
+    const T *xr = X + (ok ? p.rowX[r] : 0);
+    const int64_t k0 = (int64_t)blockIdx.y * p.kps, k1 = min(p.K, k0 + p.kps);
+    Acc acc[SM];
 #pragma unroll
-        for (int s = 0; s < SKINNY_MAX_S; ++s) acc[s] = Rt::zero();
-        const T *xr = X + p.rowX[r];
-        for (int64_t k = lane; k < p.K; k += 32) {
-            const Acc xv = Rt::load(xr + p.kX[k]);
-            const int64_t yk = p.kY[k];
+    for (int s = 0; s < SM; ++s) acc[s] = Rt::zero();
+    for (int64_t kc = k0; kc < k1; kc += KC) {
+        const int n = (int)min((int64_t)KC, k1 - kc);
+        __syncthreads();
+        skinny_stage<T, SM>(p, kc, n, koff, yv);
+        __syncthreads();
+        if (!ok) continue;
+        int i = warp;
+        for (; i + 24 < n; i += 32) {  // four independent loads in flight
+            Acc xv[4];
 #pragma unroll
-            for (int s = 0; s < SKINNY_MAX_S; ++s)
-                if (s < p.S) Rt::mac(acc[s], xv, Rt::load(Y + p.colY[s] + yk));
+            for (int u = 0; u < 4; ++u) xv[u] = Rt::load(xr + koff[i + 8 * u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int s = 0; s < SM; ++s)
+                    if (s < p.S) Rt::mac(acc[s], xv[u], yv[(i + 8 * u) * SM + s]);
         }
+        for (; i < n; i += 8) {
+            const Acc xv = Rt::load(xr + koff[i]);
 #pragma unroll
-        for (int s = 0; s < SKINNY_MAX_S; ++s) {
+            for (int s = 0; s < SM; ++s)
+                if (s < p.S) Rt::mac(acc[s], xv, yv[i * SM + s]);
+        }
+    }
+    __syncthreads();
+    Acc *red = reinterpret_cast<Acc *>(sbuf);  // [8][SM][32]
+#pragma unroll
+    for (int s = 0; s < SM; ++s) red[(warp * SM + s) * 32 + lane] = acc[s];
+    __syncthreads();
+    if (warp == 0 && ok) {
+#pragma unroll
+        for (int s = 0; s < SM; ++s) {
             if (s >= p.S) break;
-            Acc v = acc[s];
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) v = Rt::add(v, shfl_down(v, d));
-            if (lane == 0) Rt::store_add(C + p.rowC[r] + p.colC[s], v);
+            Acc v = red[s * 32 + lane];
+            for (int w = 1; w < 8; ++w) v = Rt::add(v, red[(w * SM + s) * 32 + lane]);
+            skinny_emit<Rt>(p, r, s, v);
         }
     }
 }
 
-// one thread per row: threads stride over rows, each loops over k
-template <class T>
-__global__ void __launch_bounds__(256) skinny_thread_kernel(SkinnyParams p)
+// K contiguous in X: one warp per row (8 rows per CTA), lanes along k of each
+// staged chunk of the CTA's K slice, warp shuffles.
+template <class T, int SM>
+__global__ void __launch_bounds__(256) skinny_warp_kernel(SkinnyParams p)
 {
     using Rt = Tr<T>;
     using Acc = typename Rt::Acc;
+    constexpr int KC = skinny_kc<Acc>();
+    __shared__ __align__(16) unsigned char sbuf[skinny_smem_bytes<Acc, SM>(false)];
+    int64_t *koff = reinterpret_cast<int64_t *>(sbuf);
+    Acc *yv = reinterpret_cast<Acc *>(sbuf + KC * sizeof(int64_t));
     const T *X = static_cast<const T *>(p.X);
-    const T *Y = static_cast<const T *>(p.Y);
-    typename Rt::Out *C = static_cast<typename Rt::Out *>(p.C);
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < p.R; r += (int64_t)gridDim.x * blockDim.x) {
-        Acc acc[SKINNY_MAX_S];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 8 + warp;
+    const bool ok = r < p.R;
+    const T *xr = X + (ok ? p.rowX[r] : 0);
+    const int64_t k0 = (int64_t)blockIdx.y * p.kps, k1 = min(p.K, k0 + p.kps);
+    Acc acc[SM];
 #pragma unroll
-        for (int s = 0; s < SKINNY_MAX_S; ++s) acc[s] = Rt::zero();
-        const T *xr = X + p.rowX[r];
-        for (int64_t k = 0; k < p.K; ++k) {
-            const Acc xv = Rt::load(xr + p.kX[k]);
-            const int64_t yk = p.kY[k];
+    for (int s = 0; s < SM; ++s) acc[s] = Rt::zero();
+    for (int64_t kc = k0; kc < k1; kc += KC) {
+        const int n = (int)min((int64_t)KC, k1 - kc);
+        __syncthreads();
+        skinny_stage<T, SM>(p, kc, n, koff, yv);
+        __syncthreads();
+        if (!ok) continue;
+        int i = lane;
+        for (; i + 96 < n; i += 128) {
+            Acc xv[4];
 #pragma unroll
-            for (int s = 0; s < SKINNY_MAX_S; ++s)
-                if (s < p.S) Rt::mac(acc[s], xv, Rt::load(Y + p.colY[s] + yk));
+            for (int u = 0; u < 4; ++u) xv[u] = Rt::load(xr + koff[i + 32 * u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int s = 0; s < SM; ++s)
+                    if (s < p.S) Rt::mac(acc[s], xv[u], yv[(i + 32 * u) * SM + s]);
         }
+        for (; i < n; i += 32) {
+            const Acc xv = Rt::load(xr + koff[i]);
 #pragma unroll
-        for (int s = 0; s < SKINNY_MAX_S; ++s)
-            if (s < p.S) Rt::store_add(C + p.rowC[r] + p.colC[s], acc[s]);
+            for (int s = 0; s < SM; ++s)
+                if (s < p.S) Rt::mac(acc[s], xv, yv[i * SM + s]);
+        }
+    }
+    if (!ok) return;
+#pragma unroll
+    for (int s = 0; s < SM; ++s) {
+        if (s >= p.S) break;
+        Acc v = acc[s];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v = Rt::add(v, shfl_down(v, d));
+        if (lane == 0) skinny_emit<Rt>(p, r, s, v);
+    }
+}
+
+// C[rowC[r] + colC[s]] += sum of the K-slice partials, slices in order.
+template <class T>
+__global__ void skinny_reduce_kernel(SkinnyParams p)
+{
+    using Rt = Tr<T>;
+    using Acc = typename Rt::Acc;
+    const Acc *P = static_cast<const Acc *>(p.partial);
+    const int64_t SR = (int64_t)p.S * p.R;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < SR; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i % p.R, s = i / p.R;
+        Acc v = P[i];
+        for (int j = 1; j < p.splits; ++j) v = Rt::add(v, P[(int64_t)j * SR + i]);
+        Rt::store_add(static_cast<typename Rt::Out *>(p.C) + p.rowC[r] + p.colC[s], v);
     }
 }
 
@@ -370,9 +493,35 @@ cudaError_t launch_outer(const Plan &pl, DType t, const void *A, const void *B, 
     return cudaErrorInvalidValue;
 }
 
-size_t skinny_workspace_bytes(const Plan &p)
+// K slices of the SKINNY kernel: enough CTAs for sixteen per SM, each slice
+// at least 1024 long.
+int skinny_splits(const Plan &p, bool rows_mode, int num_sms)
 {
-    return sizeof(int64_t) * 2 * (size_t)(p.M + p.N + p.K) + 256;
+    const int64_t R = std::max(p.M, p.N);
+    const int64_t row_tiles = rows_mode ? (R + 31) / 32 : (R + 7) / 8;
+    int64_t want = (16LL * num_sms + row_tiles - 1) / row_tiles;
+    want = std::min<int64_t>(want, std::max<int64_t>(1, p.K / 1024));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 1024));
+}
+
+bool skinny_rows_mode(const Plan &pl)
+{
+    const bool short_is_n = pl.N <= pl.M;
+    const ModeList &lg = short_is_n ? pl.m : pl.n;
+    const int64_t s_row = lg.n ? (lg.s0[0] < 0 ? -lg.s0[0] : lg.s0[0]) : 0;
+    const int64_t s_k0 = pl.k.n ? (short_is_n ? pl.k.s0[0] : pl.k.s1[0]) : 0;
+    const int64_t sk = s_k0 < 0 ? -s_k0 : s_k0;
+    return !(s_row == 0 || (sk != 0 && sk < s_row));
+}
+
+size_t skinny_workspace_bytes(const Plan &p, DType t, int num_sms)
+{
+    const size_t acc = (t == DT_BF16 || t == DT_F32) ? 4 : (t == DT_C64 ? 16 : 8);
+    const int sp = skinny_splits(p, skinny_rows_mode(p), num_sms);
+    const int64_t R = std::max(p.M, p.N), S = std::min(p.M, p.N);
+    size_t bytes = sizeof(int64_t) * 2 * (size_t)(p.M + p.N + p.K) + 256;
+    if (sp > 1) bytes += acc * (size_t)sp * S * R + 256;
+    return bytes;
 }
 
 bool skinny_applicable(const Plan &p)
@@ -380,16 +529,29 @@ bool skinny_applicable(const Plan &p)
     return std::min(p.M, p.N) <= SKINNY_MAX_S && p.K > 1;
 }
 
-template <class T>
-cudaError_t skinny_typed(const SkinnyParams &p, bool warp_per_row, int num_sms, cudaStream_t s)
+template <class T, int SM>
+void skinny_main(const SkinnyParams &p, bool rows_mode, cudaStream_t s)
 {
-    if (warp_per_row) {
-        int64_t blocks = std::min<int64_t>((p.R + 7) / 8, (int64_t)num_sms * 8);
-        skinny_warp_kernel<T><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(p);
+    if (rows_mode) {
+        dim3 grid((unsigned)((p.R + 31) / 32), (unsigned)p.splits);
+        skinny_rows_kernel<T, SM><<<grid, 256, 0, s>>>(p);
     } else {
-        int64_t blocks = std::min<int64_t>((p.R + 255) / 256, (int64_t)num_sms * 8);
-        skinny_thread_kernel<T><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(p);
+        dim3 grid((unsigned)((p.R + 7) / 8), (unsigned)p.splits);
+        skinny_warp_kernel<T, SM><<<grid, 256, 0, s>>>(p);
     }
+}
+
+template <class T>
+cudaError_t skinny_typed(const SkinnyParams &p, bool rows_mode, int num_sms, cudaStream_t s)
+{
+    if (p.S <= 1) skinny_main<T, 1>(p, rows_mode, s);
+    else if (p.S <= 2) skinny_main<T, 2>(p, rows_mode, s);
+    else if (p.S <= 4) skinny_main<T, 4>(p, rows_mode, s);
+    else skinny_main<T, 8>(p, rows_mode, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || p.splits == 1) return e;
+    const int64_t SR = (int64_t)p.S * p.R;
+    skinny_reduce_kernel<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((SR + 255) / 256, num_sms * 8)), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -440,18 +602,18 @@ cudaError_t launch_skinny(const Plan &pl, DType t, const void *A, const void *B,
         p.kY = kA;
         p.R = pl.N;
     }
-    // lanes along k when the long operand is contiguous along k
-    const ModeList &lg = short_is_n ? pl.m : pl.n;
-    const int64_t s_row = lg.n ? (lg.s0[0] < 0 ? -lg.s0[0] : lg.s0[0]) : 0;
-    const int64_t s_k = pl.k.n ? (short_is_n ? pl.k.s0[0] : pl.k.s1[0]) : 0;
-    const int64_t sk = s_k < 0 ? -s_k : s_k;
-    const bool warp_per_row = s_row == 0 || (sk != 0 && sk < s_row);
+    const bool rows_mode = skinny_rows_mode(pl);
+    p.splits = skinny_splits(pl, rows_mode, num_sms);
+    p.kps = (pl.K + p.splits - 1) / p.splits;
+    p.splits = (int)((pl.K + p.kps - 1) / p.kps);
+    p.partial = p.splits > 1 ? static_cast<char *>(ws) + ((sizeof(int64_t) * 2 * (size_t)(pl.M + pl.N + pl.K) + 255) & ~size_t(255))
+                             : nullptr;
     switch (t) {
-    case DT_F32: return skinny_typed<float>(p, warp_per_row, num_sms, s);
-    case DT_F64: return skinny_typed<double>(p, warp_per_row, num_sms, s);
-    case DT_C32: return skinny_typed<cf>(p, warp_per_row, num_sms, s);
-    case DT_C64: return skinny_typed<zd>(p, warp_per_row, num_sms, s);
-    case DT_BF16: return skinny_typed<uint16_t>(p, warp_per_row, num_sms, s);
+    case DT_F32: return skinny_typed<float>(p, rows_mode, num_sms, s);
+    case DT_F64: return skinny_typed<double>(p, rows_mode, num_sms, s);
+    case DT_C32: return skinny_typed<cf>(p, rows_mode, num_sms, s);
+    case DT_C64: return skinny_typed<zd>(p, rows_mode, num_sms, s);
+    case DT_BF16: return skinny_typed<uint16_t>(p, rows_mode, num_sms, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -28,7 +28,7 @@ cudaError_t launch_outer(const Plan &p, DType t, const void *A, const void *B, v
 constexpr int OUTER_MAX_SUM = 8;
 // SKINNY: one free class of at most 8 indices, K > 1.
 bool skinny_applicable(const Plan &p);
-size_t skinny_workspace_bytes(const Plan &p);
+size_t skinny_workspace_bytes(const Plan &p, DType t, int num_sms);
 cudaError_t launch_skinny(const Plan &p, DType t, const void *A, const void *B, void *C, int num_sms, void *ws,
                           cudaStream_t s);
 // REDUCE: few outputs (M*N small), long sums; deterministic two-pass.

@@ -42,7 +42,8 @@ Choice heuristic_choice(const Plan &p, DType t, int num_sms)
         c.family = GETT_FAMILY_SKINNY;
         return c;
     }
-    if (t == DT_BF16 && p.M >= 128 && p.N >= 128 && p.K >= 64) {
+    // bf16 operands: tensor cores once the packing pays for itself
+    if (t == DT_BF16 && p.M >= 512 && p.N >= 512 && p.K >= 256) {
         c.family = GETT_FAMILY_TC;
         c.algo = GETT_ALGO_NATIVE;
         return c;

@@ -3,8 +3,10 @@
     python -m paper_2410_06770_gb300.profile_case WORKLOAD [SCALE] [--calls N] [--algo A]
 
 WORKLOAD: cc, cc_perm_transA (extents a..d = SCALE, i,j = SCALE/4), stream
-(A(SCALE, SCALE, 64) x B(64, 8)), small, batched (SCALE contractions of the
-batched workload, one persistent launch per call).  Inputs are generated on the host,
+(A(SCALE, SCALE, 64) x B(64, 8)), small, gemv (A(SCALE, SCALE) x B(SCALE, 2),
+the second mode of A contracted), inner (A and B of extents SCALE^4, every
+mode contracted), batched (SCALE contractions of the batched workload, one
+persistent launch per call).  gemv and inner draw uniform values on the device.  Inputs are generated on the host,
 copied once, then the call is made N times (default 2) and synchronised.
 """
 import argparse
@@ -35,6 +37,26 @@ def main(argv=None):
             b.launch()
         torch.cuda.synchronize()
         print(b.info())
+        return 0
+    if args.workload in ("gemv", "inner"):
+        s = args.scale
+        if args.workload == "gemv":
+            sig = synth.Signature((s, s), (s, 2), (1,), (0,), (0, 1))
+        else:
+            sig = synth.Signature((s,) * 4, (s,) * 4, (0, 1, 2, 3), (0, 1, 2, 3), ())
+        la, lb, lc = (synth.layout_contiguous(e) for e in (sig.exta, sig.extb, sig.extc()))
+        g = torch.Generator(device="cuda")
+        g.manual_seed(9)
+        dt = torch.float32 if args.prefix == "s" else torch.float64
+        dA = torch.rand(la.size, dtype=dt, device="cuda", generator=g)
+        dB = torch.rand(lb.size, dtype=dt, device="cuda", generator=g)
+        dC = torch.zeros(lc.size, dtype=dt, device="cuda")
+        rep = None
+        for _ in range(args.calls):
+            _, rep = gett.xgett(args.prefix, len(sig.exta), sig.exta, la.inc, dA, len(sig.extb), sig.extb, lb.inc, dB,
+                                sig.conts, sig.conta, sig.contb, sig.perm, lc.inc, dC, mode="ex")
+        torch.cuda.synchronize()
+        print(rep)
         return 0
     if args.workload == "cc":
         p = synth.cfg_cc("plain", scale=args.scale, small_ij=max(1, args.scale // 4))

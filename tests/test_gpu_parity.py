@@ -152,6 +152,9 @@ STREAM_SHAPES = {
     "gemv_k": (synth.Signature((3000, 45), (45, 1), (1,), (0,), (0, 1)), ("rowmajor", "contig", "contig")),
     # short class on the A side, two contracted modes
     "left_skinny": (synth.Signature((2, 9, 7), (7, 9, 900), (1, 2), (1, 0), (1, 0)), ("padded", "rowmajor", "negative")),
+    # long sums: several staged K chunks per slice, K split into slices, ragged tails, S = 5
+    "gemv_rows_long": (synth.Signature((700, 5000), (5000, 5), (1,), (0,), (0, 1)), ("padded", "contig", "negative")),
+    "gemv_k_long": (synth.Signature((300, 5000), (5000, 3), (1,), (0,), (1, 0)), ("rowmajor", "negative", "padded")),
 }
 
 
