@@ -327,36 +327,44 @@ __device__ __forceinline__ typename R::Acc block_sum(typename R::Acc v, typename
     return s;
 }
 
-template <class T, int NT>
+// UNIT: both operands have increment 1 along the first contracted mode.
+// Otherwise the addresses advance by pointer increments (no per-load
+// multiply).  Each thread keeps four loads of each operand in flight.
+template <class T, int NT, bool UNIT>
 __global__ void __launch_bounds__(NT) reduce_pass1(ReduceParams p)
 {
     using R = Tr<T>;
     using Acc = typename R::Acc;
+    constexpr int U = 4;
     __shared__ Acc red[NT / 32];
     const T *A = static_cast<const T *>(p.A);
     const T *B = static_cast<const T *>(p.B);
     Acc *P = static_cast<Acc *>(p.partial);
     const int g = blockIdx.x;
     const int64_t lo = p.K * g / p.G, hi = p.K * (g + 1) / p.G;
+    const int64_t sa = UNIT ? 1 : p.sa0, sb = UNIT ? 1 : p.sb0;
     for (int64_t o = 0; o < p.O; ++o) {
         int64_t oam, ocm, obn, ocn;
         decode2(p.m, o % p.M, oam, ocm);
         decode2(p.n, o / p.M, obn, ocn);
-        Acc acc[4] = {R::zero(), R::zero(), R::zero(), R::zero()};
+        Acc acc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] = R::zero();
         int64_t k = lo;
         while (k < hi) {
             const int64_t k0 = k % p.e0;
             const int64_t seg = min(hi - k, p.e0 - k0);
             int64_t oa, ob;
             decode2(p.kr, k / p.e0, oa, ob);
-            const T *a = A + oam + oa + k0 * p.sa0;
-            const T *b = B + obn + ob + k0 * p.sb0;
-            for (int64_t j = threadIdx.x; j < seg; j += 4 * NT) {
+            const T *a = A + oam + oa + (k0 + threadIdx.x) * sa;
+            const T *b = B + obn + ob + (k0 + threadIdx.x) * sb;
+            const int64_t da = (int64_t)NT * sa, db = (int64_t)NT * sb;
+            for (int64_t j = threadIdx.x; j < seg; j += U * NT) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    int64_t jj = j + u * NT;
-                    if (jj < seg) R::mac(acc[u], R::load(a + jj * p.sa0), R::load(b + jj * p.sb0));
-                }
+                for (int u = 0; u < U; ++u)
+                    if (j + u * NT < seg) R::mac(acc[u], R::load(a + u * da), R::load(b + u * db));
+                a += U * da;
+                b += U * db;
             }
             k += seg;
         }
@@ -423,14 +431,15 @@ template <class T>
 cudaError_t reduce_typed(const ReduceParams &p, cudaStream_t s)
 {
     constexpr int NT = 256;
-    reduce_pass1<T, NT><<<p.G, NT, 0, s>>>(p);
+    if (p.sa0 == 1 && p.sb0 == 1) reduce_pass1<T, NT, true><<<p.G, NT, 0, s>>>(p);
+    else reduce_pass1<T, NT, false><<<p.G, NT, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     reduce_pass2<T, NT><<<(unsigned)p.O, NT, 0, s>>>(p);
     return cudaGetLastError();
 }
 
-int reduce_grid(int num_sms) { return num_sms * 4; }
+int reduce_grid(int num_sms) { return num_sms * 8; }
 
 }  // namespace
 
