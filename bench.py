@@ -8,8 +8,16 @@ N(0,1) inputs, column-major -- 0.55 TFLOP per call.  A step is one dgett call
 (2.1 GB) is larger than L2, so no flush is needed between steps.
 
 Extra measured forms (not part of `value`): the same contraction with output
-permutation (i,a,j,b) and row-major A, the streaming outer product, and the
-small 32x24x16x20 DGETT.
+permutation (i,a,j,b) and row-major A, the streaming outer product, the small
+32x24x16x20 DGETT, the split-precision forms (modular DGETT on bf16 tensor
+cores with sampled parity, every precision form on log-uniform data, complex
+split ZGETT), the inner product (REDUCE) and matrix-vector (SKINNY) kernels
+against their HBM and FP64-FMA floors, and the batched persistent launch of
+4096 contractions (heuristic, tuned and learned configurations).
+
+`e2e`: the same call with pinned host buffers; each step's uploads of A, B, C
+and the download of C are inside the timed region (pipelined over two device
+buffer sets).
 
 --impl reference times the CPU oracle (the plain Alg. 1 loop nest) on the
 host cores on a bounded sample of the same workload.
@@ -416,37 +424,63 @@ def sampled_parity(p, Cbuf, nsamples=128):
 
 
 def e2e_measure(p, flops, call_host, dA, dB, dC, a, stream, steps):
-    """Host buffers in pinned memory; per step: H2D of A, B, C, the dgett call,
-    D2H of C, all inside the timed region."""
+    """Host buffers in pinned memory.  Every step copies its A, B and C from
+    the host, runs the dgett call and copies C back, all inside the timed
+    region.  Two device buffer sets and separate H2D / D2H streams let step
+    i+1's upload overlap step i's contraction (a serving pipeline); step i+2
+    reuses set i only after set i's result has reached the host."""
     import torch
     from paper_2410_06770_gb300 import gett
     hA = torch.from_numpy(p.A).pin_memory()
     hB = torch.from_numpy(p.B).pin_memory()
     hC = torch.from_numpy(p.C).pin_memory()
-    hOut = torch.empty_like(hC).pin_memory()
+    sets = [(dA, dB, dC), (torch.empty_like(dA), torch.empty_like(dB), torch.empty_like(dC))]
+    outs = [torch.empty_like(hC).pin_memory(), torch.empty_like(hC).pin_memory()]
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def step():
-        dA.copy_(hA, non_blocking=True)
-        dB.copy_(hB, non_blocking=True)
-        dC.copy_(hC, non_blocking=True)
-        gett.xgett("d", a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"], a["INCB"], dB,
-                   a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], dC,
-                   a_off=p.la.off, b_off=p.lb.off, c_off=p.lc.off, mode="async", stream=stream.cuda_stream)
-        hOut.copy_(dC, non_blocking=True)
+    def run(nsteps, e_start=None):
+        free = [None, None]
+        for i in range(nsteps):
+            k = i % 2
+            xA, xB, xC = sets[k]
+            with torch.cuda.stream(h2d):
+                if free[k] is not None:
+                    h2d.wait_event(free[k])
+                xA.copy_(hA, non_blocking=True)
+                xB.copy_(hB, non_blocking=True)
+                xC.copy_(hC, non_blocking=True)
+                ready = torch.cuda.Event()
+                ready.record(h2d)
+            stream.wait_event(ready)
+            gett.xgett("d", a["RANKA"], a["EXTA"], a["INCA"], xA, a["RANKB"], a["EXTB"], a["INCB"], xB,
+                       a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], xC,
+                       a_off=p.la.off, b_off=p.lb.off, c_off=p.lc.off, mode="async", stream=stream.cuda_stream)
+            done = torch.cuda.Event()
+            done.record(stream)
+            with torch.cuda.stream(d2h):
+                d2h.wait_event(done)
+                outs[k].copy_(xC, non_blocking=True)
+                free[k] = torch.cuda.Event()
+                free[k].record(d2h)
+        for ev in free:
+            if ev is not None:
+                stream.wait_event(ev)
 
-    step()
+    run(2)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(steps):
-        step()
+    h2d.wait_stream(stream)
+    run(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     bi = hA.numel() * 8 + hB.numel() * 8 + hC.numel() * 8
-    bo = hOut.numel() * 8
+    bo = outs[0].numel() * 8
+    del sets[1]
     return {"value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": bi,
-            "d2h_bytes_per_step": bo, "ms_per_step": ms, "steps": steps}
+            "d2h_bytes_per_step": bo, "ms_per_step": ms, "steps": steps,
+            "pipeline": "2 device buffer sets; H2D of step i+1 overlaps the call of step i"}
 
 
 def time_calls(call, reps, warm=2):
@@ -735,6 +769,20 @@ def measure_forms(main_workload):
             mp = measured_peaks()
             entry["hbm_frac"] = entry["gbs"] / mp.get("hbm_gbs", 6800.0)
         out[name] = entry
+        if name == "stream":
+            # the scaled form with beta = 0 writes C without reading it
+            def call0():
+                return gett.xgett("d", a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"], a["INCB"], dB,
+                                  a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], dC,
+                                  a_off=p.la.off, b_off=p.lb.off, c_off=p.lc.off, mode="scaled", alpha=1.0,
+                                  beta=0.0, stream=stream.cuda_stream)
+            best0, _ = time_calls(call0, 5)
+            nb0 = 8.0 * (p.la.numel + p.lb.numel + p.lc.numel)
+            mp = measured_peaks()
+            out["stream_beta0"] = {"workload": desc + ", scaled form alpha = 1, beta = 0 (C not read)",
+                                   "ms": best0, "gbs": nb0 / (best0 * 1e-3) / 1e9,
+                                   "hbm_frac": nb0 / (best0 * 1e-3) / 1e9 / mp.get("hbm_gbs", 6800.0),
+                                   "speedup_vs_accumulate": ms / best0}
         del dA, dB, dC
         torch.cuda.empty_cache()
     return out

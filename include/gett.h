@@ -217,6 +217,50 @@ int sbgett_ex(int RANKA, const int64_t *EXTA, const int64_t *INCA, const uint16_
               const gett_options *opt, gett_report *rep, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Scaled form: C <- alpha * (A . B) + beta * C.                           */
+/* Alg. 1 only accumulates (C <- C + A . B); the scaling follows the       */
+/* ALPHA and BETA arguments of xGEMM and xGEMV (Sec. 2.3.1): the product   */
+/* is scaled by ALPHA and added to C scaled by BETA.                       */
+/*   alpha, beta: host pointers to one value of C's element type (float    */
+/*     for s and sb, double for d, {re, im} pairs for c and z), read       */
+/*     during the call; NULL -> GETT_ERR_ARG at position 15 / 16.          */
+/*   beta == 0: C is written without being read (it may hold NaN or        */
+/*     uninitialised values), as in BLAS.                                  */
+/*   alpha == 0, or an empty sum (a contracted extent 0): A and B are not  */
+/*     read; C <- beta * C (zeros when beta == 0; nothing when beta == 1). */
+/*   alpha == 1 and beta == 1 is exactly xgett_ex.                         */
+/* Every other argument, the options, the report and the synchronisation  */
+/* behave as in xgett_ex (the call returns after completion on `stream`).  */
+/* Complex split precision (GETT_ALGO_OZAKI_BF16 on z) with a non-real     */
+/* alpha or beta stages the product in workspace (16 bytes per output).    */
+/* ---------------------------------------------------------------------- */
+int sgett_scaled(int RANKA, const int64_t *EXTA, const int64_t *INCA, const float *A,
+                 int RANKB, const int64_t *EXTB, const int64_t *INCB, const float *B,
+                 int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                 const int64_t *INCC, float *C, const float *alpha, const float *beta,
+                 const gett_options *opt, gett_report *rep, void *stream);
+int dgett_scaled(int RANKA, const int64_t *EXTA, const int64_t *INCA, const double *A,
+                 int RANKB, const int64_t *EXTB, const int64_t *INCB, const double *B,
+                 int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                 const int64_t *INCC, double *C, const double *alpha, const double *beta,
+                 const gett_options *opt, gett_report *rep, void *stream);
+int cgett_scaled(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_float *A,
+                 int RANKB, const int64_t *EXTB, const int64_t *INCB, const gett_complex_float *B,
+                 int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                 const int64_t *INCC, gett_complex_float *C, const gett_complex_float *alpha,
+                 const gett_complex_float *beta, const gett_options *opt, gett_report *rep, void *stream);
+int zgett_scaled(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_double *A,
+                 int RANKB, const int64_t *EXTB, const int64_t *INCB, const gett_complex_double *B,
+                 int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                 const int64_t *INCC, gett_complex_double *C, const gett_complex_double *alpha,
+                 const gett_complex_double *beta, const gett_options *opt, gett_report *rep, void *stream);
+int sbgett_scaled(int RANKA, const int64_t *EXTA, const int64_t *INCA, const uint16_t *A,
+                  int RANKB, const int64_t *EXTB, const int64_t *INCB, const uint16_t *B,
+                  int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                  const int64_t *INCC, float *C, const float *alpha, const float *beta,
+                  const gett_options *opt, gett_report *rep, void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Allocation-free double-precision form.  The thesis has no counterpart;  */
 /* this entry point exists for callers that must not allocate device       */
 /* memory while they run (a process that budgets all device memory up     */

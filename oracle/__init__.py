@@ -12,6 +12,9 @@ numpy buffers.  Precisions:
   'z'      -- complex double, no conjugation;
   'direct' -- second, independent implementation (flat-index decode, no
               odometer) in double, for brute-force cross-checks.
+`gett_scaled()` is the scaled form C <- alpha * S + beta * C (the ALPHA and
+BETA of xGEMM, Sec. 2.3.1): S is Alg. 1 run on a zeroed C, combined with the
+original C element by element in double (complex double for c/z).
 Float32 and bfloat16 inputs are widened exactly to double before the call, so
 the oracle of every precision form is the fp64 (or long double) contraction of
 the exact input values.
@@ -136,6 +139,39 @@ def gett_problem(p, precision="f64", nthreads=1, C=None) -> np.ndarray:
     if rc != 0:
         raise ValueError(f"oracle rejected the problem (code {rc})")
     return Cw
+
+
+def output_positions(extc, incc, off) -> np.ndarray:
+    """Buffer positions of every logical output element (first mode fastest):
+    off + sum_q o_q INCC[q]."""
+    pos = np.array([int(off)], dtype=np.int64)
+    for e, inc in zip(extc, incc):
+        # each later mode is slower than the ones already in pos
+        pos = (pos[None, :] + np.arange(int(e), dtype=np.int64)[:, None] * int(inc)).reshape(-1)
+    return pos
+
+
+def gett_scaled(p, alpha, beta, precision="f64", nthreads=1) -> np.ndarray:
+    """The scaled form C <- alpha * S + beta * C, S the contraction's sum over
+    the contracted indices (xGEMM's ALPHA and BETA, Sec. 2.3.1; the sum itself
+    is Alg. 1 run on a zeroed C, so it starts from 0).  beta == 0 does not read
+    C (NaN there does not propagate); alpha == 0 does not form S.  Returns the
+    updated (widened) C buffer; elements outside the output layout keep their
+    values."""
+    C0 = widen(p.C).copy()
+    a = p.args()
+    pos = output_positions(p.sig.extc(), a["INCC"], p.lc.off)
+    out = C0.copy()
+    alpha = complex(alpha) if C0.dtype.kind == "c" else float(np.real(alpha))
+    beta = complex(beta) if C0.dtype.kind == "c" else float(np.real(beta))
+    if alpha != 0:
+        Z = C0.copy()
+        Z[pos] = 0
+        S = gett_problem(p, precision, nthreads, C=Z)[pos]
+        out[pos] = alpha * S if beta == 0 else alpha * S + beta * C0[pos]
+    else:
+        out[pos] = 0 if beta == 0 else beta * C0[pos]
+    return out
 
 
 def inc_coords(coords, exts):

@@ -112,8 +112,31 @@ cudaError_t run_family(const Plan &p, DType t, const Choice &ch, const void *A, 
     return e;
 }
 
+// C <- beta * C only (the scaled form with alpha == 0 or an empty sum): A and
+// B are not read.
+int run_scale_only(DType t, const Plan &p, void *C, cudaStream_t s, bool sync)
+{
+    if (p.M * p.N == 0) return GETT_OK;
+    if (p.sc.br == 1.0 && p.sc.bi == 0.0) return GETT_OK;
+    if (!C || reinterpret_cast<uintptr_t>(C) % out_align(t)) {
+        set_last_error_arg(14);
+        return GETT_ERR_ARG;
+    }
+    if (!p.c_injective) return GETT_ERR_ALIAS;
+    DevState *st = nullptr;
+    int rc = dev_state(&st);
+    if (rc != GETT_OK) return rc;
+    cudaError_t e = launch_scale_c(p, t, C, st->sms, s);
+    if (e == cudaSuccess && sync) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    return GETT_OK;
+}
+
 int run(DType t, const Args &a, const void *A, const void *B, void *C, const gett_options *opt,
-        gett_report *rep, cudaStream_t s, bool sync)
+        gett_report *rep, cudaStream_t s, bool sync, const Scale *scale = nullptr, bool alpha_zero = false)
 {
     Plan p;
     int bad = 0;
@@ -123,6 +146,13 @@ int run(DType t, const Args &a, const void *A, const void *B, void *C, const get
     if (rep) {
         std::memset(rep, 0, sizeof(*rep));
         rep->family = GETT_FAMILY_NOOP;
+    }
+    if (scale) {
+        p.sc = *scale;
+        if (p.zero_sum || (alpha_zero && !p.empty)) {
+            if (!p.zero_sum) p.c_injective = true;  // make_plan returned GETT_ERR_ALIAS otherwise
+            return run_scale_only(t, p, C, s, sync);
+        }
     }
     if (p.empty) return GETT_OK;
     const size_t esz = dtype_size(t), osz = out_elem_size(t);
@@ -208,6 +238,47 @@ using gett::Args;
     {                                                                                             \
         return gett::run(gett::DT, GETT_ARGS, A, B, C, opt, rep, (cudaStream_t)stream, true);    \
     }
+
+namespace gett {
+namespace {
+void re_im(const float *x, double *re, double *im) { *re = *x; *im = 0.0; }
+void re_im(const double *x, double *re, double *im) { *re = *x; *im = 0.0; }
+void re_im(const gett_complex_float *x, double *re, double *im) { *re = x->re; *im = x->im; }
+void re_im(const gett_complex_double *x, double *re, double *im) { *re = x->re; *im = x->im; }
+
+// alpha == 1 and beta == 1 is Alg. 1's accumulation; beta == 0 never reads C.
+template <class TC>
+int scale_of(const TC *alpha, const TC *beta, Scale *sc, bool *alpha_zero)
+{
+    if (!alpha) { set_last_error_arg(15); return GETT_ERR_ARG; }
+    if (!beta) { set_last_error_arg(16); return GETT_ERR_ARG; }
+    re_im(alpha, &sc->ar, &sc->ai);
+    re_im(beta, &sc->br, &sc->bi);
+    *alpha_zero = sc->ar == 0.0 && sc->ai == 0.0;
+    if (sc->ar == 1.0 && sc->ai == 0.0 && sc->br == 1.0 && sc->bi == 0.0) sc->mode = SCALE_ACC;
+    else if (sc->br == 0.0 && sc->bi == 0.0) sc->mode = SCALE_AX;
+    else sc->mode = SCALE_AXPBY;
+    return GETT_OK;
+}
+}  // namespace
+}  // namespace gett
+
+#define DEFINE_SCALED(prefix, T, TC, DT)                                                             \
+    extern "C" int prefix##gett_scaled(GETT_ARGS_DECL(T), TC *C, const TC *alpha, const TC *beta,      \
+                                       const gett_options *opt, gett_report *rep, void *stream)        \
+    {                                                                                                 \
+        gett::Scale sc{};                                                                             \
+        bool az = false;                                                                              \
+        int rc = gett::scale_of(alpha, beta, &sc, &az);                                               \
+        if (rc != GETT_OK) return rc;                                                                 \
+        return gett::run(gett::DT, GETT_ARGS, A, B, C, opt, rep, (cudaStream_t)stream, true, &sc, az); \
+    }
+
+DEFINE_SCALED(s, float, float, DT_F32)
+DEFINE_SCALED(d, double, double, DT_F64)
+DEFINE_SCALED(c, gett_complex_float, gett_complex_float, DT_C32)
+DEFINE_SCALED(z, gett_complex_double, gett_complex_double, DT_C64)
+DEFINE_SCALED(sb, uint16_t, float, DT_BF16)
 
 DEFINE_ENTRY(s, float, float, DT_F32)
 DEFINE_ENTRY(d, double, double, DT_F64)

@@ -149,6 +149,33 @@ template <> struct Tr<zd> {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Scaled epilogue: C <- alpha * v + beta * C, or C <- C + v (see Scale).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float scale_by(float v, double re, double) { return (float)re * v; }
+__device__ __forceinline__ double scale_by(double v, double re, double) { return re * v; }
+__device__ __forceinline__ cf scale_by(cf v, double re, double im)
+{
+    const float a = (float)re, b = (float)im;
+    return cf{a * v.re - b * v.im, a * v.im + b * v.re};
+}
+__device__ __forceinline__ zd scale_by(zd v, double re, double im)
+{
+    return zd{re * v.re - im * v.im, re * v.im + im * v.re};
+}
+
+template <class R>
+__device__ __forceinline__ void epi_store(typename R::Out *c, typename R::Acc v, const Scale &sc)
+{
+    if (sc.mode == SCALE_ACC) {
+        R::store_add(c, v);
+    } else if (sc.mode == SCALE_AX) {
+        R::store_c(c, scale_by(v, sc.ar, sc.ai));
+    } else {
+        R::store_c(c, R::add(scale_by(v, sc.ar, sc.ai), scale_by(R::load_c(c), sc.br, sc.bi)));
+    }
+}
+
 // Warp shuffles for every arithmetic type (used by the reductions).
 __device__ __forceinline__ float shfl_down(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ double shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }

@@ -1,4 +1,5 @@
 // dense_tile.cuh -- one BM x BN output tile of C[m,n] += sum_k A[m,k] B[k,n]
+// (or the scaled form alpha * sum + beta * C)
 // on CUDA cores, with A, B and C addressed through the planner's offset
 // tables.  Used by the single-call dense kernel and the batched persistent
 // kernel.
@@ -24,6 +25,7 @@ struct TileArgs {
     int64_t kbeg, kend;  // contracted range of this tile
     int a_m_fast, b_n_fast, c_m_fast;
     void *partial;       // if set: write the tile (Acc) here instead of adding into C
+    Scale sc;            // how the tile meets C (SCALE_ACC: C += tile)
 };
 
 // sA: 2*BK*BM, sB: 2*BK*BN shared arrays; sRowA: BM, sColB: BN.
@@ -150,13 +152,25 @@ __device__ __forceinline__ void dense_tile(const TileArgs &p, typename Tr<T>::Ac
         int64_t n = n0 + tn + j * (BN / TN);
         cc[j] = n < p.N ? p.colC[n] : 0;
     }
+    if (p.sc.mode == SCALE_ACC) {
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        int64_t m = m0 + tm + i * (BM / TM);
+        for (int i = 0; i < TM; ++i) {
+            int64_t m = m0 + tm + i * (BM / TM);
 #pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            int64_t n = n0 + tn + j * (BN / TN);
-            if (m < p.M && n < p.N) R::store_add(C + rc[i] + cc[j], acc[i][j]);
+            for (int j = 0; j < TN; ++j) {
+                int64_t n = n0 + tn + j * (BN / TN);
+                if (m < p.M && n < p.N) R::store_add(C + rc[i] + cc[j], acc[i][j]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            int64_t m = m0 + tm + i * (BM / TM);
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                int64_t n = n0 + tn + j * (BN / TN);
+                if (m < p.M && n < p.N) epi_store<R>(C + rc[i] + cc[j], acc[i][j], p.sc);
+            }
         }
     }
 }

@@ -22,6 +22,18 @@ inline size_t dtype_size(DType t)
     return 0;
 }
 
+// How a kernel's result v meets C (the scaled form follows xGEMM's ALPHA and
+// BETA, Sec. 2.3.1: C <- alpha * A.B + beta * C).  SCALE_ACC is Alg. 1's
+// accumulation C <- C + v and the default (a zero-initialised Scale);
+// SCALE_AXPBY writes alpha * v + beta * C; SCALE_AX writes alpha * v without
+// reading C (beta == 0).  alpha = ar + i ai, beta = br + i bi (the imaginary
+// parts are ignored for real types; float types round them to float).
+enum ScaleMode : int { SCALE_ACC = 0, SCALE_AXPBY = 1, SCALE_AX = 2 };
+struct Scale {
+    int mode;
+    double ar, ai, br, bi;
+};
+
 // One class of modes after planning.  For M: s0 = INCA, s1 = INCC.  For N:
 // s0 = INCB, s1 = INCC.  For K: s0 = INCA, s1 = INCB.  Modes are ordered
 // from fastest (index 0) to slowest; a flat class index i decodes with the
@@ -39,7 +51,15 @@ struct Plan {
     ModeList m, n, k;
     int64_t M, N, K;
     int64_t offA, offB, offC;  // element offsets applied to the user pointers
-    bool empty;                // M*N == 0 or K == 0: nothing to do
+    bool empty;                // M*N == 0 or K == 0: nothing to accumulate
+    // K == 0 with M*N > 0: the sum is empty but m and n are planned (the
+    // scaled form still writes beta * C); c_injective records whether C's
+    // layout passed the injectivity test in that case
+    bool zero_sum;
+    bool c_injective;
+    // how the sum meets C; make_plan sets SCALE_ACC (Alg. 1), the scaled
+    // entry points overwrite it
+    Scale sc;
     // address spans (elements, relative to the user pointers) for alias checks
     int64_t a_lo, a_hi, b_lo, b_hi, c_lo, c_hi;
 };

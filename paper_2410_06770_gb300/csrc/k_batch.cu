@@ -85,6 +85,7 @@ __device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tab
     a.b_n_fast = pr.b_n_fast;
     a.c_m_fast = pr.c_m_fast;
     a.partial = pr.splits > 1 ? pr.partial + (int64_t)split * pr.M * pr.N : nullptr;
+    a.sc = Scale{};
     dense_tile<T, c.bm, c.bn, c.bk, c.tm, c.tn>(a, smem_f, smem_f + 2 * c.bk * c.bm, smem_i, smem_i + c.bm);
 }
 

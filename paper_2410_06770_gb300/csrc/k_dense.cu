@@ -49,6 +49,7 @@ struct DenseParams {
     int tiles_m, tiles_n;
     int a_m_fast, b_n_fast, c_m_fast;
     void *partial;  // split-K partial tiles (Acc), null when S == 1
+    Scale sc;       // how the sum meets C
 };
 
 template <class T, int BM, int BN, int BK, int TM, int TN>
@@ -81,6 +82,7 @@ dense_kernel(DenseParams p)
     a.b_n_fast = p.b_n_fast;
     a.c_m_fast = p.c_m_fast;
     a.partial = p.partial ? static_cast<Acc *>(p.partial) + (int64_t)split * p.M * p.N : nullptr;
+    a.sc = p.sc;
     dense_tile<T, BM, BN, BK, TM, TN>(a, sA, sB, sRowA, sColB);
 }
 
@@ -100,7 +102,7 @@ __global__ void splitk_reduce_kernel(DenseParams p, int S)
         else { n = i % p.N; m = i / p.N; }
         Acc s = P[i];
         for (int t = 1; t < S; ++t) s = R::add(s, P[(int64_t)t * MN + i]);
-        R::store_add(C + p.rowC[m] + p.colC[n], s);
+        epi_store<R>(C + p.rowC[m] + p.colC[n], s, p.sc);
     }
 }
 
@@ -228,6 +230,7 @@ cudaError_t launch_dense(const Plan &pl, DType t, const void *A, const void *B, 
     p.a_m_fast = (am != 0 && (ak == 0 || am <= ak)) ? 1 : 0;
     p.b_n_fast = (bn != 0 && (bk == 0 || bn <= bk)) ? 1 : 0;
     p.c_m_fast = (cm != 0 && (cn == 0 || cm <= cn)) ? 1 : 0;
+    p.sc = pl.sc;
     p.partial = S > 1 ? static_cast<char *>(ws) + align256(sizeof(int64_t) * 2 * (size_t)(pl.M + pl.N + pl.K))
                       : nullptr;
     if ((int64_t)p.tiles_m * p.tiles_n > (int64_t)INT32_MAX || S > 65535) return cudaErrorInvalidValue;

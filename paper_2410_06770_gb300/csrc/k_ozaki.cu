@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
                                                     const unsigned long long *__restrict__ maxB,
                                                     const int64_t *__restrict__ rowC,
                                                     const int64_t *__restrict__ colC, double *__restrict__ C,
-                                                    OzConsts c, int64_t shift_rows)
+                                                    OzConsts c, int64_t shift_rows, Scale sc)
 {
     const int64_t MN = M * N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
@@ -377,8 +377,31 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
         const double f2 = __longlong_as_double((long long)(e2 + 1023) << 52);
         const double val = negv ? -((mag * f1) * f2) : (mag * f1) * f2;
         double *dst = C + rowC[m] + colC[n];
-        *dst = *dst + val;
+        if (sc.mode == SCALE_ACC) *dst = *dst + val;
+        else if (sc.mode == SCALE_AX) *dst = sc.ar * val;
+        else *dst = sc.ar * val + sc.br * *dst;
     }
+}
+
+// Complex scaled form with a non-real alpha or beta: the recombination wrote
+// the real form's values to T (re-rows m < M, im-rows M + m, column pitch 2M);
+// C[rowC[m] + colC[n]] <- alpha * (T_re + i T_im) + beta * C.
+__global__ void oz_complex_combine_kernel(const double *__restrict__ T, int64_t M, int64_t N,
+                                          const int64_t *__restrict__ rowC, const int64_t *__restrict__ colC,
+                                          zd *C, Scale sc)
+{
+    const int64_t MN = M * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i % M, n = i / M;
+        const zd v{T[n * 2 * M + m], T[n * 2 * M + M + m]};
+        epi_store<Tr<zd>>(C + rowC[m] + colC[n], v, sc);
+    }
+}
+
+__global__ void iota_kernel(int64_t *t, int64_t n, int64_t step)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = i * step;
 }
 
 // Offset tables (in doubles) of the real form of a complex contraction:
@@ -482,21 +505,21 @@ void oz_setup(int64_t K, int want_L, OzConsts *c)
 template <int L>
 void launch_crt_t(const int8_t *R, int64_t M, int64_t N, const unsigned long long *maxA,
                   const unsigned long long *maxB, const int64_t *rowC, const int64_t *colC, double *C,
-                  const OzConsts &c, int num_sms, cudaStream_t s, int64_t shift_rows)
+                  const OzConsts &c, int num_sms, cudaStream_t s, int64_t shift_rows, const Scale &sc)
 {
     const int64_t MN = M * N;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((MN + 255) / 256, (int64_t)num_sms * 16));
-    oz_crt_kernel<L><<<blocks, 256, 0, s>>>(R, M, N, maxA, maxB, rowC, colC, C, c, shift_rows);
+    oz_crt_kernel<L><<<blocks, 256, 0, s>>>(R, M, N, maxA, maxB, rowC, colC, C, c, shift_rows, sc);
 }
 
 cudaError_t launch_crt(const int8_t *R, int64_t M, int64_t N, const unsigned long long *maxA,
                        const unsigned long long *maxB, const int64_t *rowC, const int64_t *colC, double *C,
-                       const OzConsts &c, int num_sms, cudaStream_t s, int64_t shift_rows = -1)
+                       const OzConsts &c, int num_sms, cudaStream_t s, const Scale &sc, int64_t shift_rows = -1)
 {
     if (shift_rows <= 0) shift_rows = M;
-#define CASE(L)                                                                       \
-    case L:                                                                           \
-        launch_crt_t<L>(R, M, N, maxA, maxB, rowC, colC, C, c, num_sms, s, shift_rows); \
+#define CASE(L)                                                                           \
+    case L:                                                                               \
+        launch_crt_t<L>(R, M, N, maxA, maxB, rowC, colC, C, c, num_sms, s, shift_rows, sc); \
         break;
     switch (c.L) {
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
@@ -606,7 +629,7 @@ cudaError_t launch_ozaki(const Plan &pl, int L_req, const void *A, const void *B
     p.R = o.R;
     e = launch_tc_gemm(TC_MODE_MOD, o.RA, o.RB, c.L, p, s);
     if (e != cudaSuccess) return e;
-    return launch_crt(o.R, pl.M, pl.N, o.maxA, o.maxB, o.rowC, o.colC, Cb, c, num_sms, s);
+    return launch_crt(o.R, pl.M, pl.N, o.maxA, o.maxB, o.rowC, o.colC, Cb, c, num_sms, s, pl.sc);
 }
 
 namespace {
@@ -617,9 +640,18 @@ struct OzComplexLayout {
     unsigned long long *maxA, *maxB;
     uint16_t *RA, *RB;
     int8_t *R;
+    double *T;              // non-real alpha or beta: [N][2M] real-form result
+    int64_t *rowT, *colT;   // its offset tables
     int64_t ld;
     size_t total;
 };
+
+// A non-real alpha or beta mixes the real and imaginary parts, which the
+// recombination writes from different threads: go through T.
+bool complex_scale_via_temp(const Scale &sc)
+{
+    return sc.mode != SCALE_ACC && (sc.ai != 0.0 || sc.bi != 0.0);
+}
 
 OzComplexLayout oz_complex_layout(const Plan &p, int L, void *ws)
 {
@@ -642,6 +674,11 @@ OzComplexLayout oz_complex_layout(const Plan &p, int L, void *ws)
     o.RA = reinterpret_cast<uint16_t *>(take(2 * (size_t)L * M2 * o.ld));
     o.RB = reinterpret_cast<uint16_t *>(take(2 * (size_t)L * p.N * o.ld));
     o.R = reinterpret_cast<int8_t *>(take((size_t)L * M2 * p.N));
+    if (complex_scale_via_temp(p.sc)) {
+        o.T = reinterpret_cast<double *>(take(8 * (size_t)M2 * p.N));
+        o.rowT = t64(M2);
+        o.colT = t64(p.N);
+    }
     o.total = off;
     return o;
 }
@@ -714,7 +751,21 @@ cudaError_t launch_ozaki_complex(const Plan &pl, int L_req, const void *A, const
     p.R = o.R;
     e = launch_tc_gemm(TC_MODE_MOD, o.RA, o.RB, c.L, p, s);
     if (e != cudaSuccess) return e;
-    return launch_crt(o.R, M2, pl.N, o.maxA, o.maxB, o.rowC2, o.colC2, Cb, c, num_sms, s, pl.M);
+    if (!complex_scale_via_temp(pl.sc))  // real alpha and beta act on each part alone
+        return launch_crt(o.R, M2, pl.N, o.maxA, o.maxB, o.rowC2, o.colC2, Cb, c, num_sms, s, pl.sc, pl.M);
+    {
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((std::max(M2, pl.N) + 255) / 256, 4096));
+        iota_kernel<<<blocks, 256, 0, s>>>(o.rowT, M2, 1);
+        iota_kernel<<<blocks, 256, 0, s>>>(o.colT, pl.N, M2);
+    }
+    const Scale store{SCALE_AX, 1.0, 0.0, 0.0, 0.0};
+    e = launch_crt(o.R, M2, pl.N, o.maxA, o.maxB, o.rowT, o.colT, o.T, c, num_sms, s, store, pl.M);
+    if (e != cudaSuccess) return e;
+    const int64_t MN = pl.M * pl.N;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((MN + 255) / 256, (int64_t)num_sms * 16));
+    oz_complex_combine_kernel<<<blocks, 256, 0, s>>>(o.T, pl.M, pl.N, o.rowC, o.colC, reinterpret_cast<zd *>(C) + pl.offC,
+                                                     pl.sc);
+    return cudaGetLastError();
 }
 
 }  // namespace gett

@@ -53,55 +53,92 @@ struct OuterParams {
     int nk;                       // contracted length (1 for a pure outer product)
     int64_t kx[OUTER_MAX_K];      // offsets of contracted index k in X
     int64_t ky[OUTER_MAX_K];      // and in Y
+    Scale sc;                     // SCALE_AX: C is written without being read
 };
 
-template <class T, int NT>
+// Each work item is one chunk of the run, one index of the run class's other
+// modes and a group of OUTER_NY consecutive indices of the other class: the
+// run operand's values are loaded once per group (registers), the group's
+// operand values and C offsets sit in shared memory.  FP64 arithmetic is
+// scarce on this GPU (about 0.6 T operations/s, so the outer product's one
+// FMA per element is within 1.5x of the HBM time): the scaled forms cost no
+// extra operation per element beyond beta * C.
+constexpr int OUTER_NY = 8;
+
+template <class T, int NT, int KM>
 __global__ void __launch_bounds__(NT) outer_kernel(OuterParams p)
 {
     using R = Tr<T>;
     using Acc = typename R::Acc;
     using Out = typename R::Out;
-    constexpr int U = 4;
+    constexpr int U = sizeof(Acc) > 8 ? 2 : 4;
+    __shared__ Acc sY[OUTER_NY][KM];
+    __shared__ int64_t sOcy[OUTER_NY];
     const T *X = static_cast<const T *>(p.X);
     const T *Y = static_cast<const T *>(p.Y);
     Out *C = static_cast<Out *>(p.C);
+    const bool acc_c = p.sc.mode == SCALE_ACC;
+    const int64_t ngroups = (p.ny + OUTER_NY - 1) / OUTER_NY;
     for (int64_t item = blockIdx.x; item < p.items; item += gridDim.x) {
-        int64_t c = item % p.nchunks;
-        int64_t rest = item / p.nchunks;
-        int64_t ixr = rest % p.nxr;
-        int64_t iy = rest / p.nxr;
-        int64_t ox, ocx, oy, ocy;
+        const int64_t c = item % p.nchunks;
+        const int64_t rest = item / p.nchunks;
+        const int64_t ixr = rest % p.nxr;
+        const int64_t g = rest / p.nxr;
+        const int nyg = (int)min((int64_t)OUTER_NY, p.ny - g * OUTER_NY);
+        int64_t ox, ocx;
         decode2(p.xr, ixr, ox, ocx);
-        decode2(p.y, iy, oy, ocy);
-        Acc yv[OUTER_MAX_K];
+        __syncthreads();  // the previous item's readers are done with sY
+        if (threadIdx.x < OUTER_NY) {
+            const int j = threadIdx.x;
+            int64_t oy = 0, ocy = 0;
+            if (j < nyg) decode2(p.y, g * OUTER_NY + j, oy, ocy);
+            sOcy[j] = ocy;
+            // the scaled forms fold alpha into the staged values, so no
+            // per-element multiply by alpha is needed
 #pragma unroll
-        for (int k = 0; k < OUTER_MAX_K; ++k) yv[k] = k < p.nk ? R::load(Y + oy + p.ky[k]) : R::zero();
+            for (int k = 0; k < KM; ++k) {
+                Acc v = (j < nyg && k < p.nk) ? R::load(Y + oy + p.ky[k]) : R::zero();
+                sY[j][k] = acc_c ? v : scale_by(v, p.sc.ar, p.sc.ai);
+            }
+        }
+        __syncthreads();
         const T *xb = X + ox;
-        Out *cb = C + ocx + ocy;
+        Out *cb = C + ocx;
         const int64_t x0 = c * p.chunk;
         const int64_t x1 = min(p.e0, x0 + p.chunk);
         for (int64_t x = x0 + threadIdx.x; x < x1; x += U * NT) {
-            Acc cv[U];
+            Acc xv[U][KM];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                int64_t xx = x + u * NT;
-                if (xx < x1) cv[u] = R::load_c(cb + xx * p.sc0);
+                const int64_t xx = x + u * NT;
+#pragma unroll
+                for (int k = 0; k < KM; ++k)
+                    xv[u][k] = (k < p.nk && xx < x1) ? R::load(xb + xx * p.sx0 + p.kx[k]) : R::zero();
             }
-            for (int k = 0; k < p.nk; ++k) {
-                Acc xv[U];
+            for (int j = 0; j < nyg; ++j) {
+                Out *cj = cb + sOcy[j];
+                // C's contribution first: C (accumulate), beta * C, or nothing
+                Acc cv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    int64_t xx = x + u * NT;
-                    if (xx < x1) xv[u] = R::load(xb + xx * p.sx0 + p.kx[k]);
+                    const int64_t xx = x + u * NT;
+                    cv[u] = R::zero();
+                    if (xx < x1 && acc_c) cv[u] = R::load_c(cj + xx * p.sc0);
+                    else if (xx < x1 && p.sc.mode == SCALE_AXPBY)
+                        cv[u] = scale_by(R::load_c(cj + xx * p.sc0), p.sc.br, p.sc.bi);
                 }
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (x + u * NT < x1) R::mac(cv[u], xv[u], yv[k]);
-            }
+                for (int k = 0; k < KM; ++k) {
+                    if (k >= p.nk) break;
+                    const Acc yk = sY[j][k];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                int64_t xx = x + u * NT;
-                if (xx < x1) R::store_c(cb + xx * p.sc0, cv[u]);
+                    for (int u = 0; u < U; ++u) R::mac(cv[u], xv[u][k], yk);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t xx = x + u * NT;
+                    if (xx < x1) R::store_c(cj + xx * p.sc0, cv[u]);
+                }
             }
         }
     }
@@ -121,6 +158,7 @@ struct SkinnyParams {
     int splits;                   // K slices (grid.y)
     int64_t kps;                  // K per slice
     void *partial;                // splits > 1: Acc[splits][S][R]
+    Scale sc;
 };
 
 template <class Rt>
@@ -130,7 +168,7 @@ __device__ __forceinline__ void skinny_emit(const SkinnyParams &p, int64_t r, in
     if (p.splits > 1)
         static_cast<Acc *>(p.partial)[((int64_t)blockIdx.y * p.S + s) * p.R + r] = v;
     else
-        Rt::store_add(static_cast<typename Rt::Out *>(p.C) + p.rowC[r] + p.colC[s], v);
+        epi_store<Rt>(static_cast<typename Rt::Out *>(p.C) + p.rowC[r] + p.colC[s], v, p.sc);
 }
 
 // K chunk staged in shared memory by each SKINNY CTA: 2 KB of Acc values
@@ -283,6 +321,23 @@ __global__ void __launch_bounds__(256) skinny_warp_kernel(SkinnyParams p)
     }
 }
 
+// C <- beta * C over the output index space (the scaled form when alpha == 0
+// or the sum is empty); beta == 0 writes zeros without reading C.
+template <class T>
+__global__ void scale_c_kernel(ModeList m, ModeList n, int64_t M, int64_t MN, typename Tr<T>::Out *C, Scale sc)
+{
+    using R = Tr<T>;
+    const bool zero = sc.br == 0.0 && sc.bi == 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a, cm, b, cn;
+        decode2(m, i % M, a, cm);
+        decode2(n, i / M, b, cn);
+        typename R::Out *c = C + cm + cn;
+        if (zero) R::store_c(c, R::zero());
+        else R::store_c(c, scale_by(R::load_c(c), sc.br, sc.bi));
+    }
+}
+
 // C[rowC[r] + colC[s]] += sum of the K-slice partials, slices in order.
 template <class T>
 __global__ void skinny_reduce_kernel(SkinnyParams p)
@@ -295,7 +350,7 @@ __global__ void skinny_reduce_kernel(SkinnyParams p)
         const int64_t r = i % p.R, s = i / p.R;
         Acc v = P[i];
         for (int j = 1; j < p.splits; ++j) v = Rt::add(v, P[(int64_t)j * SR + i]);
-        Rt::store_add(static_cast<typename Rt::Out *>(p.C) + p.rowC[r] + p.colC[s], v);
+        epi_store<Rt>(static_cast<typename Rt::Out *>(p.C) + p.rowC[r] + p.colC[s], v, p.sc);
     }
 }
 
@@ -309,6 +364,7 @@ struct ReduceParams {
     int64_t K, M, O;
     int G;
     void *partial;   // Acc[O * G]
+    Scale sc;
 };
 
 // Sum over the CTA: warp shuffles, then warps in index order (fixed order).
@@ -391,7 +447,7 @@ __global__ void __launch_bounds__(NT) reduce_pass2(ReduceParams p)
         decode2(p.m, o % p.M, oam, ocm);
         decode2(p.n, o / p.M, obn, ocn);
         Out *C = static_cast<Out *>(p.C);
-        R::store_add(C + ocm + ocn, s);
+        epi_store<R>(C + ocm + ocn, s, p.sc);
     }
 }
 
@@ -423,7 +479,11 @@ cudaError_t outer_typed(const OuterParams &p, int num_sms, cudaStream_t s)
     constexpr int NT = 256;
     int64_t blocks = std::min<int64_t>(p.items, (int64_t)num_sms * 8);
     if (blocks < 1) blocks = 1;
-    outer_kernel<T, NT><<<(unsigned)blocks, NT, 0, s>>>(p);
+    // KM >= nk bounds the contracted values held per run element
+    if (p.nk <= 1) outer_kernel<T, NT, 1><<<(unsigned)blocks, NT, 0, s>>>(p);
+    else if (p.nk <= 2) outer_kernel<T, NT, 2><<<(unsigned)blocks, NT, 0, s>>>(p);
+    else if (p.nk <= 4) outer_kernel<T, NT, 4><<<(unsigned)blocks, NT, 0, s>>>(p);
+    else outer_kernel<T, NT, OUTER_MAX_K><<<(unsigned)blocks, NT, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -456,6 +516,7 @@ cudaError_t launch_outer(const Plan &pl, DType t, const void *A, const void *B, 
     else if (pl.n.n == 0) run_in_m = true;
     else run_in_m = pl.m.s1[0] <= pl.n.s1[0];
     OuterParams p{};
+    p.sc = pl.sc;
     p.C = Cb;
     const ModeList &run = run_in_m ? pl.m : pl.n;
     const ModeList &oth = run_in_m ? pl.n : pl.m;
@@ -491,7 +552,7 @@ cudaError_t launch_outer(const Plan &pl, DType t, const void *A, const void *B, 
     p.ny = prod(p.y);
     p.chunk = 8192;
     p.nchunks = (p.e0 + p.chunk - 1) / p.chunk;
-    p.items = p.nchunks * p.nxr * p.ny;
+    p.items = p.nchunks * p.nxr * ((p.ny + OUTER_NY - 1) / OUTER_NY);
     switch (t) {
     case DT_F32: return outer_typed<float>(p, num_sms, s);
     case DT_F64: return outer_typed<double>(p, num_sms, s);
@@ -577,6 +638,7 @@ cudaError_t launch_skinny(const Plan &pl, DType t, const void *A, const void *B,
     const char *Ab = static_cast<const char *>(A) + pl.offA * (int64_t)esz;
     const char *Bb = static_cast<const char *>(B) + pl.offB * (int64_t)esz;
     SkinnyParams p{};
+    p.sc = pl.sc;
     p.C = static_cast<char *>(C) + pl.offC * (int64_t)out_size(t);
     p.K = pl.K;
     // the short class becomes the register-held columns
@@ -627,6 +689,23 @@ cudaError_t launch_skinny(const Plan &pl, DType t, const void *A, const void *B,
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_scale_c(const Plan &pl, DType t, void *C, int num_sms, cudaStream_t s)
+{
+    const int64_t MN = pl.M * pl.N;
+    if (MN == 0) return cudaSuccess;
+    char *Cb = static_cast<char *>(C) + pl.offC * (int64_t)out_size(t);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((MN + 255) / 256, 8LL * num_sms));
+    switch (t) {
+    case DT_F32: scale_c_kernel<float><<<blocks, 256, 0, s>>>(pl.m, pl.n, pl.M, MN, (float *)Cb, pl.sc); break;
+    case DT_F64: scale_c_kernel<double><<<blocks, 256, 0, s>>>(pl.m, pl.n, pl.M, MN, (double *)Cb, pl.sc); break;
+    case DT_C32: scale_c_kernel<cf><<<blocks, 256, 0, s>>>(pl.m, pl.n, pl.M, MN, (cf *)Cb, pl.sc); break;
+    case DT_C64: scale_c_kernel<zd><<<blocks, 256, 0, s>>>(pl.m, pl.n, pl.M, MN, (zd *)Cb, pl.sc); break;
+    case DT_BF16: scale_c_kernel<uint16_t><<<blocks, 256, 0, s>>>(pl.m, pl.n, pl.M, MN, (float *)Cb, pl.sc); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 size_t reduce_workspace_bytes(const Plan &p, DType t, int num_sms)
 {
     size_t acc = (t == DT_BF16 || t == DT_F32) ? 4 : (t == DT_C64 ? 16 : 8);
@@ -638,6 +717,7 @@ cudaError_t launch_reduce(const Plan &pl, DType t, const void *A, const void *B,
 {
     const size_t esz = dtype_size(t);
     ReduceParams p{};
+    p.sc = pl.sc;
     p.A = static_cast<const char *>(A) + pl.offA * (int64_t)esz;
     p.B = static_cast<const char *>(B) + pl.offB * (int64_t)esz;
     p.C = static_cast<char *>(C) + pl.offC * (int64_t)out_size(t);

@@ -216,7 +216,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     const int64_t n = (int64_t)tn * BN + h * 128 + i;
                     if (n < p.N) {
                         float *dst = C + p.colC[n];
-                        *dst = *dst + res[i];
+                        if (p.smode == SCALE_ACC) *dst = *dst + res[i];
+                        else if (p.smode == SCALE_AX) *dst = p.alpha * res[i];
+                        else *dst = p.alpha * res[i] + p.beta * *dst;
                     }
                 }
             }

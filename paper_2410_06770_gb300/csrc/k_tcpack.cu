@@ -198,6 +198,9 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
     p.rowC = rowC;
     p.colC = colC;
     p.c_slice = 0;
+    p.smode = pl.sc.mode;
+    p.alpha = (float)pl.sc.ar;
+    p.beta = (float)pl.sc.br;
     return launch_tc_gemm(TC_MODE_F32, Ap, Bp, 1, p, s);
 }
 

@@ -36,6 +36,10 @@ size_t reduce_workspace_bytes(const Plan &p, DType t, int num_sms);
 cudaError_t launch_reduce(const Plan &p, DType t, const void *A, const void *B, void *C, int num_sms,
                           void *ws, cudaStream_t s);
 
+// C <- beta * C over the planned output (the scaled form with alpha == 0 or
+// an empty sum); uses p.sc's beta.
+cudaError_t launch_scale_c(const Plan &p, DType t, void *C, int num_sms, cudaStream_t s);
+
 // ---- tensor-core forms ----
 // s / bf16 inputs: packed bf16 pieces + one tcgen05 GEMM (k_tcpack.cu)
 int tc_split_blocks(int algo);

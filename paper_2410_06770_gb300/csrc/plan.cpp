@@ -115,6 +115,7 @@ void set_last_cuda_error(int err) { tl_cuda_err = err; }
 int make_plan(const Args &a, Plan *p, int *bad_arg)
 {
     std::memset(p, 0, sizeof(*p));
+    p->sc = Scale{SCALE_ACC, 1.0, 0.0, 1.0, 0.0};
     *bad_arg = 0;
 #define BAD(pos)              \
     do {                      \
@@ -182,15 +183,25 @@ int make_plan(const Args &a, Plan *p, int *bad_arg)
     span_of(a.RANKB, a.EXTB, a.INCB, &p->b_lo, &p->b_hi);
     span_of(rc, extc, a.INCC, &p->c_lo, &p->c_hi);
 
-    bool empty = false;
-    for (int i = 0; i < nm; ++i) empty |= mm[i].ext == 0;
-    for (int i = 0; i < nn_; ++i) empty |= nn[i].ext == 0;
-    for (int i = 0; i < nk; ++i) empty |= kk[i].ext == 0;
-    if (empty) {
+    bool no_out = false, no_sum = false;
+    for (int i = 0; i < nm; ++i) no_out |= mm[i].ext == 0;
+    for (int i = 0; i < nn_; ++i) no_out |= nn[i].ext == 0;
+    for (int i = 0; i < nk; ++i) no_sum |= kk[i].ext == 0;
+    p->zero_sum = false;
+    p->c_injective = true;
+    if (no_out) {
         p->empty = true;
         return GETT_OK;
     }
-    if (rc > 0 && !injective(rc, extc, a.INCC)) return GETT_ERR_ALIAS;
+    const bool inj = rc == 0 || injective(rc, extc, a.INCC);
+    if (no_sum) {
+        // nothing to accumulate; plan m and n only (for beta * C)
+        nk = 0;
+        p->zero_sum = true;
+        p->c_injective = inj;
+    } else if (!inj) {
+        return GETT_ERR_ALIAS;
+    }
 
     // (i) squeeze extent-1 modes
     auto squeeze = [](Mode *m, int n) {
@@ -252,7 +263,8 @@ int make_plan(const Args &a, Plan *p, int *bad_arg)
     p->offA = offA;
     p->offB = offB;
     p->offC = offC;
-    p->empty = false;
+    p->empty = no_sum;
+    if (no_sum) p->K = 0;
     return GETT_OK;
 }
 

@@ -27,6 +27,10 @@ struct TcGemmParams {
     float *C;
     const int64_t *rowC, *colC;
     int64_t c_slice;
+    // MODE_F32 epilogue: SCALE_ACC adds into C, SCALE_AX writes alpha * D,
+    // SCALE_AXPBY writes alpha * D + beta * C (real alpha, beta)
+    int smode;
+    float alpha, beta;
 };
 
 // Row pitch (elements) of a packed operand with K columns: multiple of 8

@@ -97,6 +97,9 @@ def lib():
         getattr(L, p + "gett_async").restype = ctypes.c_int
         getattr(L, p + "gett_ex").argtypes = _ARGS14 + [ctypes.POINTER(Options), ctypes.POINTER(Report), _vp]
         getattr(L, p + "gett_ex").restype = ctypes.c_int
+        getattr(L, p + "gett_scaled").argtypes = _ARGS14 + [_vp, _vp, ctypes.POINTER(Options),
+                                                            ctypes.POINTER(Report), _vp]
+        getattr(L, p + "gett_scaled").restype = ctypes.c_int
     L.gett_plan_describe.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
                                      ctypes.c_int, _ip, _ip, _ip, _i64p, ctypes.POINTER(PlanInfo)]
     L.gett_plan_describe.restype = ctypes.c_int
@@ -152,10 +155,25 @@ def options(algo="default", family="auto", config=-1, split_k=0, moduli=0) -> Op
     return o
 
 
+def _scalar(prefix: str, x):
+    """A host scalar of C's element type for the scaled entry points (kept
+    alive by the caller); None passes NULL."""
+    if x is None:
+        return None
+    if prefix in ("s", "sb"):
+        return ctypes.c_float(float(x))
+    if prefix == "d":
+        return ctypes.c_double(float(x))
+    z = complex(x)
+    t = ctypes.c_float if prefix == "c" else ctypes.c_double
+    return (t * 2)(z.real, z.imag)
+
+
 def xgett(prefix: str, RANKA, EXTA, INCA, A, RANKB, EXTB, INCB, B, CONTS, CONTA, CONTB, PERM, INCC, C,
           *, a_off=0, b_off=0, c_off=0, stream=None, mode="sync", opts: Optional[Options] = None,
-          raise_on_error=True):
-    """Call {prefix}gett / _async / _ex.  Returns (status, report dict or None)."""
+          alpha=1.0, beta=1.0, raise_on_error=True):
+    """Call {prefix}gett / _async / _ex / _scaled (mode "scaled": C <- alpha
+    A.B + beta C).  Returns (status, report dict or None)."""
     L = lib()
     args = [int(RANKA), _i64(EXTA), _i64(INCA), _ptr(A, a_off), int(RANKB), _i64(EXTB), _i64(INCB),
             _ptr(B, b_off), int(CONTS), _i32(CONTA), _i32(CONTB), _i32(PERM), _i64(INCC), _ptr(C, c_off)]
@@ -169,6 +187,13 @@ def xgett(prefix: str, RANKA, EXTA, INCA, A, RANKB, EXTB, INCB, B, CONTS, CONTA,
         o = opts if opts is not None else options()
         st = getattr(L, prefix + "gett_ex")(*args, ctypes.byref(o), ctypes.byref(rep),
                                             ctypes.c_void_p(int(stream or 0)))
+    elif mode == "scaled":
+        rep = Report()
+        o = opts if opts is not None else options()
+        al, be = _scalar(prefix, alpha), _scalar(prefix, beta)
+        st = getattr(L, prefix + "gett_scaled")(*args, ctypes.byref(al) if al is not None else None,
+                                                ctypes.byref(be) if be is not None else None,
+                                                ctypes.byref(o), ctypes.byref(rep), ctypes.c_void_p(int(stream or 0)))
     else:
         raise ValueError(mode)
     if raise_on_error:

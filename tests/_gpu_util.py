@@ -52,14 +52,15 @@ def download(t, dtype) -> np.ndarray:
     return a.view(dtype) if a.dtype != dtype else a
 
 
-def run_gpu(prefix, p: synth.Problem, mode="sync", opts=None, stream=None):
-    """Run the contraction on the GPU; returns (C buffer after, report)."""
+def run_gpu(prefix, p: synth.Problem, mode="sync", opts=None, stream=None, alpha=1.0, beta=1.0):
+    """Run the contraction on the GPU; returns (C buffer after, report).
+    alpha and beta are used by mode "scaled"."""
     dA, dB, dC = upload(p.A), upload(p.B), upload(p.C)
     a = p.args()
     st, rep = gett.xgett(prefix, a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"], a["INCB"],
                          dB, a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], dC,
                          a_off=p.la.off, b_off=p.lb.off, c_off=p.lc.off, mode=mode, opts=opts,
-                         stream=stream)
+                         stream=stream, alpha=alpha, beta=beta)
     if mode == "async":
         import torch
         torch.cuda.synchronize()

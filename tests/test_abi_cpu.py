@@ -185,3 +185,39 @@ def test_planner_preserves_the_contraction(L, family, seed):
         assert sc > 0
     for _, sa, sb in info["k"]:
         assert sa > 0 or (sa == 0 and sb >= 0)
+
+
+def _call_scaled(L, alpha=1.0, beta=1.0, prefix="d", C=0, **kw):
+    a = _args(**kw)
+    st, _ = gett.xgett(prefix, a["RANKA"], a["EXTA"], a["INCA"], 0, a["RANKB"], a["EXTB"], a["INCB"], 0,
+                       a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], C, mode="scaled",
+                       alpha=alpha, beta=beta, raise_on_error=False)
+    return st, gett.last_error_arg()
+
+
+@pytest.mark.parametrize("prefix", ("s", "d", "c", "z", "sb"))
+def test_scaled_null_scalars_reported(L, prefix):
+    """alpha and beta are arguments 15 and 16 of the scaled form."""
+    assert _call_scaled(L, alpha=None, prefix=prefix) == (gett.GETT_ERR_ARG, 15)
+    assert _call_scaled(L, beta=None, prefix=prefix) == (gett.GETT_ERR_ARG, 16)
+
+
+def test_scaled_validates_like_the_plain_form(L):
+    assert _call_scaled(L, alpha=2.0, beta=0.5, PERM=(0, 0)) == (gett.GETT_ERR_ARG, 12)
+    st, _ = _call_scaled(L, alpha=2.0, beta=0.5, INCC=(1, 2))
+    assert st == gett.GETT_ERR_ALIAS
+
+
+def test_scaled_empty_sum(L):
+    """A contracted extent 0 with beta == 1 changes nothing (no pointer read);
+    with another beta C is written, so a NULL C and a non-injective C are
+    reported before any device work."""
+    kw = dict(EXTA=(3, 0), EXTB=(0, 5), INCC=(1, 3))
+    assert _call_scaled(L, alpha=2.0, beta=1.0, **kw)[0] == gett.GETT_OK
+    assert _call_scaled(L, alpha=2.0, beta=0.5, **kw) == (gett.GETT_ERR_ARG, 14)
+    # a C layout that is not injective (never dereferenced: the check comes first)
+    kw_alias = dict(EXTA=(3, 0), EXTB=(0, 5), INCC=(1, 2))
+    assert _call_scaled(L, alpha=2.0, beta=0.5, C=4096, **kw_alias)[0] == gett.GETT_ERR_ALIAS
+    assert _call_scaled(L, alpha=2.0, beta=1.0, C=4096, **kw_alias)[0] == gett.GETT_OK
+    # zero free extent: nothing to write at all
+    assert _call_scaled(L, alpha=2.0, beta=0.5, EXTA=(0, 4))[0] == gett.GETT_OK
