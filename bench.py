@@ -718,6 +718,55 @@ def measure_streaming_forms(dfma_tflops=None):
         out[name] = ent
         del dA, dB, dC
         torch.cuda.empty_cache()
+    out.update(measure_aux_forms(bw, dfma_tflops))
+    return out
+
+
+def measure_aux_forms(bw, dfma_tflops):
+    """Transpose (xGETP) of a 128^4 FP64 tensor with its modes reversed (read
+    2.1 GB, write 2.1 GB; C is not read), and reductions (xGETR) of a
+    16384 x 16384 FP64 matrix over either mode (read 2.1 GB, one FMA per
+    element: FP64-bound on this GPU)."""
+    import torch
+    from paper_2410_06770_gb300 import gett, synth
+    out = {}
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    ext = (128, 128, 128, 128)
+    la = synth.layout_contiguous(ext)
+    perm = (3, 2, 1, 0)
+    lc = synth.layout_contiguous(tuple(ext[perm.index(q)] for q in range(4)))
+    dA = torch.rand(la.size, dtype=torch.float64, device="cuda", generator=g)
+    dC = torch.empty(lc.size, dtype=torch.float64, device="cuda")
+
+    def tcall():
+        gett.getp("d", 4, ext, la.inc, dA, perm, lc.inc, dC, alpha=1.0, beta=0.0)
+    best, _ = time_calls(tcall, 5)
+    nbytes = 16.0 * la.numel
+    out["transpose"] = {"op": "dgetp", "shape": "A(128,128,128,128) -> C with PERM (3,2,1,0), beta = 0",
+                        "ms": best, "gbs": nbytes / (best * 1e-3) / 1e9,
+                        "hbm_frac": nbytes / (best * 1e-3) / 1e9 / bw}
+    del dA, dC
+    torch.cuda.empty_cache()
+    n = 16384
+    dA = torch.rand(n * n, dtype=torch.float64, device="cuda", generator=g)
+    dC = torch.empty(n, dtype=torch.float64, device="cuda")
+    for red, name in (((0,), "reduce_fast_mode"), ((1,), "reduce_slow_mode")):
+        def rcall():
+            gett.getr("d", 2, (n, n), (1, n), dA, 1, red, (0,), (1,), dC, alpha=1.0, beta=0.0)
+        best, _ = time_calls(rcall, 5)
+        nbytes = 8.0 * n * n
+        ent = {"op": "dgetr", "shape": f"A({n},{n}) summed over mode {red[0]}", "ms": best,
+               "gbs": nbytes / (best * 1e-3) / 1e9, "hbm_frac": nbytes / (best * 1e-3) / 1e9 / bw}
+        if dfma_tflops:
+            alu_floor = n * n / (dfma_tflops * 1e12 / 2)
+            hbm_floor = nbytes / (bw * 1e9)
+            ent["bound"] = "hbm" if hbm_floor >= alu_floor else "alu"
+            ent["floor_ms"] = max(alu_floor, hbm_floor) * 1e3
+            ent["floor_frac"] = ent["floor_ms"] / best
+        out[name] = ent
+    del dA, dC
+    torch.cuda.empty_cache()
     return out
 
 

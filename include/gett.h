@@ -261,6 +261,58 @@ int sbgett_scaled(int RANKA, const int64_t *EXTA, const int64_t *INCA, const uin
                   const gett_options *opt, gett_report *rep, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Transpose and reduction.  The thesis lists both among the operations a  */
+/* full BLAS-like tensor interface would need next (Sec. 8, future work);  */
+/* their arguments follow xGETT's conventions (Secs. 5.4-5.7: extents and  */
+/* increments per mode, 0-based mode indices, PERM[p] = output position of */
+/* free mode p, one INCC per output mode, negative increments point at     */
+/* coordinate 0) and the scaled form above (alpha, beta host pointers;     */
+/* beta == 0 does not read C; alpha == 0 does not read A).  Both return    */
+/* after completion on `stream` and report errors like xgett_ex.           */
+/*                                                                         */
+/* xGETP: C[o_0 .. o_{r-1} placed by PERM] <- alpha * A[o] + beta * C.     */
+/*   Positions: 1 RANKA, 2 EXTA, 3 INCA, 4 A, 5 PERM (RANKA entries),      */
+/*   6 INCC, 7 C, 8 alpha, 9 beta.  It equals xGETT with a rank-0 B of     */
+/*   value 1 (CONTS = 0).                                                  */
+/* xGETR: C[free modes of A, ascending, placed by PERM] <- alpha * sum     */
+/*   over the NRED modes RED[0..NRED-1] of A + beta * C.  Positions: 1-4   */
+/*   as above, 5 NRED (0..RANKA), 6 RED (distinct modes of A), 7 PERM      */
+/*   (RANKA - NRED entries), 8 INCC, 9 C, 10 alpha, 11 beta.  It equals    */
+/*   xGETT with B a tensor of ones over the reduced modes; the same        */
+/*   selector and kernels run it.                                          */
+/* ---------------------------------------------------------------------- */
+int sgetp(int RANKA, const int64_t *EXTA, const int64_t *INCA, const float *A,
+          const int *PERM, const int64_t *INCC, float *C, const float *alpha,
+          const float *beta, void *stream);
+int dgetp(int RANKA, const int64_t *EXTA, const int64_t *INCA, const double *A,
+          const int *PERM, const int64_t *INCC, double *C, const double *alpha,
+          const double *beta, void *stream);
+int cgetp(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_float *A,
+          const int *PERM, const int64_t *INCC, gett_complex_float *C, const gett_complex_float *alpha,
+          const gett_complex_float *beta, void *stream);
+int zgetp(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_double *A,
+          const int *PERM, const int64_t *INCC, gett_complex_double *C, const gett_complex_double *alpha,
+          const gett_complex_double *beta, void *stream);
+int sbgetp(int RANKA, const int64_t *EXTA, const int64_t *INCA, const uint16_t *A,
+           const int *PERM, const int64_t *INCC, float *C, const float *alpha,
+           const float *beta, void *stream);
+int sgetr(int RANKA, const int64_t *EXTA, const int64_t *INCA, const float *A,
+          int NRED, const int *RED, const int *PERM, const int64_t *INCC, float *C,
+          const float *alpha, const float *beta, void *stream);
+int dgetr(int RANKA, const int64_t *EXTA, const int64_t *INCA, const double *A,
+          int NRED, const int *RED, const int *PERM, const int64_t *INCC, double *C,
+          const double *alpha, const double *beta, void *stream);
+int cgetr(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_float *A,
+          int NRED, const int *RED, const int *PERM, const int64_t *INCC, gett_complex_float *C,
+          const gett_complex_float *alpha, const gett_complex_float *beta, void *stream);
+int zgetr(int RANKA, const int64_t *EXTA, const int64_t *INCA, const gett_complex_double *A,
+          int NRED, const int *RED, const int *PERM, const int64_t *INCC, gett_complex_double *C,
+          const gett_complex_double *alpha, const gett_complex_double *beta, void *stream);
+int sbgetr(int RANKA, const int64_t *EXTA, const int64_t *INCA, const uint16_t *A,
+           int NRED, const int *RED, const int *PERM, const int64_t *INCC, float *C,
+           const float *alpha, const float *beta, void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Allocation-free double-precision form.  The thesis has no counterpart;  */
 /* this entry point exists for callers that must not allocate device       */
 /* memory while they run (a process that budgets all device memory up     */

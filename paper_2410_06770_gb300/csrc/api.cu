@@ -248,10 +248,10 @@ void re_im(const gett_complex_double *x, double *re, double *im) { *re = x->re; 
 
 // alpha == 1 and beta == 1 is Alg. 1's accumulation; beta == 0 never reads C.
 template <class TC>
-int scale_of(const TC *alpha, const TC *beta, Scale *sc, bool *alpha_zero)
+int scale_of(const TC *alpha, const TC *beta, Scale *sc, bool *alpha_zero, int pos_alpha = 15)
 {
-    if (!alpha) { set_last_error_arg(15); return GETT_ERR_ARG; }
-    if (!beta) { set_last_error_arg(16); return GETT_ERR_ARG; }
+    if (!alpha) { set_last_error_arg(pos_alpha); return GETT_ERR_ARG; }
+    if (!beta) { set_last_error_arg(pos_alpha + 1); return GETT_ERR_ARG; }
     re_im(alpha, &sc->ar, &sc->ai);
     re_im(beta, &sc->br, &sc->bi);
     *alpha_zero = sc->ar == 0.0 && sc->ai == 0.0;
@@ -260,8 +260,135 @@ int scale_of(const TC *alpha, const TC *beta, Scale *sc, bool *alpha_zero)
     else sc->mode = SCALE_AXPBY;
     return GETT_OK;
 }
+// Argument positions: an xGETT position of the equivalent contraction ->
+// the position in xGETP (1 RANKA, 2 EXTA, 3 INCA, 4 A, 5 PERM, 6 INCC, 7 C)
+// or xGETR (1-4, 5 NRED, 6 RED, 7 PERM, 8 INCC, 9 C).
+int getp_pos(int pos)
+{
+    switch (pos) {
+    case 12: return 5;
+    case 13: return 6;
+    case 14: return 7;
+    default: return pos <= 4 ? pos : 0;
+    }
+}
+int getr_pos(int pos)
+{
+    switch (pos) {
+    case 9: return 5;
+    case 10: case 11: return 6;
+    case 12: return 7;
+    case 13: return 8;
+    case 14: return 9;
+    default: return pos <= 4 ? pos : 0;
+    }
+}
+
 }  // namespace
+
+// Transpose (Sec. 8 future work): the contraction with a rank-0 B of value 1,
+// run by the transpose kernel.
+int run_transpose(DType t, int RANKA, const int64_t *EXTA, const int64_t *INCA, const void *A, const int *PERM,
+                  const int64_t *INCC, void *C, const Scale &sc, bool alpha_zero, cudaStream_t s)
+{
+    Args a{RANKA, EXTA, INCA, 0, nullptr, nullptr, 0, nullptr, nullptr, PERM, INCC};
+    Plan p;
+    int bad = 0;
+    int rc = make_plan(a, &p, &bad);
+    set_last_error_arg(getp_pos(bad));
+    if (rc != GETT_OK) return rc;
+    p.sc = sc;
+    if (p.empty) return GETT_OK;
+    if (alpha_zero) return run_scale_only(t, p, C, s, true);
+    if (!A || reinterpret_cast<uintptr_t>(A) % in_align(t)) { set_last_error_arg(4); return GETT_ERR_ARG; }
+    if (!C || reinterpret_cast<uintptr_t>(C) % out_align(t)) { set_last_error_arg(7); return GETT_ERR_ARG; }
+    if (ranges_overlap(C, p.c_lo, p.c_hi, out_elem_size(t), A, p.a_lo, p.a_hi, dtype_size(t))) return GETT_ERR_ALIAS;
+    DevState *st = nullptr;
+    rc = dev_state(&st);
+    if (rc != GETT_OK) return rc;
+    cudaError_t e = launch_transpose(p, t, A, C, st->sms, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    return GETT_OK;
+}
+
+// Reduction (Sec. 8 future work): the contraction of A with a B of ones over
+// the reduced modes (extents EXTA[RED[t]], every increment 0, so B is the one
+// element unit_operand gives); the selector and kernels are the contraction's.
+int run_reduce(DType t, int RANKA, const int64_t *EXTA, const int64_t *INCA, const void *A, int NRED,
+               const int *RED, const int *PERM, const int64_t *INCC, void *C, const Scale &sc, bool alpha_zero,
+               cudaStream_t s)
+{
+    if (RANKA < 0 || RANKA > GETT_MAX_RANK) { set_last_error_arg(1); return GETT_ERR_ARG; }
+    if (RANKA > 0 && !EXTA) { set_last_error_arg(2); return GETT_ERR_ARG; }
+    if (NRED < 0 || NRED > RANKA) { set_last_error_arg(5); return GETT_ERR_ARG; }
+    if (NRED > 0 && !RED) { set_last_error_arg(6); return GETT_ERR_ARG; }
+    if (NRED == 0) return run_transpose(t, RANKA, EXTA, INCA, A, PERM, INCC, C, sc, alpha_zero, s);
+    int64_t extb[GETT_MAX_RANK], incb[GETT_MAX_RANK];
+    int contb[GETT_MAX_RANK];
+    for (int i = 0; i < NRED; ++i) {
+        if (RED[i] < 0 || RED[i] >= RANKA) { set_last_error_arg(6); return GETT_ERR_ARG; }
+        extb[i] = EXTA[RED[i]];
+        incb[i] = 0;
+        contb[i] = i;
+    }
+    Args a{RANKA, EXTA, INCA, NRED, extb, incb, NRED, RED, contb, PERM, INCC};
+    {
+        // report argument errors before any device call
+        Plan p;
+        int bad = 0;
+        const int rc = make_plan(a, &p, &bad);
+        if (rc != GETT_OK) {
+            set_last_error_arg(getr_pos(bad));
+            return rc;
+        }
+        if (p.empty && !p.zero_sum) return GETT_OK;
+    }
+    const void *B = nullptr;
+    cudaError_t e = unit_operand(t, &B);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GETT_ERR_CUDA;
+    }
+    int rc = run(t, a, A, B, C, nullptr, nullptr, s, true, &sc, alpha_zero);
+    if (rc == GETT_ERR_ARG) set_last_error_arg(getr_pos(gett_last_error_arg()));
+    return rc;
+}
+
 }  // namespace gett
+
+#define DEFINE_AUX(prefix, T, TC, DT)                                                                      \
+    extern "C" int prefix##getp(int RANKA, const int64_t *EXTA, const int64_t *INCA, const T *A,            \
+                                const int *PERM, const int64_t *INCC, TC *C, const TC *alpha, const TC *beta, \
+                                void *stream)                                                               \
+    {                                                                                                       \
+        gett::Scale sc{};                                                                                   \
+        bool az = false;                                                                                    \
+        int rc = gett::scale_of(alpha, beta, &sc, &az, 8);                                                  \
+        if (rc != GETT_OK) return rc;                                                                       \
+        return gett::run_transpose(gett::DT, RANKA, EXTA, INCA, A, PERM, INCC, C, sc, az,                   \
+                                   (cudaStream_t)stream);                                                   \
+    }                                                                                                       \
+    extern "C" int prefix##getr(int RANKA, const int64_t *EXTA, const int64_t *INCA, const T *A, int NRED,  \
+                                const int *RED, const int *PERM, const int64_t *INCC, TC *C, const TC *alpha, \
+                                const TC *beta, void *stream)                                               \
+    {                                                                                                       \
+        gett::Scale sc{};                                                                                   \
+        bool az = false;                                                                                    \
+        int rc = gett::scale_of(alpha, beta, &sc, &az, 10);                                                 \
+        if (rc != GETT_OK) return rc;                                                                       \
+        return gett::run_reduce(gett::DT, RANKA, EXTA, INCA, A, NRED, RED, PERM, INCC, C, sc, az,           \
+                                (cudaStream_t)stream);                                                      \
+    }
+
+DEFINE_AUX(s, float, float, DT_F32)
+DEFINE_AUX(d, double, double, DT_F64)
+DEFINE_AUX(c, gett_complex_float, gett_complex_float, DT_C32)
+DEFINE_AUX(z, gett_complex_double, gett_complex_double, DT_C64)
+DEFINE_AUX(sb, uint16_t, float, DT_BF16)
 
 #define DEFINE_SCALED(prefix, T, TC, DT)                                                             \
     extern "C" int prefix##gett_scaled(GETT_ARGS_DECL(T), TC *C, const TC *alpha, const TC *beta,      \

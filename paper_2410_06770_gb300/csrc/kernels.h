@@ -40,6 +40,15 @@ cudaError_t launch_reduce(const Plan &p, DType t, const void *A, const void *B, 
 // an empty sum); uses p.sc's beta.
 cudaError_t launch_scale_c(const Plan &p, DType t, void *C, int num_sms, cudaStream_t s);
 
+// ---- transpose and the reduction's unit operand (k_aux.cu) ----
+// Transpose: the planned contraction with no contracted and no B-free modes
+// (C[rowC[m]] <- A[rowA[m]] under p.sc).  Tiled through shared memory when A's
+// and C's fastest modes differ.
+bool transpose_tiled(const Plan &p);
+cudaError_t launch_transpose(const Plan &p, DType t, const void *A, void *C, int num_sms, cudaStream_t s);
+// Device address of one element of value 1 of type t (the B of a reduction).
+cudaError_t unit_operand(DType t, const void **out);
+
 // ---- tensor-core forms ----
 // s / bf16 inputs: packed bf16 pieces + one tcgen05 GEMM (k_tcpack.cu)
 int tc_split_blocks(int algo);

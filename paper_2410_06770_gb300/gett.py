@@ -100,6 +100,11 @@ def lib():
         getattr(L, p + "gett_scaled").argtypes = _ARGS14 + [_vp, _vp, ctypes.POINTER(Options),
                                                             ctypes.POINTER(Report), _vp]
         getattr(L, p + "gett_scaled").restype = ctypes.c_int
+        getattr(L, p + "getp").argtypes = [ctypes.c_int, _i64p, _i64p, _vp, _ip, _i64p, _vp, _vp, _vp, _vp]
+        getattr(L, p + "getp").restype = ctypes.c_int
+        getattr(L, p + "getr").argtypes = [ctypes.c_int, _i64p, _i64p, _vp, ctypes.c_int, _ip, _ip, _i64p, _vp,
+                                           _vp, _vp, _vp]
+        getattr(L, p + "getr").restype = ctypes.c_int
     L.gett_plan_describe.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
                                      ctypes.c_int, _ip, _ip, _ip, _i64p, ctypes.POINTER(PlanInfo)]
     L.gett_plan_describe.restype = ctypes.c_int
@@ -217,3 +222,30 @@ def last_error_arg() -> int:
 
 def device_status() -> int:
     return lib().gett_device_status()
+
+
+def getp(prefix: str, RANKA, EXTA, INCA, A, PERM, INCC, C, *, alpha=1.0, beta=0.0, a_off=0, c_off=0,
+         stream=None, raise_on_error=True) -> int:
+    """{prefix}getp: C[o placed by PERM] <- alpha A[o] + beta C (transpose)."""
+    L = lib()
+    al, be = _scalar(prefix, alpha), _scalar(prefix, beta)
+    st = getattr(L, prefix + "getp")(int(RANKA), _i64(EXTA), _i64(INCA), _ptr(A, a_off), _i32(PERM), _i64(INCC),
+                                     _ptr(C, c_off), ctypes.byref(al) if al is not None else None,
+                                     ctypes.byref(be) if be is not None else None, ctypes.c_void_p(int(stream or 0)))
+    if raise_on_error:
+        check(st)
+    return st
+
+
+def getr(prefix: str, RANKA, EXTA, INCA, A, NRED, RED, PERM, INCC, C, *, alpha=1.0, beta=0.0, a_off=0, c_off=0,
+         stream=None, raise_on_error=True) -> int:
+    """{prefix}getr: C[free modes placed by PERM] <- alpha sum_{RED} A + beta C (reduction)."""
+    L = lib()
+    al, be = _scalar(prefix, alpha), _scalar(prefix, beta)
+    st = getattr(L, prefix + "getr")(int(RANKA), _i64(EXTA), _i64(INCA), _ptr(A, a_off), int(NRED), _i32(RED),
+                                     _i32(PERM), _i64(INCC), _ptr(C, c_off),
+                                     ctypes.byref(al) if al is not None else None,
+                                     ctypes.byref(be) if be is not None else None, ctypes.c_void_p(int(stream or 0)))
+    if raise_on_error:
+        check(st)
+    return st

@@ -221,3 +221,51 @@ def test_scaled_empty_sum(L):
     assert _call_scaled(L, alpha=2.0, beta=1.0, C=4096, **kw_alias)[0] == gett.GETT_OK
     # zero free extent: nothing to write at all
     assert _call_scaled(L, alpha=2.0, beta=0.5, EXTA=(0, 4))[0] == gett.GETT_OK
+
+
+def _getp(**kw):
+    a = dict(RANKA=3, EXTA=(3, 4, 5), INCA=(1, 3, 12), A=0, PERM=(2, 0, 1), INCC=(1, 4, 20), C=0,
+             alpha=1.0, beta=0.0)
+    a.update(kw)
+    st = gett.getp("d", a["RANKA"], a["EXTA"], a["INCA"], a["A"], a["PERM"], a["INCC"], a["C"],
+                   alpha=a["alpha"], beta=a["beta"], raise_on_error=False)
+    return st, gett.last_error_arg()
+
+
+def _getr(**kw):
+    a = dict(RANKA=3, EXTA=(3, 4, 5), INCA=(1, 3, 12), A=0, NRED=1, RED=(1,), PERM=(1, 0), INCC=(1, 5), C=0,
+             alpha=1.0, beta=0.0)
+    a.update(kw)
+    st = gett.getr("d", a["RANKA"], a["EXTA"], a["INCA"], a["A"], a["NRED"], a["RED"], a["PERM"], a["INCC"],
+                   a["C"], alpha=a["alpha"], beta=a["beta"], raise_on_error=False)
+    return st, gett.last_error_arg()
+
+
+@pytest.mark.parametrize("kw,pos", [
+    (dict(RANKA=-1), 1), (dict(EXTA=None), 2), (dict(EXTA=(3, -4, 5)), 2), (dict(INCA=None), 3),
+    (dict(PERM=(0, 0, 1)), 5), (dict(PERM=(0, 1, 3)), 5), (dict(PERM=None), 5), (dict(INCC=None), 6),
+    (dict(alpha=None), 8), (dict(beta=None), 9), (dict(), 4), (dict(A=4096), 7),
+])
+def test_transpose_argument_positions(L, kw, pos):
+    """xGETP positions: 1 RANKA, 2 EXTA, 3 INCA, 4 A, 5 PERM, 6 INCC, 7 C, 8 alpha, 9 beta (A and C
+    are only checked for NULL / alignment here, never dereferenced)."""
+    assert _getp(**kw) == (gett.GETT_ERR_ARG, pos)
+
+
+def test_transpose_non_injective_c_is_alias(L):
+    assert _getp(INCC=(1, 2, 3))[0] == gett.GETT_ERR_ALIAS
+
+
+@pytest.mark.parametrize("kw,pos", [
+    (dict(NRED=4), 5), (dict(NRED=-1), 5), (dict(RED=None), 6), (dict(RED=(3,)), 6), (dict(RED=(-1,)), 6),
+    (dict(NRED=2, RED=(1, 1), PERM=(0,), INCC=(1,)), 6), (dict(PERM=(0, 0)), 7), (dict(PERM=(0,)), 7),
+    (dict(INCC=None), 8), (dict(alpha=None), 10), (dict(beta=None), 11),
+])
+def test_reduction_argument_positions(L, kw, pos):
+    """xGETR positions: 5 NRED, 6 RED, 7 PERM, 8 INCC, 10 alpha, 11 beta."""
+    assert _getr(**kw) == (gett.GETT_ERR_ARG, pos)
+
+
+def test_aux_empty_outputs_are_noops(L):
+    assert _getp(EXTA=(3, 0, 5))[0] == gett.GETT_OK
+    assert _getr(EXTA=(0, 4, 5))[0] == gett.GETT_OK
