@@ -8,7 +8,7 @@
 // run by its own kernel: when A's smallest-increment mode is not C's, a
 // 32 x 32 tile goes through shared memory so that the reads run along A's
 // fastest mode and the writes along C's; otherwise both run along the same
-// mode (a streaming copy).  HBM-bound: 8 bytes read + 8 written per double
+// mode in 128 x 32 blocks over it and the next mode (a streaming copy).  HBM-bound: 8 bytes read + 8 written per double
 // (plus 8 read when C is accumulated).
 //
 // Reduction: the contraction with a B of ones over the reduced modes, all of
@@ -36,6 +36,8 @@ struct TransParams {
     int64_t a1, c1;   // and of the second
     ModeList rest;    // all other modes (s0: A, s1: C)
     int64_t t0n, t1n, items;
+    int64_t tg, t0g;  // tile kernel: tiles of mode 0 per item, item groups along mode 0
+    int wide;         // rows kernel: 1024 x 1 blocks instead of 128 x 32
     Scale sc;
 };
 
@@ -48,8 +50,10 @@ __device__ __forceinline__ void trans_store(typename R::Out *c, typename R::Acc 
 
 // Tiles of TT x TT over (mode 0, mode 1) times the other modes; a CTA of
 // 32 x 8 threads reads the tile with lanes along mode 1 (A's fastest) and
-// writes it with lanes along mode 0 (C's fastest).
-template <class T>
+// writes it with lanes along mode 0 (C's fastest).  Addresses advance by
+// increments (no per-element 64-bit products); UNIT: A's mode-1 and C's
+// mode-0 increments are 1.
+template <class T, bool UNIT>
 __global__ void __launch_bounds__(256) transpose_tile_kernel(TransParams p)
 {
     using R = Tr<T>;
@@ -57,69 +61,114 @@ __global__ void __launch_bounds__(256) transpose_tile_kernel(TransParams p)
     using Out = typename R::Out;
     __shared__ Acc tile[TT][TT + 1];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t a1 = UNIT ? 1 : p.a1, c0 = UNIT ? 1 : p.c0;
+    const bool plain = p.sc.mode == SCALE_AX && p.sc.ar == 1.0 && p.sc.ai == 0.0;
+    // an item is a run of up to tg tiles along mode 0 at one (mode-1 tile,
+    // other modes) position: its index arithmetic is shared by the run
     for (int64_t item = blockIdx.x; item < p.items; item += gridDim.x) {
-        const int64_t t0 = item % p.t0n;
-        const int64_t r1 = item / p.t0n;
+        const int64_t g0 = item % p.t0g;
+        const int64_t r1 = item / p.t0g;
         const int64_t t1 = r1 % p.t1n;
         const int64_t ir = r1 / p.t1n;
         int64_t oa, oc;
         decode2(p.rest, ir, oa, oc);
-        const T *A = static_cast<const T *>(p.A) + oa;
-        Out *C = static_cast<Out *>(p.C) + oc;
-        const int64_t i0 = t0 * TT, i1 = t1 * TT;
-        __syncthreads();  // the previous tile has been written out
+        const int64_t i1 = t1 * TT;
+        const int n1 = (int)min((int64_t)TT, p.e1 - i1);
+        const T *abase = static_cast<const T *>(p.A) + oa + (i1 + tx) * a1;
+        Out *cbase = static_cast<Out *>(p.C) + oc + (i1 + ty) * p.c1;
+        const int64_t tend = min(p.t0n, (g0 + 1) * p.tg);
+        for (int64_t t0 = g0 * p.tg; t0 < tend; ++t0) {
+            const int64_t i0 = t0 * TT;
+            // rows this thread touches: mode-0 index i0 + ty + 8 j when reading,
+            // mode-1 index i1 + ty + 8 j when writing
+            const int n0 = (int)min((int64_t)TT, p.e0 - i0);
+            __syncthreads();  // the previous tile has been written out
+            if (tx < n1) {
+                const T *src = abase + (i0 + ty) * p.a0;
 #pragma unroll
-        for (int r = ty; r < TT; r += 8) {
-            const int64_t x0 = i0 + r, x1 = i1 + tx;
-            if (x0 < p.e0 && x1 < p.e1) tile[r][tx] = R::load(A + x0 * p.a0 + x1 * p.a1);
-        }
-        __syncthreads();
+                for (int r = ty; r < TT; r += 8, src += 8 * p.a0)
+                    if (r < n0) tile[r][tx] = R::load(src);
+            }
+            __syncthreads();
+            if (tx < n0) {
+                Out *dst = cbase + (i0 + tx) * c0;
 #pragma unroll
-        for (int r = ty; r < TT; r += 8) {
-            const int64_t x0 = i0 + tx, x1 = i1 + r;
-            if (x0 < p.e0 && x1 < p.e1) trans_store<R>(C + x0 * p.c0 + x1 * p.c1, tile[tx][r], p.sc);
+                for (int r = ty; r < TT; r += 8, dst += 8 * p.c1) {
+                    if (r >= n1) continue;
+                    if (plain) R::store_c(dst, tile[tx][r]);
+                    else trans_store<R>(dst, tile[tx][r], p.sc);
+                }
+            }
         }
     }
 }
 
-// A's and C's fastest modes coincide: stream along mode 0 in chunks of
-// 256 x 4 elements, one chunk and one index of the other modes per item.
-template <class T>
-__global__ void __launch_bounds__(256) transpose_stream_kernel(TransParams p)
+// A's and C's fastest modes coincide (mode 0): both sides run along mode 0.
+// A work item is 128 elements of mode 0 (a warp, 4 per lane) times 32
+// indices of mode 1 (8 warps, 4 passes) times one index of the other modes,
+// so short fastest modes still keep every thread busy; all 16 loads of a
+// thread are issued before its stores.
+// WIDE (mode 1 shorter than 32, mode 0 long): 1024 elements of mode 0 (8
+// warps side by side) and one index of mode 1 per item instead.
+template <class T, bool WIDE>
+__global__ void __launch_bounds__(256) transpose_rows_kernel(TransParams p)
 {
     using R = Tr<T>;
+    using Acc = typename R::Acc;
     using Out = typename R::Out;
-    constexpr int U = 4, CH = 256 * U;
+    constexpr int UX = 4, UY = WIDE ? 1 : 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool plain = p.sc.mode == SCALE_AX && p.sc.ar == 1.0 && p.sc.ai == 0.0;
+    // an item is a run of up to tg blocks along mode 0 (shared index arithmetic)
     for (int64_t item = blockIdx.x; item < p.items; item += gridDim.x) {
-        const int64_t t0 = item % p.t0n;
-        const int64_t ir = item / p.t0n;
+        const int64_t g0 = item % p.t0g;
+        const int64_t r1 = item / p.t0g;
+        const int64_t t1 = r1 % p.t1n;
+        const int64_t ir = r1 / p.t1n;
         int64_t oa, oc;
         decode2(p.rest, ir, oa, oc);
-        const T *A = static_cast<const T *>(p.A) + oa;
-        Out *C = static_cast<Out *>(p.C) + oc;
-        typename R::Acc v[U];
+        const int64_t y0 = WIDE ? t1 : t1 * 8 * UY + warp;
+        const int64_t tend = min(p.t0n, (g0 + 1) * p.tg);
+        for (int64_t t0 = g0 * p.tg; t0 < tend; ++t0) {
+            const int64_t x0 = WIDE ? t0 * 8 * 32 * UX + warp * 32 * UX + lane : t0 * 32 * UX + lane;
+            const T *src = static_cast<const T *>(p.A) + oa + x0 * p.a0 + y0 * p.a1;
+            Out *dst = static_cast<Out *>(p.C) + oc + x0 * p.c0 + y0 * p.c1;
+            Acc v[UY][UX];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t x = t0 * CH + u * 256 + threadIdx.x;
-            if (x < p.e0) v[u] = R::load(A + x * p.a0);
-        }
+            for (int j = 0; j < UY; ++j)
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t x = t0 * CH + u * 256 + threadIdx.x;
-            if (x < p.e0) trans_store<R>(C + x * p.c0, v[u], p.sc);
+                for (int u = 0; u < UX; ++u)
+                    if (x0 + 32 * u < p.e0 && y0 + 8 * j < p.e1) v[j][u] = R::load(src + 32 * u * p.a0 + 8 * j * p.a1);
+#pragma unroll
+            for (int j = 0; j < UY; ++j)
+#pragma unroll
+                for (int u = 0; u < UX; ++u) {
+                    if (!(x0 + 32 * u < p.e0 && y0 + 8 * j < p.e1)) continue;
+                    Out *c = dst + 32 * u * p.c0 + 8 * j * p.c1;
+                    if (plain) R::store_c(c, v[j][u]);
+                    else trans_store<R>(c, v[j][u], p.sc);
+                }
         }
     }
 }
 
-// Drop modes i and j (i != j, either may be -1) from a list.
+// Drop modes i and j (i != j, either may be -1) from a list; the rest is
+// ordered by A's increment, so consecutive work items read nearby data.
 ModeList without(const ModeList &L, int i, int j)
 {
     ModeList r{};
     for (int q = 0; q < L.n; ++q) {
         if (q == i || q == j) continue;
-        r.ext[r.n] = L.ext[q];
-        r.s0[r.n] = L.s0[q];
-        r.s1[r.n] = L.s1[q];
+        int at = r.n;
+        while (at > 0 && std::llabs(r.s0[at - 1]) > std::llabs(L.s0[q])) {
+            r.ext[at] = r.ext[at - 1];
+            r.s0[at] = r.s0[at - 1];
+            r.s1[at] = r.s1[at - 1];
+            --at;
+        }
+        r.ext[at] = L.ext[q];
+        r.s0[at] = L.s0[q];
+        r.s1[at] = L.s1[q];
         ++r.n;
     }
     return r;
@@ -139,8 +188,10 @@ template <class T>
 cudaError_t transpose_typed(const TransParams &p, bool tiled, int num_sms, cudaStream_t s)
 {
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(p.items, (int64_t)num_sms * 8));
-    if (tiled) transpose_tile_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(p);
-    else transpose_stream_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(p);
+    if (tiled && p.a1 == 1 && p.c0 == 1) transpose_tile_kernel<T, true><<<(unsigned)blocks, 256, 0, s>>>(p);
+    else if (tiled) transpose_tile_kernel<T, false><<<(unsigned)blocks, 256, 0, s>>>(p);
+    else if (p.wide) transpose_rows_kernel<T, true><<<(unsigned)blocks, 256, 0, s>>>(p);
+    else transpose_rows_kernel<T, false><<<(unsigned)blocks, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -196,12 +247,31 @@ cudaError_t launch_transpose(const Plan &pl, DType t, const void *A, void *C, in
         p.rest = without(pl.m, 0, ia);
         p.t0n = (p.e0 + TT - 1) / TT;
         p.t1n = (p.e1 + TT - 1) / TT;
-        p.items = p.t0n * p.t1n * count(p.rest);
+        p.tg = std::min<int64_t>(p.t0n, 8);
+        p.t0g = (p.t0n + p.tg - 1) / p.tg;
+        p.items = p.t0g * p.t1n * count(p.rest);
     } else {
-        if (pl.m.n > 0) p.rest = without(pl.m, 0, -1);
-        p.t0n = (p.e0 + 1023) / 1024;
-        p.t1n = 1;
-        p.items = p.t0n * count(p.rest);
+        // mode 1: the next mode by C increment (mode 1 of the plan), if any
+        if (pl.m.n > 1) {
+            p.e1 = pl.m.ext[1];
+            p.a1 = pl.m.s0[1];
+            p.c1 = pl.m.s1[1];
+            p.rest = without(pl.m, 0, 1);
+        } else {
+            p.e1 = 1;
+            p.rest.n = 0;
+        }
+        p.wide = p.e1 < 32 && p.e0 >= 1024;
+        if (p.wide) {  // 1024 x 1 blocks
+            p.t0n = (p.e0 + 1023) / 1024;
+            p.t1n = p.e1;
+        } else {  // 128 x 32 blocks
+            p.t0n = (p.e0 + 127) / 128;
+            p.t1n = (p.e1 + 31) / 32;
+        }
+        p.tg = std::min<int64_t>(p.t0n, 8);
+        p.t0g = (p.t0n + p.tg - 1) / p.tg;
+        p.items = p.t0g * p.t1n * count(p.rest);
     }
     switch (t) {
     case DT_F32: return transpose_typed<float>(p, tiled, num_sms, s);

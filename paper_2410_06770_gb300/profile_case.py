@@ -5,7 +5,8 @@
 WORKLOAD: cc, cc_perm_transA (extents a..d = SCALE, i,j = SCALE/4), stream
 (A(SCALE, SCALE, 64) x B(64, 8)), small, gemv (A(SCALE, SCALE) x B(SCALE, 2),
 the second mode of A contracted), inner (A and B of extents SCALE^4, every
-mode contracted), batched (SCALE contractions of the batched workload, one
+mode contracted), transpose (xGETP of A(SCALE^4) with its modes reversed),
+batched (SCALE contractions of the batched workload, one
 persistent launch per call).  gemv and inner draw uniform values on the device.  Inputs are generated on the host,
 copied once, then the call is made N times (default 2) and synchronised.
 """
@@ -37,6 +38,21 @@ def main(argv=None):
             b.launch()
         torch.cuda.synchronize()
         print(b.info())
+        return 0
+    if args.workload == "transpose":
+        # A(s,s,s,s) -> C with the modes reversed (xGETP), FP64, C not read
+        s4 = (args.scale,) * 4
+        la = synth.layout_contiguous(s4)
+        perm = (3, 2, 1, 0)
+        lc = synth.layout_contiguous(s4)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(9)
+        dA = torch.rand(la.size, dtype=torch.float64, device="cuda", generator=g)
+        dC = torch.empty(lc.size, dtype=torch.float64, device="cuda")
+        for _ in range(args.calls):
+            gett.getp("d", 4, s4, la.inc, dA, perm, lc.inc, dC, alpha=1.0, beta=0.0)
+        torch.cuda.synchronize()
+        print("transpose", s4, perm)
         return 0
     if args.workload in ("gemv", "inner"):
         s = args.scale

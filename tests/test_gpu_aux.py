@@ -49,6 +49,9 @@ TRANSPOSES = [
     ((9, 300), (1, 0), ("rowmajor", "contig")),
     ((4, 5, 6, 7, 2), (4, 0, 3, 1, 2), ("padded", "padded")),
     ((1,), (0,), ("contig", "contig")),
+    ((3000, 5, 7), (0, 2, 1), ("contig", "padded")),    # long fastest mode, short next mode: wide blocks
+    ((100, 3, 2), (0, 2, 1), ("padded", "negative")),
+    ((2000, 40), (0, 1), ("contig", "contig")),         # fuses to one mode
     ((), (), ("contig", "contig")),
 ]
 
