@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -49,13 +50,31 @@ struct OzConsts {
     float ipre[OZ_MAX_L];                   // (p_0 ... p_{i-1})^{-1} mod p_i
     int half[OZ_MAX_L];                     // mixed-radix digits of (P-1)/2
     float halff[OZ_MAX_L];
+    // the residue kernel's constants as f32x2 pairs (the same value twice)
+    uint64_t k13[OZ_MAX_L], k26[OZ_MAX_L], k39[OZ_MAX_L], kinv[OZ_MAX_L], knegp[OZ_MAX_L];
 };
 
-__device__ __forceinline__ uint16_t f2bf_bits(float x)
+// Packed pairs of fp32 (Blackwell f32x2): each lane is rounded exactly as
+// the scalar .rn instruction, so results equal the per-element code.
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
 {
-    __nv_bfloat16 b = __float2bfloat16_rn(x);
-    return *reinterpret_cast<uint16_t *>(&b);
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__host__ __device__ constexpr uint64_t pair_bits(uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; }
 
 // Nearest integer of x * r for |x * r| < 2^22, with two full-rate fp32 ops:
 // adding 1.5 * 2^23 leaves no fraction bits, so the fused multiply-add rounds
@@ -103,18 +122,38 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool val
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Gathered tiles of the scan and residue kernels: OZ_STAGES buffers of TR x
+// (TKP + 1) doubles (the scan) or RTR x (RTKP + 1) (the residues) in dynamic
+// shared memory, OZ_STAGES - 1 tiles in flight.
+constexpr int RTR = 32, RTKP = 64;
+constexpr int OZ_STAGES = 3;
+constexpr size_t OZ_SMEM = (size_t)OZ_STAGES *
+                           (TR * (TKP + 1) > RTR * (RTKP + 1) ? TR * (TKP + 1) : RTR * (RTKP + 1)) * sizeof(uint64_t);
+
+// Element offset of (row r, k) in the operand: through the offset tables, or
+// AFF (one mode per class after fusion) r * sr + k * sk.
+template <bool AFF>
+__device__ __forceinline__ int64_t oz_off(const int64_t *rowT, const int64_t *kT, int64_t sr, int64_t sk, int64_t r,
+                                          int64_t k)
+{
+    return AFF ? r * sr + k * sk : rowT[r] + kT[k];
+}
 
 // Row maxima of |x| (as bit patterns) over K, for the scaling.  Tiles of 32
-// rows x 64 k are gathered with cp.async into a double buffer; each warp
+// rows x 64 k are gathered with cp.async through OZ_STAGES buffers; each warp
 // reduces its values in registers / with shuffles before one shared atomic.
-template <int ROW_FAST>
+template <int ROW_FAST, bool AFF>
 __global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict__ src,
                                                        const int64_t *__restrict__ rowT,
-                                                       const int64_t *__restrict__ kT, int64_t rows, int64_t K,
+                                                       const int64_t *__restrict__ kT, int64_t sr, int64_t sk,
+                                                       int64_t rows, int64_t K,
                                                        unsigned long long *__restrict__ maxbits)
 {
-    __shared__ uint64_t tile[2][TR][TKP + 1];
+    extern __shared__ __align__(16) uint64_t oz_dyn[];
+    auto tile = [&](int b, int r, int k) -> uint64_t & { return oz_dyn[(b * TR + r) * (TKP + 1) + k]; };
     __shared__ unsigned long long smax[TR];
     const int64_t tiles_k = (K + TKP - 1) / TKP;
     const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
@@ -127,20 +166,25 @@ __global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict
             if (ROW_FAST) { r = e % TR; k = e / TR; }
             else { k = e % TKP; r = e / TKP; }
             const bool valid = r0 + r < rows && k0 + k < K;
-            const double *g = valid ? src + rowT[r0 + r] + kT[k0 + k] : src;
-            cp_async8(&tile[buf][r][k], g, valid);
+            const double *g = valid ? src + oz_off<AFF>(rowT, kT, sr, sk, r0 + r, k0 + k) : src;
+            cp_async8(&tile(buf, r, k), g, valid);
         }
         cp_async_commit();
     };
-    int buf = 0;
     int64_t t = blockIdx.x;
-    if (t < ntiles) issue(t, 0);
+#pragma unroll
+    for (int st = 0; st < OZ_STAGES - 1; ++st) {
+        const int64_t ts = t + (int64_t)st * gridDim.x;
+        if (ts < ntiles) issue(ts, st);
+        else cp_async_commit();  // empty groups keep the group count uniform
+    }
+    int buf = 0;
     for (; t < ntiles; t += gridDim.x) {
-        const int64_t tn = t + gridDim.x;
-        if (tn < ntiles) issue(tn, buf ^ 1);
+        const int64_t tn = t + (int64_t)(OZ_STAGES - 1) * gridDim.x;
+        if (tn < ntiles) issue(tn, (buf + OZ_STAGES - 1) % OZ_STAGES);
         else cp_async_commit();
         if (threadIdx.x < TR) smax[threadIdx.x] = 0;
-        cp_async_wait1();
+        cp_async_wait<OZ_STAGES - 1>();
         __syncthreads();
         const int64_t r0 = (t / tiles_k) * TR;
         // row-fast mapping: a thread's elements share one row; otherwise a warp
@@ -153,7 +197,7 @@ __global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict
             int r, k;
             if (ROW_FAST) { r = e % TR; k = e / TR; }
             else { k = e % TKP; r = e / TKP; }
-            unsigned long long b = tile[buf][r][k] & 0x7FFFFFFFFFFFFFFFull;
+            unsigned long long b = tile(buf, r, k) & 0x7FFFFFFFFFFFFFFFull;
             if ((b >> 52) == 0x7FF) b = 0;  // inf / nan do not set the scale
             if (ROW_FAST) {
                 mine = b > mine ? b : mine;
@@ -172,107 +216,184 @@ __global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict
         if (threadIdx.x < TR && r0 + threadIdx.x < rows && smax[threadIdx.x])
             atomicMax(&maxbits[r0 + threadIdx.x], smax[threadIdx.x]);
         __syncthreads();
-        buf ^= 1;
+        buf = (buf + 1) % OZ_STAGES;
+    }
+}
+
+// Row maxima for one mode per class with rows contiguous (|sr| = 1): no
+// staging; a CTA owns 32 rows (lanes) and one slice of K, its 8 warps take
+// interleaved k with 4 loads in flight each, and the warps' maxima meet in
+// shared memory before one atomic per row.
+__global__ void __launch_bounds__(256) oz_maxbits_rows_kernel(const double *__restrict__ src, int64_t sr,
+                                                             int64_t sk, int64_t rows, int64_t K, int64_t kslice,
+                                                             unsigned long long *__restrict__ maxbits)
+{
+    __shared__ unsigned long long red[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t k0 = (int64_t)blockIdx.y * kslice, k1 = min(K, k0 + kslice);
+    unsigned long long mine = 0;
+    if (r < rows) {
+        const unsigned long long *x = reinterpret_cast<const unsigned long long *>(src) + r * sr;
+        int64_t k = k0 + warp;
+        for (; k + 24 < k1; k += 32) {
+            unsigned long long b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[u] = __ldg(x + (k + 8 * u) * sk) & 0x7FFFFFFFFFFFFFFFull;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if ((b[u] >> 52) != 0x7FF && b[u] > mine) mine = b[u];  // inf / nan do not set the scale
+        }
+        for (; k < k1; k += 8) {
+            const unsigned long long b = __ldg(x + k * sk) & 0x7FFFFFFFFFFFFFFFull;
+            if ((b >> 52) != 0x7FF && b > mine) mine = b;
+        }
+    }
+    red[warp][lane] = mine;
+    __syncthreads();
+    if (warp == 0 && r < rows) {
+        for (int w = 1; w < 8; ++w) mine = red[w][lane] > mine ? red[w][lane] : mine;
+        if (mine) atomicMax(&maxbits[r], mine);
     }
 }
 
 // residues of round(x * 2^shift) for every modulus, packed [L][rows][ld] bf16.
-// Tiles of 32 rows x 64 k are gathered with cp.async into a double buffer, so
-// the next tile's loads are in flight while the current one is converted.
+// Tiles of RTR rows x RTKP k are gathered with cp.async through OZ_STAGES
+// buffers, so the next tiles' loads are in flight while one is converted.
 // Each thread converts two neighbouring k of one row and stores both bf16
-// residues of a modulus with one 32-bit store (ld is even, k0 multiple of 64).
-template <int ROW_FAST, int L>
+// residues of a modulus with one 32-bit store (ld is even, k0 a multiple of
+// RTKP); a warp covers 64 k of a row, 128 bytes of every plane.
+template <int ROW_FAST, bool AFF, int L>
 __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict__ src,
                                                        const int64_t *__restrict__ rowT,
-                                                       const int64_t *__restrict__ kT, int64_t rows, int64_t K,
+                                                       const int64_t *__restrict__ kT, int64_t sr, int64_t sk,
+                                                       int64_t rows, int64_t K,
                                                        const unsigned long long *__restrict__ maxbits, int kbits,
                                                        OzConsts c, uint16_t *__restrict__ out, int64_t ld,
                                                        int64_t plane, int64_t neg_from)
 {
-    __shared__ uint64_t tile[2][TR][TKP + 1];
-    __shared__ int sshift[2][TR];
-    const int64_t tiles_k = (K + TKP - 1) / TKP;
-    const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
+    extern __shared__ __align__(16) uint64_t oz_dyn[];
+    auto tile = [&](int b, int r, int k) -> uint64_t & { return oz_dyn[(b * RTR + r) * (RTKP + 1) + k]; };
+    __shared__ int sshift[OZ_STAGES][RTR];
+    const int64_t tiles_k = (K + RTKP - 1) / RTKP;
+    const int64_t ntiles = ((rows + RTR - 1) / RTR) * tiles_k;
     auto issue = [&](int64_t t, int buf) {
-        const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
-        if (threadIdx.x < TR)
+        const int64_t r0 = (t / tiles_k) * RTR, k0 = (t % tiles_k) * RTKP;
+        if (threadIdx.x < RTR)
             sshift[buf][threadIdx.x] = r0 + threadIdx.x < rows ? shift_for(maxbits[r0 + threadIdx.x], kbits) : 0;
 #pragma unroll
-        for (int j = 0; j < TR * TKP / PT; ++j) {
+        for (int j = 0; j < RTR * RTKP / PT; ++j) {
             const int e = threadIdx.x + j * PT;
             int r, k;
-            if (ROW_FAST) { r = e % TR; k = e / TR; }
-            else { k = e % TKP; r = e / TKP; }
+            if (ROW_FAST) { r = e % RTR; k = e / RTR; }
+            else { k = e % RTKP; r = e / RTKP; }
             const bool valid = r0 + r < rows && k0 + k < K;
-            const double *g = valid ? src + rowT[r0 + r] + kT[k0 + k] : src;
-            cp_async8(&tile[buf][r][k], g, valid);
+            const double *g = valid ? src + oz_off<AFF>(rowT, kT, sr, sk, r0 + r, k0 + k) : src;
+            cp_async8(&tile(buf, r, k), g, valid);
         }
         cp_async_commit();
     };
-    int buf = 0;
     int64_t t = blockIdx.x;
-    if (t < ntiles) issue(t, 0);
-    for (; t < ntiles; t += gridDim.x) {
-        const int64_t tn = t + gridDim.x;
-        if (tn < ntiles) issue(tn, buf ^ 1);
-        else cp_async_commit();  // empty group keeps the group count uniform
-        cp_async_wait1();
-        __syncthreads();
-        const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
 #pragma unroll
-        for (int j = 0; j < TR * TKP / (2 * PT); ++j) {
+    for (int st = 0; st < OZ_STAGES - 1; ++st) {
+        const int64_t ts = t + (int64_t)st * gridDim.x;
+        if (ts < ntiles) issue(ts, st);
+        else cp_async_commit();  // empty groups keep the group count uniform
+    }
+    int buf = 0;
+    for (; t < ntiles; t += gridDim.x) {
+        const int64_t tn = t + (int64_t)(OZ_STAGES - 1) * gridDim.x;
+        if (tn < ntiles) issue(tn, (buf + OZ_STAGES - 1) % OZ_STAGES);
+        else cp_async_commit();
+        cp_async_wait<OZ_STAGES - 1>();
+        __syncthreads();
+        const int64_t r0 = (t / tiles_k) * RTR, k0 = (t % tiles_k) * RTKP;
+#pragma unroll
+        for (int j = 0; j < RTR * RTKP / (2 * PT); ++j) {
             const int e = threadIdx.x + j * PT;
-            const int kp = e % (TKP / 2), r = e / (TKP / 2);
+            const int kp = e % (RTKP / 2), r = e / (RTKP / 2);
             const int k = 2 * kp;
             if (r0 + r >= rows || k0 + k >= K) continue;
             // four 13-bit limbs of the scaled integer, sign applied to the limbs,
-            // converted to float through the 2^23 mantissa (no conversion op)
-            float l0[2], l1[2], l2[2], l3[2];
+            // converted to float through the 2^23 mantissa (no conversion op);
+            // the two elements travel as one f32x2 pair
+            uint32_t lb[4][2], sgb[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const uint64_t bits = tile[buf][r][k + u];
+                const uint64_t bits = tile(buf, r, k + u);
                 const uint64_t v = scaled_int(bits & 0x7FFFFFFFFFFFFFFFull, sshift[buf][r]);
                 // k >= neg_from: the value enters negated (the -Im block of the
                 // real form of a complex matrix)
                 const bool neg = ((bits >> 63) != 0) != (k0 + k + u >= neg_from);
-                const float sg = neg ? -1.f : 1.f;
-                l0[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)(v & 0x1FFF)) - 8388608.0f);
-                l1[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)((v >> 13) & 0x1FFF)) - 8388608.0f);
-                l2[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)((v >> 26) & 0x1FFF)) - 8388608.0f);
-                l3[u] = sg * (__int_as_float(0x4B000000 | (uint32_t)(v >> 39)) - 8388608.0f);
+                sgb[u] = neg ? 0xBF800000u : 0x3F800000u;  // -1.0f / 1.0f
+                lb[0][u] = 0x4B000000u | (uint32_t)(v & 0x1FFF);
+                lb[1][u] = 0x4B000000u | (uint32_t)((v >> 13) & 0x1FFF);
+                lb[2][u] = 0x4B000000u | (uint32_t)((v >> 26) & 0x1FFF);
+                lb[3][u] = 0x4B000000u | (uint32_t)(v >> 39);
             }
+            constexpr uint64_t kNeg2p23 = pair_bits(0xCB000000u, 0xCB000000u);  // -2^23
+            const uint64_t sg = pair_bits(sgb[0], sgb[1]);
+            uint64_t limb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) limb[i] = mul2(add2(pair_bits(lb[i][0], lb[i][1]), kNeg2p23), sg);
+            constexpr uint64_t kMagic = pair_bits(0x4B400000u, 0x4B400000u);     // 1.5 * 2^23
+            constexpr uint64_t kNegMagic = pair_bits(0xCB400000u, 0xCB400000u);
             uint32_t *o = reinterpret_cast<uint32_t *>(out + (r0 + r) * ld + k0 + k);
+            const int64_t plane2 = plane / 2;  // plane pitch in 32-bit words (plane is even)
 #pragma unroll
-            for (int l = 0; l < L; ++l) {
-                float x[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    // |s| <= 127 * 3 * 8191 + 8192 < 2^22: exact; nearest rounding of
-                    // s / p is exact for odd p, so the residue lies in [-(p-1)/2, (p-1)/2]
-                    const float sum = fmaf(l3[u], c.c39[l], fmaf(l2[u], c.c26[l], fmaf(l1[u], c.c13[l], l0[u])));
-                    x[u] = fmaf(-round_mul(sum, c.invp[l]), c.pf[l], sum);
-                }
+            for (int l = 0; l < L; ++l, o += plane2) {
+                // |s| <= 127 * 3 * 8191 + 8192 < 2^22: exact; nearest rounding of
+                // s / p is exact for odd p, so the residue lies in [-(p-1)/2, (p-1)/2]
+                uint64_t sum = fma2(limb[1], c.k13[l], limb[0]);
+                sum = fma2(limb[2], c.k26[l], sum);
+                sum = fma2(limb[3], c.k39[l], sum);
+                const uint64_t q = add2(fma2(sum, c.kinv[l], kMagic), kNegMagic);
+                const uint64_t x = fma2(q, c.knegp[l], sum);
                 // |x| <= 127 has at most 7 significant bits: its bf16 pattern is the
                 // upper half of the fp32 pattern; pack both upper halves at once
-                o[(l * plane) / 2] = __byte_perm(__float_as_uint(x[0]), __float_as_uint(x[1]), 0x7632);
+                *o = __byte_perm((uint32_t)x, (uint32_t)(x >> 32), 0x7632);
             }
         }
         __syncthreads();
-        buf ^= 1;
+        buf = (buf + 1) % OZ_STAGES;
     }
 }
 
-template <int ROW_FAST>
-cudaError_t launch_residues(const double *src, const int64_t *rowT, const int64_t *kT, int64_t rows, int64_t K,
-                            const unsigned long long *maxbits, int kbits, const OzConsts &c, uint16_t *out,
-                            int64_t ld, int blocks, cudaStream_t s, int64_t plane = -1, int64_t neg_from = -1)
+// Dynamic shared memory above 48 KB needs the per-kernel opt-in, once per
+// kernel (the template parameter is the kernel itself).
+template <auto KERNEL>
+cudaError_t oz_smem_optin()
+{
+    static const cudaError_t e =
+        cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    return e;
+}
+
+template <int ROW_FAST, bool AFF>
+cudaError_t launch_maxbits(const double *src, const int64_t *rowT, const int64_t *kT, int64_t sr, int64_t sk,
+                           int64_t rows, int64_t K, unsigned long long *maxbits, int blocks, cudaStream_t s)
+{
+    cudaError_t e = oz_smem_optin<oz_maxbits_kernel<ROW_FAST, AFF>>();
+    if (e != cudaSuccess) return e;
+    oz_maxbits_kernel<ROW_FAST, AFF><<<blocks, PT, OZ_SMEM, s>>>(src, rowT, kT, sr, sk, rows, K, maxbits);
+    return cudaGetLastError();
+}
+
+template <int ROW_FAST, bool AFF>
+cudaError_t launch_residues(const double *src, const int64_t *rowT, const int64_t *kT, int64_t sr, int64_t sk,
+                            int64_t rows, int64_t K, const unsigned long long *maxbits, int kbits,
+                            const OzConsts &c, uint16_t *out, int64_t ld, int blocks, cudaStream_t s,
+                            int64_t plane = -1, int64_t neg_from = -1)
 {
     if (plane < 0) plane = rows * ld;
     if (neg_from < 0) neg_from = K;
-#define CASE(LL)                                                                                    \
-    case LL:                                                                                        \
-        oz_residue_kernel<ROW_FAST, LL><<<blocks, PT, 0, s>>>(src, rowT, kT, rows, K, maxbits, kbits, c, out, ld, \
-                                                              plane, neg_from);                     \
+    cudaError_t e = cudaSuccess;
+#define CASE(LL)                                                                                          \
+    case LL:                                                                                              \
+        e = oz_smem_optin<oz_residue_kernel<ROW_FAST, AFF, LL>>();                                          \
+        if (e != cudaSuccess) return e;                                                                   \
+        oz_residue_kernel<ROW_FAST, AFF, LL><<<blocks, PT, OZ_SMEM, s>>>(src, rowT, kT, sr, sk, rows, K, maxbits, \
+                                                                         kbits, c, out, ld, plane, neg_from); \
         break;
     switch (c.L) {
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
@@ -283,17 +404,48 @@ cudaError_t launch_residues(const double *src, const int64_t *rowT, const int64_
     return cudaGetLastError();
 }
 
-template <int L>
+// n = i / M for 32-bit i through a precomputed multiplier (Granlund and
+// Montgomery's round-up method): the multiplier is 2^32 + mul = ceil(2^(32 +
+// shift) / M) with shift = ceil(log2 M), exact for every i < 2^32 and
+// 1 <= M < 2^31 (the launcher's condition; checked exhaustively near 0, near
+// 2^32 and around every multiple of M for divisors up to 2^31).
+struct Div32 {
+    uint32_t d, mul, shift;
+};
+inline Div32 make_div32(uint32_t d)
+{
+    Div32 r{d, 0, 0};
+    uint32_t sh = 0;
+    while ((1ull << sh) < d) ++sh;
+    r.shift = sh;
+    r.mul = (uint32_t)((((1ull << (32 + sh)) + d - 1) / d) & 0xFFFFFFFFull);
+    return r;
+}
+__device__ __forceinline__ uint32_t div32(const Div32 &q, uint32_t i)
+{
+    // (2^32 + mul) * i >> (32 + shift), the 2^32 term as i itself
+    const uint64_t t = (uint64_t)__umulhi(i, q.mul) + i;
+    return (uint32_t)(t >> q.shift);
+}
+
+template <int L, bool IDX32>
 __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ R, int64_t M, int64_t N,
                                                     const unsigned long long *__restrict__ maxA,
                                                     const unsigned long long *__restrict__ maxB,
                                                     const int64_t *__restrict__ rowC,
                                                     const int64_t *__restrict__ colC, double *__restrict__ C,
-                                                    OzConsts c, int64_t shift_rows, Scale sc)
+                                                    OzConsts c, int64_t shift_rows, Scale sc, Div32 divM)
 {
     const int64_t MN = M * N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = i % M, n = i / M;
+        int64_t m, n;
+        if (IDX32) {
+            n = div32(divM, (uint32_t)i);
+            m = i - n * M;
+        } else {
+            m = i % M;
+            n = i / M;
+        }
         // Garner's mixed-radix digits: X = v_0 + p_0 v_1 + p_0 p_1 v_2 + ...,
         // v_a = (r_a - sum_{b<a} v_b (p_0..p_{b-1} mod p_a)) (p_0..p_{a-1})^{-1} mod p_a.
         // fp32 holds every intermediate exactly: the prefix sum is at most
@@ -324,25 +476,37 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
         for (int a = L - 1; a >= 0; --a)
             if (cmp == 0) cmp = v[a] > c.halff[a] ? 1 : (v[a] < c.halff[a] ? -1 : 0);
         const bool negv = cmp > 0;
-        // exact Horner evaluation of the mixed-radix digits in three 64-bit
-        // limbs (|X| < P < 2^160), then one correctly rounded conversion
-        uint64_t h0 = 0, h1 = 0, h2 = 0;
+        // exact Horner evaluation of the mixed-radix digits (|X| < P < 2^160)
+        // in five 32-bit limbs, two digits per step: h <- h p_a p_{a-1} +
+        // (d_a p_{a-1} + d_{a-1}), with p_a p_{a-1} < 2^16; then one correctly
+        // rounded conversion.  Negative values use the digits of P - 1 - X.
+        uint32_t dg[L];
 #pragma unroll
-        for (int a = L - 1; a >= 0; --a) {
-            const uint64_t pa = (uint64_t)c.p[a];
+        for (int a = 0; a < L; ++a) {
             // exact small non-negative integer float -> integer via the 2^23 mantissa
             const float df = negv ? (c.pf[a] - 1.f - v[a]) : v[a];
-            const uint64_t d = (uint64_t)(__float_as_int(df + 8388608.0f) & 0x7FFFFF);
-            const uint64_t l0 = h0 * pa, c0 = __umul64hi(h0, pa);
-            const uint64_t l1 = h1 * pa, c1 = __umul64hi(h1, pa);
-            h2 = h2 * pa + c1;
-            h1 = l1 + c0;
-            h2 += (h1 < c0) ? 1 : 0;
-            h0 = l0 + d;
-            const uint64_t k0 = (h0 < d) ? 1 : 0;
-            h1 += k0;
-            h2 += (k0 && h1 == 0) ? 1 : 0;
+            dg[a] = (uint32_t)(__float_as_int(df + 8388608.0f) & 0x7FFFFF);
         }
+        uint32_t h[5] = {0, 0, 0, 0, 0};
+        int a = L - 1;
+        if (L % 2) {
+            h[0] = dg[L - 1];
+            --a;
+        }
+#pragma unroll
+        for (; a > 0; a -= 2) {
+            const uint32_t q = (uint32_t)c.p[a] * (uint32_t)c.p[a - 1];
+            uint64_t carry = (uint64_t)dg[a] * (uint32_t)c.p[a - 1] + dg[a - 1];
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                const uint64_t prod = (uint64_t)h[t] * q + carry;
+                h[t] = (uint32_t)prod;
+                carry = prod >> 32;
+            }
+        }
+        uint64_t h0 = ((uint64_t)h[1] << 32) | h[0];
+        uint64_t h1 = ((uint64_t)h[3] << 32) | h[2];
+        uint64_t h2 = h[4];
         if (negv) {  // value = -(X' + 1)
             h0 += 1;
             if (h0 == 0) {
@@ -370,7 +534,10 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
             drop = 0;
         }
         const double mag = __ull2double_rn(top);
-        const int e = drop - (shift_for(maxA[m % shift_rows], c.ka) + shift_for(maxB[n], c.kb));
+        // row of the scale: m, or m - shift_rows for the imaginary rows of the
+        // complex real form (M is shift_rows or twice it)
+        const int64_t ms = m >= shift_rows ? m - shift_rows : m;
+        const int e = drop - (shift_for(maxA[ms], c.ka) + shift_for(maxB[n], c.kb));
         // mag * 2^e in two exact power-of-two steps (no overflow of the factors)
         const int e1 = e / 2, e2 = e - e1;
         const double f1 = __longlong_as_double((long long)(e1 + 1023) << 52);
@@ -484,6 +651,16 @@ void oz_setup(int64_t K, int want_L, OzConsts *c)
         c->c13[i] = sym(m13);
         c->c26[i] = sym(m13 * m13);
         c->c39[i] = sym(m13 * m13 % p * m13);
+        auto pair = [](float f) {
+            uint32_t b;
+            std::memcpy(&b, &f, 4);
+            return pair_bits(b, b);
+        };
+        c->k13[i] = pair(c->c13[i]);
+        c->k26[i] = pair(c->c26[i]);
+        c->k39[i] = pair(c->c39[i]);
+        c->kinv[i] = pair(c->invp[i]);
+        c->knegp[i] = pair(-c->pf[i]);
         long long pre = 1;  // (p_0 ... p_{j-1}) mod p
         for (int j = 0; j < OZ_MAX_L; ++j) {
             long long w = pre % p;
@@ -509,7 +686,14 @@ void launch_crt_t(const int8_t *R, int64_t M, int64_t N, const unsigned long lon
 {
     const int64_t MN = M * N;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((MN + 255) / 256, (int64_t)num_sms * 16));
-    oz_crt_kernel<L><<<blocks, 256, 0, s>>>(R, M, N, maxA, maxB, rowC, colC, C, c, shift_rows, sc);
+    if (MN < (1LL << 32) && M < (1LL << 31)) {
+        // every grid-stride index stays below 2^32 + 2^31: i < MN < 2^32 when it is used
+        oz_crt_kernel<L, true><<<blocks, 256, 0, s>>>(R, M, N, maxA, maxB, rowC, colC, C, c, shift_rows, sc,
+                                                       make_div32((uint32_t)M));
+    } else {
+        oz_crt_kernel<L, false><<<blocks, 256, 0, s>>>(R, M, N, maxA, maxB, rowC, colC, C, c, shift_rows, sc,
+                                                        Div32{1, 0, 0});
+    }
 }
 
 cudaError_t launch_crt(const int8_t *R, int64_t M, int64_t N, const unsigned long long *maxA,
@@ -589,6 +773,55 @@ size_t ozaki_workspace_bytes(const Plan &p, int L)
     return oz_layout(p, L, nullptr).total;
 }
 
+namespace {
+
+cudaError_t oz_maxbits(const double *X, const int64_t *rowT, const int64_t *kT, bool row_fast, bool aff, int64_t sr,
+                       int64_t sk, int64_t rows, int64_t K, unsigned long long *mx, int blocks, cudaStream_t s)
+{
+    if (aff && (sr == 1 || sr == -1) && rows > 0 && K > 0) {
+        // enough CTAs for about 16 per SM; each K slice at least 256 long
+        const int64_t rb = (rows + 31) / 32;
+        const int64_t want = std::max<int64_t>(1, (2LL * blocks + rb - 1) / rb);
+        const int64_t slices = std::min<int64_t>(want, std::max<int64_t>(1, K / 256));
+        const int64_t kslice = (K + slices - 1) / slices;
+        dim3 grid((unsigned)rb, (unsigned)((K + kslice - 1) / kslice));
+        oz_maxbits_rows_kernel<<<grid, 256, 0, s>>>(X, sr, sk, rows, K, kslice, mx);
+        return cudaGetLastError();
+    }
+    if (row_fast) return aff ? launch_maxbits<1, true>(X, rowT, kT, sr, sk, rows, K, mx, blocks, s)
+                             : launch_maxbits<1, false>(X, rowT, kT, sr, sk, rows, K, mx, blocks, s);
+    return aff ? launch_maxbits<0, true>(X, rowT, kT, sr, sk, rows, K, mx, blocks, s)
+               : launch_maxbits<0, false>(X, rowT, kT, sr, sk, rows, K, mx, blocks, s);
+}
+
+cudaError_t oz_residues(const double *X, const int64_t *rowT, const int64_t *kT, bool row_fast, bool aff, int64_t sr,
+                        int64_t sk, int64_t rows, int64_t K, const unsigned long long *mx, int kbits,
+                        const OzConsts &c, uint16_t *out, int64_t ld, int blocks, cudaStream_t s, int64_t plane = -1,
+                        int64_t neg_from = -1)
+{
+    if (row_fast)
+        return aff ? launch_residues<1, true>(X, rowT, kT, sr, sk, rows, K, mx, kbits, c, out, ld, blocks, s, plane,
+                                              neg_from)
+                   : launch_residues<1, false>(X, rowT, kT, sr, sk, rows, K, mx, kbits, c, out, ld, blocks, s, plane,
+                                               neg_from);
+    return aff ? launch_residues<0, true>(X, rowT, kT, sr, sk, rows, K, mx, kbits, c, out, ld, blocks, s, plane,
+                                          neg_from)
+               : launch_residues<0, false>(X, rowT, kT, sr, sk, rows, K, mx, kbits, c, out, ld, blocks, s, plane,
+                                           neg_from);
+}
+
+// Scale scan (row maxima) then residue planes of one operand.
+cudaError_t oz_scan_and_residues(const double *X, const int64_t *rowT, const int64_t *kT, bool row_fast, bool aff,
+                                 int64_t sr, int64_t sk, int64_t rows, int64_t K, unsigned long long *mx, int kbits,
+                                 const OzConsts &c, uint16_t *out, int64_t ld, int blocks, cudaStream_t s)
+{
+    cudaError_t e = oz_maxbits(X, rowT, kT, row_fast, aff, sr, sk, rows, K, mx, blocks, s);
+    if (e != cudaSuccess) return e;
+    return oz_residues(X, rowT, kT, row_fast, aff, sr, sk, rows, K, mx, kbits, c, out, ld, blocks, s);
+}
+
+}  // namespace
+
 cudaError_t launch_ozaki(const Plan &pl, int L_req, const void *A, const void *B, void *C, void *ws, int num_sms,
                          int *err, cudaStream_t s)
 {
@@ -610,15 +843,15 @@ cudaError_t launch_ozaki(const Plan &pl, int L_req, const void *A, const void *B
         int64_t n = ((rows + TR - 1) / TR) * ((pl.K + TKP - 1) / TKP);
         return (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * 8));
     };
-    if (a_row_fast) oz_maxbits_kernel<1><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA);
-    else oz_maxbits_kernel<0><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA);
-    if (b_row_fast) oz_maxbits_kernel<1><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB);
-    else oz_maxbits_kernel<0><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB);
-    e = a_row_fast ? launch_residues<1>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA, c.ka, c, o.RA, o.ld, blocks_for(pl.M), s)
-                   : launch_residues<0>(Ab, o.rowA, o.kA, pl.M, pl.K, o.maxA, c.ka, c, o.RA, o.ld, blocks_for(pl.M), s);
+    // one mode per class after fusion: addresses without the offset tables
+    const bool a_aff = pl.m.n <= 1 && pl.k.n <= 1, b_aff = pl.n.n <= 1 && pl.k.n <= 1;
+    const int64_t a_sr = pl.m.n ? pl.m.s0[0] : 0, a_sk = pl.k.n ? pl.k.s0[0] : 0;
+    const int64_t b_sr = pl.n.n ? pl.n.s0[0] : 0, b_sk = pl.k.n ? pl.k.s1[0] : 0;
+    e = oz_scan_and_residues(Ab, o.rowA, o.kA, a_row_fast, a_aff, a_sr, a_sk, pl.M, pl.K, o.maxA, c.ka, c, o.RA,
+                             o.ld, blocks_for(pl.M), s);
     if (e != cudaSuccess) return e;
-    e = b_row_fast ? launch_residues<1>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB, c.kb, c, o.RB, o.ld, blocks_for(pl.N), s)
-                   : launch_residues<0>(Bb, o.colB, o.kB, pl.N, pl.K, o.maxB, c.kb, c, o.RB, o.ld, blocks_for(pl.N), s);
+    e = oz_scan_and_residues(Bb, o.colB, o.kB, b_row_fast, b_aff, b_sr, b_sk, pl.N, pl.K, o.maxB, c.kb, c, o.RB,
+                             o.ld, blocks_for(pl.N), s);
     if (e != cudaSuccess) return e;
     TcGemmParams p{};
     p.M = pl.M;
@@ -723,24 +956,19 @@ cudaError_t launch_ozaki_complex(const Plan &pl, int L_req, const void *A, const
         return (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * 8));
     };
     // scales: a complex row's maximum over both parts (its re-row covers both)
-    if (a_row_fast) oz_maxbits_kernel<1><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA2, o.kAre, pl.M, K2, o.maxA);
-    else oz_maxbits_kernel<0><<<blocks_for(pl.M), PT, 0, s>>>(Ab, o.rowA2, o.kAre, pl.M, K2, o.maxA);
-    if (b_row_fast) oz_maxbits_kernel<1><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB2, o.kB2, pl.N, K2, o.maxB);
-    else oz_maxbits_kernel<0><<<blocks_for(pl.N), PT, 0, s>>>(Bb, o.colB2, o.kB2, pl.N, K2, o.maxB);
+    e = oz_maxbits(Ab, o.rowA2, o.kAre, a_row_fast, false, 0, 0, pl.M, K2, o.maxA, blocks_for(pl.M), s);
+    if (e == cudaSuccess) e = oz_maxbits(Bb, o.colB2, o.kB2, b_row_fast, false, 0, 0, pl.N, K2, o.maxB, blocks_for(pl.N), s);
+    if (e != cudaSuccess) return e;
     const int64_t planeA = M2 * o.ld;
     // re-rows: [Re | -Im], im-rows: [Im | Re]
-    e = a_row_fast ? launch_residues<1>(Ab, o.rowA2, o.kAre, pl.M, K2, o.maxA, c.ka, c, o.RA, o.ld, blocks_for(pl.M), s,
-                                        planeA, pl.K)
-                   : launch_residues<0>(Ab, o.rowA2, o.kAre, pl.M, K2, o.maxA, c.ka, c, o.RA, o.ld, blocks_for(pl.M), s,
-                                        planeA, pl.K);
+    e = oz_residues(Ab, o.rowA2, o.kAre, a_row_fast, false, 0, 0, pl.M, K2, o.maxA, c.ka, c, o.RA, o.ld,
+                    blocks_for(pl.M), s, planeA, pl.K);
     if (e != cudaSuccess) return e;
-    e = a_row_fast ? launch_residues<1>(Ab, o.rowA2 + pl.M, o.kAim, pl.M, K2, o.maxA, c.ka, c, o.RA + pl.M * o.ld,
-                                        o.ld, blocks_for(pl.M), s, planeA, K2)
-                   : launch_residues<0>(Ab, o.rowA2 + pl.M, o.kAim, pl.M, K2, o.maxA, c.ka, c, o.RA + pl.M * o.ld,
-                                        o.ld, blocks_for(pl.M), s, planeA, K2);
+    e = oz_residues(Ab, o.rowA2 + pl.M, o.kAim, a_row_fast, false, 0, 0, pl.M, K2, o.maxA, c.ka, c,
+                    o.RA + pl.M * o.ld, o.ld, blocks_for(pl.M), s, planeA, K2);
     if (e != cudaSuccess) return e;
-    e = b_row_fast ? launch_residues<1>(Bb, o.colB2, o.kB2, pl.N, K2, o.maxB, c.kb, c, o.RB, o.ld, blocks_for(pl.N), s)
-                   : launch_residues<0>(Bb, o.colB2, o.kB2, pl.N, K2, o.maxB, c.kb, c, o.RB, o.ld, blocks_for(pl.N), s);
+    e = oz_residues(Bb, o.colB2, o.kB2, b_row_fast, false, 0, 0, pl.N, K2, o.maxB, c.kb, c, o.RB, o.ld,
+                    blocks_for(pl.N), s);
     if (e != cudaSuccess) return e;
     TcGemmParams p{};
     p.M = M2;
