@@ -54,10 +54,12 @@ constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_THREADS = (2 + NUM_EPI_WARPS) * 32;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 
+#define GETT_MF(i) static_cast<float>(kOzModuli[i])
 __constant__ float c_moduli[OZ_MAX_L] = {
-    kOzModuli[0],  kOzModuli[1],  kOzModuli[2],  kOzModuli[3],  kOzModuli[4],  kOzModuli[5],  kOzModuli[6],
-    kOzModuli[7],  kOzModuli[8],  kOzModuli[9],  kOzModuli[10], kOzModuli[11], kOzModuli[12], kOzModuli[13],
-    kOzModuli[14], kOzModuli[15], kOzModuli[16], kOzModuli[17], kOzModuli[18], kOzModuli[19]};
+    GETT_MF(0),  GETT_MF(1),  GETT_MF(2),  GETT_MF(3),  GETT_MF(4),  GETT_MF(5),  GETT_MF(6),
+    GETT_MF(7),  GETT_MF(8),  GETT_MF(9),  GETT_MF(10), GETT_MF(11), GETT_MF(12), GETT_MF(13),
+    GETT_MF(14), GETT_MF(15), GETT_MF(16), GETT_MF(17), GETT_MF(18), GETT_MF(19)};
+#undef GETT_MF
 
 template <int MODE>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
