@@ -374,7 +374,7 @@ def gpu_arm(args, dist: Dist):
         result["forms"] = measure_forms(args.workload)
         result["forms"].update(measure_split_forms())
         result["forms"].update(measure_streaming_forms(pk.get("dfma_tflops")))
-        result["forms"]["batched"] = measure_batched()
+        result["forms"]["batched"] = measure_batched(ffma_tflops=pk.get("ffma_tflops"))
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         v, cores, desc, dt = oracle_sample(p, args.cpu_seconds)
         result["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
@@ -599,10 +599,12 @@ def measure_split_forms():
 MODEL_PATH = os.path.join(ROOT, "paper_2410_06770_gb300", "models", "planner_mlp.npz")
 
 
-def measure_batched(n=4096):
+def measure_batched(n=4096, ffma_tflops=None):
     """The batched workload: one persistent launch (CUDA graph replay) for all
     contractions vs one plain call per contraction, with heuristic, tuned and
-    (if a trained model is committed) learned tile configurations."""
+    (if a trained model is committed) learned tile configurations.  Roofline:
+    the sum over problems of max(2|C|K / FFMA peak, bytes / HBM), bytes = A
+    and B at their storage size plus C read and written (fp32)."""
     import torch
     import oracle
     from paper_2410_06770_gb300 import batch as gb
@@ -666,6 +668,17 @@ def measure_batched(n=4096):
         out["batched_learned"] = tune.throughput(probs, "learned")
         gb.clear_model()
     out["speedup_batched_vs_per_call"] = out["per_call"]["ms"] / out["batched_heuristic"]["ms"]
+    if ffma_tflops:
+        bw = measured_peaks().get("hbm_gbs", 6800.0) * 1e9
+        roof_s = 0.0
+        for pr in probs:
+            esz = 2 if pr["dtype"] == "bf16" else 4
+            nbytes = esz * (pr["la"].numel + pr["lb"].numel) + 8 * pr["lc"].numel
+            roof_s += max(tune.flops(pr) / (ffma_tflops * 1e12), nbytes / bw)
+        best = min(v["ms"] for k, v in out.items() if k.startswith("batched_"))
+        out["roofline"] = {"ms": roof_s * 1e3, "frac_of_best": roof_s * 1e3 / best,
+                           "definition": "sum over problems of max(flops / FFMA peak, bytes / HBM), "
+                                         "FFMA peak measured, HBM of MEASURED_PEAKS"}
     return out
 
 

@@ -269,3 +269,36 @@ def test_reduction_argument_positions(L, kw, pos):
 def test_aux_empty_outputs_are_noops(L):
     assert _getp(EXTA=(3, 0, 5))[0] == gett.GETT_OK
     assert _getr(EXTA=(0, 4, 5))[0] == gett.GETT_OK
+
+
+def _unfusable_free_modes(n):
+    """A with n free modes of extent 2 (increments 1, 2, 4, ...) and one
+    contracted mode of extent 3, B a vector over that mode; C holds A's free
+    modes in reverse order, so no two of them fuse (their C increments fall
+    as their A increments rise)."""
+    exta = (2,) * n + (3,)
+    inca = tuple(2 ** i for i in range(n)) + (2 ** n,)
+    perm = tuple(range(n - 1, -1, -1))
+    incc = tuple(2 ** i for i in range(n))
+    return exta, inca, perm, incc
+
+
+@pytest.mark.parametrize("n,ok", [(24, True), (25, False)])
+def test_modes_per_class_limit(L, n, ok):
+    """At most 24 modes of extent > 1 per class after fusion (GETT_MAX_MODES);
+    beyond that GETT_ERR_UNSUPPORTED, before any device work."""
+    exta, inca, perm, incc = _unfusable_free_modes(n)
+    st, info = gett.plan_describe(n + 1, exta, inca, 1, (3,), (1,), 1, (n,), (0,), perm, incc)
+    if ok:
+        assert st == gett.GETT_OK and info["nm"] == n and info["M"] == 2 ** n
+    else:
+        assert st == gett.GETT_ERR_UNSUPPORTED
+
+
+def test_rank_limit_as_passed(L):
+    """64 modes per tensor as passed (GETT_MAX_RANK); extent-1 modes squeeze."""
+    st, info = gett.plan_describe(64, (1,) * 63 + (5,), (1,) * 64, 1, (5,), (1,), 1, (63,), (0,),
+                                  tuple(range(63)), (1,) * 63)
+    assert st == gett.GETT_OK and info["K"] == 5 and info["nm"] == 0
+    st, _ = _call(L, RANKA=65, EXTA=(1,) * 65, INCA=(1,) * 65)
+    assert st == gett.GETT_ERR_ARG and gett.last_error_arg() == 1

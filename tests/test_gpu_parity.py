@@ -172,3 +172,18 @@ def test_streaming_short_sums_and_skinny(prefix, name):
     compare(prefix, q, got, oracle_ref(q))
     got2, rep2 = run_gpu(prefix, q)  # the selector's own choice
     compare(prefix, q, got2, oracle_ref(q))
+
+
+@pytest.mark.parametrize("prefix", ("d", "z"))
+def test_most_modes_per_class(prefix):
+    """24 unfusable free modes in A (the per-class limit after fusion), one
+    contracted mode; C holds them in reverse order.  Integer data: bit-exact."""
+    n = 24
+    exta = (2,) * n + (3,)
+    perm = tuple(range(n - 1, -1, -1)) + (n,)
+    sig = synth.Signature(exta, (3, 2), (n,), (0,), perm)
+    dtype = np.complex128 if prefix == "z" else np.float64
+    p = synth.make_problem(sig, np.random.default_rng(24), dtype, "int", ("contig", "contig", "contig"), "int")
+    got, rep = run_gpu(prefix, p, mode="ex")
+    assert rep["nm"] == n
+    compare(prefix, p, got, oracle_ref(p), exact=True)
