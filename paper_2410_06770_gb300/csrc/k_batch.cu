@@ -112,12 +112,14 @@ __global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *
     __shared__ float smem_f[smem_floats()];
     __shared__ int64_t smem_i[smem_ints()];
     __shared__ unsigned long long s_item;
-    while (true) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
-        __syncthreads();
-        const unsigned long long it = s_item;
-        __syncthreads();
-        if (it >= (unsigned long long)nwork) break;
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
+    __syncthreads();
+    unsigned long long it = s_item;
+    while (it < (unsigned long long)nwork) {
+        // thread 0 asks for the next item now: the atomic's round trip overlaps
+        // this item's tile (most items are a few tens of KFLOP)
+        unsigned long long next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1ull);
         const uint2 w = work[it % (unsigned long long)wrap];
         const BatchProb pr = probs[w.x];
         const int key = pr.cfg * 2 + pr.dtype;
@@ -132,7 +134,10 @@ __global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *
         case 7: run_tile<uint16_t, 3>(pr, tables, w.y, smem_f, smem_i); break;
         default: break;
         }
+        __syncthreads();  // the tile's shared memory and s_item are free again
+        if (threadIdx.x == 0) s_item = next;
         __syncthreads();
+        it = s_item;
     }
 }
 
