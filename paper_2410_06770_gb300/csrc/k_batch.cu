@@ -89,6 +89,69 @@ __device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tab
     dense_tile<T, c.bm, c.bn, c.bk, c.tm, c.tn>(a, smem_f, smem_f + 2 * c.bk * c.bm, smem_i, smem_i + c.bm);
 }
 
+// Short sums (K <= 8, one K slice): each thread forms its TM x TN outputs
+// straight from gathered loads -- no shared-memory staging, no barriers, no
+// padding of K to the tile's BK.  Same thread-to-output mapping as the staged
+// tile (lanes along C's smaller increment) and the same summation order (k
+// ascending from zero, then added to C), so the results are identical.
+template <class T, int CFG>
+__device__ __forceinline__ void run_direct(const BatchProb &pr, const int64_t *tables, int item)
+{
+    using R = Tr<T>;
+    using Acc = typename R::Acc;
+    constexpr BCfg c = kB[CFG];
+    constexpr int TM = c.tm, TN = c.tn, RM = c.bm / c.tm, RN = c.bn / c.tn;
+    const int tile = item;  // one slice
+    const int64_t m0 = (int64_t)(tile / pr.tiles_n) * c.bm, n0 = (int64_t)(tile % pr.tiles_n) * c.bn;
+    const int64_t *rowA = tables + pr.tab;
+    const int64_t *rowC = rowA + pr.M, *colB = rowC + pr.M, *colC = colB + pr.N, *kA = colC + pr.N;
+    const int64_t *kB = kA + pr.K;
+    const int tid = threadIdx.x;
+    int tm, tn;
+    if (pr.c_m_fast) { tm = tid % RM; tn = tid / RM; }
+    else { tn = tid % RN; tm = tid / RN; }
+    const T *A = static_cast<const T *>(pr.A);
+    const T *B = static_cast<const T *>(pr.B);
+    int64_t oa[TM], oc[TM], ob[TN], od[TN];
+    bool vm[TM], vn[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t m = m0 + tm + i * RM;
+        vm[i] = m < pr.M;
+        oa[i] = vm[i] ? rowA[m] : 0;
+        oc[i] = vm[i] ? rowC[m] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        const int64_t n = n0 + tn + j * RN;
+        vn[j] = n < pr.N;
+        ob[j] = vn[j] ? colB[n] : 0;
+        od[j] = vn[j] ? colC[n] : 0;
+    }
+    Acc acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = R::zero();
+    for (int64_t k = 0; k < pr.K; ++k) {
+        const int64_t ka = kA[k], kb = kB[k];
+        Acc a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = vm[i] ? R::load(A + oa[i] + ka) : R::zero();
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = vn[j] ? R::load(B + ob[j] + kb) : R::zero();
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) R::mac(acc[i][j], a[i], b[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+            if (vm[i] && vn[j]) R::store_add(pr.C + oc[i] + od[j], acc[i][j]);
+}
+
 // largest shared footprint over the configurations (floats / int64s)
 constexpr int smem_floats()
 {
@@ -123,7 +186,19 @@ __global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *
         const uint2 w = work[it % (unsigned long long)wrap];
         const BatchProb pr = probs[w.x];
         const int key = pr.cfg * 2 + pr.dtype;
-        switch (key) {
+        if (pr.K <= 8 && pr.splits == 1) {
+            switch (key) {
+            case 0: run_direct<float, 0>(pr, tables, w.y); break;
+            case 1: run_direct<uint16_t, 0>(pr, tables, w.y); break;
+            case 2: run_direct<float, 1>(pr, tables, w.y); break;
+            case 3: run_direct<uint16_t, 1>(pr, tables, w.y); break;
+            case 4: run_direct<float, 2>(pr, tables, w.y); break;
+            case 5: run_direct<uint16_t, 2>(pr, tables, w.y); break;
+            case 6: run_direct<float, 3>(pr, tables, w.y); break;
+            case 7: run_direct<uint16_t, 3>(pr, tables, w.y); break;
+            default: break;
+            }
+        } else switch (key) {
         case 0: run_tile<float, 0>(pr, tables, w.y, smem_f, smem_i); break;
         case 1: run_tile<uint16_t, 0>(pr, tables, w.y, smem_f, smem_i); break;
         case 2: run_tile<float, 1>(pr, tables, w.y, smem_f, smem_i); break;
