@@ -2,12 +2,13 @@
 //
 // OUTER: no contracted mode of extent > 1 (the thesis's "nothing
 // contraction", Sec. 7): C[m,n] += A[m] * B[n]; also short sums (K <= 8):
-// C[m,n] += sum_k A[m,k] B[k,n].  Every C element is read and written once,
-// so the kernel is bound by HBM bandwidth.  C is walked along its
-// smallest-increment mode (the first mode of whichever class holds it), in
-// runs of that mode; the operand that varies along the run is read along the
-// same index (once per k), the other operand is K values per run held in
-// registers.
+// C[m,n] += sum_k A[m,k] B[k,n].  Every C element is read and written once
+// (written only, in the scaled form with beta = 0), so the kernel is bound by
+// HBM bandwidth.  C is walked along its smallest-increment mode (the first
+// mode of whichever class holds it), in chunks of that mode; the operand that
+// varies along the run is loaded once per element into registers and serves
+// a group of 8 indices of the other class, whose operand values (alpha folded
+// in) and C offsets sit in shared memory.
 //
 // SKINNY: one free class of at most 8 indices and a long sum (matrix-vector
 // like).  Each of the (up to 8) short-class outputs of a long-class row is
@@ -24,10 +25,14 @@
 //
 // REDUCE: few output elements and long sums (the "scalar contraction" of
 // Sec. 7 and its neighbours).  Pass 1 splits the flat contracted index
-// space into a fixed number of contiguous ranges, one per CTA, and sums each
-// range with a fixed per-thread stride, warp shuffles and a fixed cross-warp
-// order; pass 2 adds the per-CTA partials in CTA order and accumulates into
-// C.  The result is bitwise reproducible on a given GPU.
+// space into 8 contiguous ranges per SM, one per CTA, and sums each range
+// with a fixed per-thread stride (4 loads of each operand in flight, unit
+// stride specialised), warp shuffles and a fixed cross-warp order; pass 2
+// adds the per-CTA partials in CTA order and applies the epilogue to C.  The
+// result is bitwise reproducible on a given GPU.
+//
+// Every kernel here applies the plan's Scale in its epilogue (C += v, or
+// alpha v + beta C, or alpha v without reading C).
 #include <cuda_runtime.h>
 
 #include <algorithm>
