@@ -4,7 +4,8 @@
 //  * K == 1 (no contracted extent > 1): OUTER streaming kernel;
 //  * at most 32 outputs and K >= 8192: REDUCE streaming kernel;
 //  * K <= 8 with at least 2^16 outputs: OUTER (short sums);
-//  * one free class of at most 8 indices: SKINNY streaming kernel;
+//  * one free class of at most 8 indices and max(M, N) * K >= 2^16: SKINNY;
+//  * bf16 operands with M, N >= 512 and K >= 256: tcgen05 tensor cores;
 //  * otherwise the DENSE tiled kernel with the largest tile that still gives
 //    at least one tile per SM, else the smallest tile plus split-K so the
 //    grid covers the SMs.
