@@ -187,3 +187,25 @@ def test_most_modes_per_class(prefix):
     got, rep = run_gpu(prefix, p, mode="ex")
     assert rep["nm"] == n
     compare(prefix, p, got, oracle_ref(p), exact=True)
+
+
+@pytest.mark.parametrize("prefix", ("d", "z"))
+def test_bilinearity_gpu(prefix):
+    """gett(A1 + A2, B) = gett(A1, B) + gett(A2, B) on integer data, bit for
+    bit, at a size that spans many tiles (a property that holds at any size)."""
+    dtype = np.complex128 if prefix == "z" else np.float64
+    sig = synth.Signature((96, 40, 70), (70, 130, 40), (1, 2), (2, 0), (1, 0, 2))
+    p1 = synth.make_problem(sig, np.random.default_rng(61), dtype, "int", ("padded", "negative", "padded"), "zeros")
+    p2 = p1.copy()
+    rng = np.random.default_rng(62)
+    v = rng.integers(-8, 9, p1.la.numel).astype(np.float64)
+    if prefix == "z":
+        v = v + 1j * rng.integers(-8, 9, p1.la.numel)
+    p2.A = synth.fill(p1.la, v, dtype, np.nan)
+    ps = p1.copy()
+    ps.A = p1.A + p2.A
+    lhs, _ = run_gpu(prefix, ps)
+    r1, _ = run_gpu(prefix, p1)
+    r2, _ = run_gpu(prefix, p2)
+    lg = synth.gather(ps.lc, lhs)
+    assert np.array_equal(lg, synth.gather(p1.lc, r1) + synth.gather(p2.lc, r2))

@@ -434,3 +434,24 @@ def test_planted_mistakes_are_caught(mutant, tmp_path):
         if caught:
             break
     assert caught, f"mutant {mutant} survived the integer-exact einsum pin"
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_bilinearity(seed):
+    """The contraction is linear in A (and in B): gett(A1 + A2, B) = gett(A1, B)
+    + gett(A2, B), exactly on integer data (every partial sum is an exact
+    double), within rounding on uniform data."""
+    for dist in ("int", "uniform"):
+        p1 = synth.thesis_problem("basic", 4000 + seed, np.float64, dist)
+        p2 = p1.copy()
+        rng = np.random.default_rng(4100 + seed)
+        vals = rng.integers(-8, 9, p1.A.shape).astype(np.float64) if dist == "int" else rng.uniform(-1, 1, p1.A.shape)
+        p2.A = np.where(np.isnan(p1.A), np.nan, vals)
+        ps = p1.copy()
+        ps.A = p1.A + p2.A
+        lhs = synth.logical(ps.lc, oracle.gett_problem(ps))
+        rhs = synth.logical(p1.lc, oracle.gett_problem(p1)) + synth.logical(p2.lc, oracle.gett_problem(p2))
+        if dist == "int":
+            assert np.array_equal(lhs, rhs)
+        else:
+            assert np.linalg.norm(lhs - rhs) <= 1e-14 * np.linalg.norm(lhs)
