@@ -57,9 +57,14 @@ struct BatchProb {
     float *partial;   // splits > 1: [splits][M*N] partial tiles
 };
 
+// K offsets of one slice staged in shared memory (at most kStageK entries per
+// operand): a K step then waits for one global round trip (the operands)
+// instead of two (the offset table, then the operands).
+constexpr int kStageK = 1536;
+
 template <class T, int CFG>
 __device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tables, int item, float *smem_f,
-                                         int64_t *smem_i)
+                                         int64_t *smem_i, int64_t *skA, int64_t *skB)
 {
     constexpr BCfg c = kB[CFG];
     const int tile = item / pr.splits, split = item % pr.splits;
@@ -75,6 +80,19 @@ __device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tab
     a.colC = t + 2 * pr.M + pr.N;
     a.kA = t + 2 * pr.M + 2 * pr.N;
     a.kB = t + 2 * pr.M + 2 * pr.N + pr.K;
+    {
+        const int64_t kb = split * pr.kps, n = min(pr.K, kb + pr.kps) - kb;
+        if (n <= kStageK) {
+            // visible to the tile after its first barrier (the row/column
+            // offset staging); the tile indexes kA[k] for k in [kb, kb + n)
+            for (int64_t i = threadIdx.x; i < n; i += BT) {
+                skA[i] = a.kA[kb + i];
+                skB[i] = a.kB[kb + i];
+            }
+            a.kA = skA - kb;
+            a.kB = skB - kb;
+        }
+    }
     a.M = pr.M;
     a.N = pr.N;
     a.m0 = (int64_t)tm * c.bm;
@@ -174,6 +192,7 @@ __global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *
 {
     __shared__ float smem_f[smem_floats()];
     __shared__ int64_t smem_i[smem_ints()];
+    __shared__ int64_t skA[kStageK], skB[kStageK];
     __shared__ unsigned long long s_item;
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
     __syncthreads();
@@ -199,14 +218,14 @@ __global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *
             default: break;
             }
         } else switch (key) {
-        case 0: run_tile<float, 0>(pr, tables, w.y, smem_f, smem_i); break;
-        case 1: run_tile<uint16_t, 0>(pr, tables, w.y, smem_f, smem_i); break;
-        case 2: run_tile<float, 1>(pr, tables, w.y, smem_f, smem_i); break;
-        case 3: run_tile<uint16_t, 1>(pr, tables, w.y, smem_f, smem_i); break;
-        case 4: run_tile<float, 2>(pr, tables, w.y, smem_f, smem_i); break;
-        case 5: run_tile<uint16_t, 2>(pr, tables, w.y, smem_f, smem_i); break;
-        case 6: run_tile<float, 3>(pr, tables, w.y, smem_f, smem_i); break;
-        case 7: run_tile<uint16_t, 3>(pr, tables, w.y, smem_f, smem_i); break;
+        case 0: run_tile<float, 0>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
+        case 1: run_tile<uint16_t, 0>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
+        case 2: run_tile<float, 1>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
+        case 3: run_tile<uint16_t, 1>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
+        case 4: run_tile<float, 2>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
+        case 5: run_tile<uint16_t, 2>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
+        case 6: run_tile<float, 3>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
+        case 7: run_tile<uint16_t, 3>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
         default: break;
         }
         __syncthreads();  // the tile's shared memory and s_item are free again
@@ -436,8 +455,12 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
     const int ctas = sms * (o.ctas_per_sm > 0 ? o.ctas_per_sm : kCtasPerSm);
 
     // K slices: a tile whose work is far above the average share of a CTA is
-    // split along K so the longest work item stays short (tail effects);
-    // slices of one tile are added into C in slice order by a second kernel.
+    // split along K so the longest work item stays short (tail effects), and
+    // so is any tile with more than kMaxSteps K steps whatever its area: a
+    // small tile with a long sum is a chain of dependent gathers, so its time
+    // grows with its K steps, not with its flops.  Slices of one tile are
+    // added into C in slice order by a second kernel.
+    constexpr int64_t kMaxSteps = 96, kMaxSplits = 512;  // kMaxSteps * BK <= kStageK
     double total_cost = 0;
     for (const BatchProb &pr : hp)
         total_cost += (double)pr.tiles_m * pr.tiles_n * kB[pr.cfg].bm * kB[pr.cfg].bn * (double)pr.K;
@@ -448,8 +471,9 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
         BatchProb &pr = hp[j];
         const int bk = kB[pr.cfg].bk;
         const double tile_cost = (double)kB[pr.cfg].bm * kB[pr.cfg].bn * (double)pr.K;
-        int64_t S = (int64_t)std::ceil(tile_cost / target);
-        S = std::min<int64_t>(S, 64);
+        const int64_t steps = (pr.K + bk - 1) / bk;
+        int64_t S = std::max<int64_t>((int64_t)std::ceil(tile_cost / target), (steps + kMaxSteps - 1) / kMaxSteps);
+        S = std::min<int64_t>(S, kMaxSplits);
         S = std::min<int64_t>(S, std::max<int64_t>(1, pr.K / 128));
         if (S < 1) S = 1;
         int64_t kps = (pr.K + S - 1) / S;
