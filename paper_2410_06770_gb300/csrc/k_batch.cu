@@ -55,7 +55,20 @@ struct BatchProb {
     int splits;       // K slices (1: the tile is added into C directly)
     int64_t kps;      // K per slice (multiple of the tile's BK)
     float *partial;   // splits > 1: [splits][M*N] partial tiles
+    int tpi;          // tiles per work item (short sums: several; else 1)
 };
+
+// A short-sum problem (K <= 8, one slice) takes its outputs straight from
+// gathered loads; several of its tiles form one work item so that a few
+// tens of thousands of outputs share the item's fixed latency.
+__host__ __device__ inline bool batch_direct(const BatchProb &pr) { return pr.K <= 8 && pr.splits == 1; }
+
+// work items of a problem: tile runs (short sums) or tiles x K slices
+inline int batch_items(const BatchProb &pr)
+{
+    const int nt = pr.tiles_m * pr.tiles_n;
+    return batch_direct(pr) ? (nt + pr.tpi - 1) / pr.tpi : nt * pr.splits;
+}
 
 // K offsets of one slice staged in shared memory (at most kStageK entries per
 // operand): a K step then waits for one global round trip (the operands)
@@ -205,17 +218,20 @@ __global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *
         const uint2 w = work[it % (unsigned long long)wrap];
         const BatchProb pr = probs[w.x];
         const int key = pr.cfg * 2 + pr.dtype;
-        if (pr.K <= 8 && pr.splits == 1) {
-            switch (key) {
-            case 0: run_direct<float, 0>(pr, tables, w.y); break;
-            case 1: run_direct<uint16_t, 0>(pr, tables, w.y); break;
-            case 2: run_direct<float, 1>(pr, tables, w.y); break;
-            case 3: run_direct<uint16_t, 1>(pr, tables, w.y); break;
-            case 4: run_direct<float, 2>(pr, tables, w.y); break;
-            case 5: run_direct<uint16_t, 2>(pr, tables, w.y); break;
-            case 6: run_direct<float, 3>(pr, tables, w.y); break;
-            case 7: run_direct<uint16_t, 3>(pr, tables, w.y); break;
-            default: break;
+        if (batch_direct(pr)) {
+            const int tend = min(pr.tiles_m * pr.tiles_n, ((int)w.y + 1) * pr.tpi);
+            for (int tile = (int)w.y * pr.tpi; tile < tend; ++tile) {
+                switch (key) {
+                case 0: run_direct<float, 0>(pr, tables, tile); break;
+                case 1: run_direct<uint16_t, 0>(pr, tables, tile); break;
+                case 2: run_direct<float, 1>(pr, tables, tile); break;
+                case 3: run_direct<uint16_t, 1>(pr, tables, tile); break;
+                case 4: run_direct<float, 2>(pr, tables, tile); break;
+                case 5: run_direct<uint16_t, 2>(pr, tables, tile); break;
+                case 6: run_direct<float, 3>(pr, tables, tile); break;
+                case 7: run_direct<uint16_t, 3>(pr, tables, tile); break;
+                default: break;
+                }
             }
         } else switch (key) {
         case 0: run_tile<float, 0>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
@@ -482,6 +498,10 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
         if (S > 1 && partial_floats + S * pr.M * pr.N > (int64_t)(1 << 28)) S = 1, kps = pr.K;
         pr.splits = (int)S;
         pr.kps = S > 1 ? kps : pr.K;
+        pr.tpi = 1;
+        if (batch_direct(pr))
+            pr.tpi = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)pr.tiles_m * pr.tiles_n,
+                                                                   32768 / (kB[pr.cfg].bm * kB[pr.cfg].bn)));
         if (S > 1) {
             partial_off[j] = partial_floats;
             partial_floats += S * pr.M * pr.N;
@@ -504,10 +524,10 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
         decode_host(p.k, p.K, t + 2 * p.M + 2 * p.N, t + 2 * p.M + 2 * p.N + p.K);
         b->flops += 2.0 * (double)p.M * (double)p.N * (double)p.K;
         b->config_count[pr.cfg]++;
-        const int nt = pr.tiles_m * pr.tiles_n;
-        for (int tt = 0; tt < nt * pr.splits; ++tt) {
+        const int nitems = batch_items(pr);
+        for (int tt = 0; tt < nitems; ++tt) {
             work.push_back(make_uint2((unsigned)j, (unsigned)tt));
-            cost.push_back((double)kB[pr.cfg].bm * kB[pr.cfg].bn * (double)pr.kps);
+            cost.push_back((double)kB[pr.cfg].bm * kB[pr.cfg].bn * (double)pr.kps * pr.tpi);
         }
     }
     b->prob_start.assign(n, 0);
@@ -523,7 +543,7 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
     {
         int64_t pos = 0;
         for (size_t j = 0; j < hp.size(); ++j) {
-            const int nt = hp[j].tiles_m * hp[j].tiles_n * hp[j].splits;
+            const int nt = batch_items(hp[j]);
             b->prob_start[hp_index[j]] = pos;
             b->prob_count[hp_index[j]] = nt;
             pos += nt;
