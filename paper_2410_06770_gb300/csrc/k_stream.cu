@@ -83,7 +83,6 @@ __global__ void __launch_bounds__(NT) outer_kernel(OuterParams p)
     const T *Y = static_cast<const T *>(p.Y);
     Out *C = static_cast<Out *>(p.C);
     const bool acc_c = p.sc.mode == SCALE_ACC;
-    const int64_t ngroups = (p.ny + OUTER_NY - 1) / OUTER_NY;
     for (int64_t item = blockIdx.x; item < p.items; item += gridDim.x) {
         const int64_t c = item % p.nchunks;
         const int64_t rest = item / p.nchunks;
