@@ -20,6 +20,8 @@
 // so results do not depend on scheduling.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "dense_tile.cuh"
 #include "kernels.h"
@@ -179,6 +181,47 @@ bool dense_config_valid(DType t, int cfg)
 {
     if (cfg < 0 || cfg >= DENSE_NUM_CONFIGS) return false;
     return !(t == DT_C64 && cfg == 0);
+}
+
+namespace {
+
+template <class T>
+int occupancy_of(int cfg)
+{
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (cfg) {
+    case 0:
+        if constexpr (sizeof(T) != 16)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dense_kernel<T, 128, 128, 8, 8, 8>, 256, 0);
+        break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dense_kernel<T, 64, 64, 8, 4, 4>, 256, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dense_kernel<T, 32, 32, 16, 2, 2>, 256, 0); break;
+    default: break;
+    }
+    return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+}  // namespace
+
+int dense_ctas_per_sm(DType t, int cfg)
+{
+    // resident CTAs of each (type, configuration), asked once
+    static int cache[5][DENSE_NUM_CONFIGS] = {};
+    static std::mutex mu;
+    if (!dense_config_valid(t, cfg)) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    int &c = cache[t][cfg];
+    if (c == 0) {
+        switch (t) {
+        case DT_F32: c = occupancy_of<float>(cfg); break;
+        case DT_F64: c = occupancy_of<double>(cfg); break;
+        case DT_C32: c = occupancy_of<cf>(cfg); break;
+        case DT_C64: c = occupancy_of<zd>(cfg); break;
+        case DT_BF16: c = occupancy_of<uint16_t>(cfg); break;
+        }
+    }
+    return c;
 }
 
 void dense_tile_shape(int cfg, int *bm, int *bn, int *bk)

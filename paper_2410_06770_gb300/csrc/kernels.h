@@ -13,6 +13,8 @@ bool dense_config_valid(DType t, int cfg);
 void dense_tile_shape(int cfg, int *bm, int *bn, int *bk);
 size_t dense_workspace_bytes(const Plan &p, DType t, int cfg, int split_k);
 int dense_effective_split(const Plan &p, int cfg, int split_k);
+// CTAs of the configuration resident on one SM (occupancy query, cached).
+int dense_ctas_per_sm(DType t, int cfg);
 cudaError_t launch_dense(const Plan &p, DType t, const void *A, const void *B, void *C, int cfg,
                          int split_k, void *ws, cudaStream_t s);
 

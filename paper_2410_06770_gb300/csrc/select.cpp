@@ -7,14 +7,42 @@
 //  * one free class of at most 8 indices and max(M, N) * K >= 2^16: SKINNY;
 //  * bf16 operands with M, N >= 512 and K >= 256: tcgen05 tensor cores;
 //  * otherwise the DENSE tiled kernel with the largest tile that still gives
-//    at least one tile per SM, else the smallest tile plus split-K so the
-//    grid covers the SMs.
+//    at least one tile per SM (split along K when that fills the last wave
+//    of tiles), else the smallest tile plus split-K so the grid covers the
+//    SMs.
 #include <algorithm>
 
 #include "kernels.h"
 #include "select.h"
 
 namespace gett {
+
+namespace {
+
+// K slices that fill the last wave of a large tile grid: 1 when the tiles
+// already fill their waves to 98 %, else the smallest S <= 32 whose tiles x S
+// fill them to 99 %, with slices of at least 512 and at most 4 GB of partial
+// tiles (1 if none qualifies).  The slices are added in order by the split-K
+// reduce, so the result stays deterministic.
+int balance_split(const Plan &p, DType t, int cfg, int64_t tiles, int num_sms)
+{
+    const int64_t slots = (int64_t)num_sms * dense_ctas_per_sm(t, cfg);
+    auto fill = [&](int64_t units) {
+        const int64_t waves = (units + slots - 1) / slots;
+        return (double)units / (double)(waves * slots);
+    };
+    if (fill(tiles) >= 0.98) return 1;
+    const size_t acc = (t == DT_C64) ? 16 : ((t == DT_F64 || t == DT_C32) ? 8 : 4);
+    for (int S = 2; S <= 32; ++S) {
+        const int Se = dense_effective_split(p, cfg, S);
+        if (Se != S || p.K / S < 512) continue;
+        if ((double)acc * S * (double)p.M * (double)p.N > 4e9) break;
+        if (fill(tiles * S) >= 0.99) return S;
+    }
+    return 1;
+}
+
+}  // namespace
 
 Choice heuristic_choice(const Plan &p, DType t, int num_sms)
 {
@@ -57,7 +85,7 @@ Choice heuristic_choice(const Plan &p, DType t, int num_sms)
         int64_t tiles = ((p.M + bm - 1) / bm) * ((p.N + bn - 1) / bn);
         if (tiles >= num_sms) {
             c.config = cfg;
-            c.split_k = 1;
+            c.split_k = balance_split(p, t, cfg, tiles, num_sms);
             return c;
         }
     }
