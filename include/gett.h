@@ -161,7 +161,7 @@ typedef enum gett_algo {
 typedef enum gett_family {
     GETT_FAMILY_AUTO = 0,
     GETT_FAMILY_NOOP = 1,     /* empty output or empty sum                 */
-    GETT_FAMILY_DENSE = 2,    /* tiled GETT on CUDA cores / DMMA           */
+    GETT_FAMILY_DENSE = 2,    /* tiled GETT on CUDA cores (FMA)            */
     GETT_FAMILY_OUTER = 3,    /* streaming: no contracted extent > 1       */
     GETT_FAMILY_REDUCE = 4,   /* streaming: few outputs, long sums         */
     GETT_FAMILY_SKINNY = 5,   /* streaming: a free extent <= 8             */
