@@ -4,8 +4,8 @@ Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
 legs may import this package.  The CUDA library never calls it; the two share
 no code.
 
-`gett()` runs Alg. 1 of the thesis (Sec. 6) in plain C (gett_oracle.c) on
-numpy buffers.  Precisions:
+`gett_raw()` (and `gett_problem()` on a synth.Problem) runs Alg. 1 of the
+thesis (Sec. 6) in plain C (gett_oracle.c) on numpy buffers.  Precisions:
   'f64'    -- products and sums in double, each product added to C in turn
               (exactly the loop of Alg. 1);
   'ld'     -- the same loop accumulated in long double, rounded once;

@@ -4,7 +4,8 @@ Network: x -> relu(W1 x + b1) -> relu(W2 h1 + b2) -> W3 h2 + b3.
 Loss: sum(mask * (y - t)^2) / sum(mask).  Parameters are one flat vector in
 the layout W1[h][f], b1[h], W2[h][h], b2[h], W3[o][h], b3[o].  Written from
 the definitions (chain rule by hand); pinned by central finite differences in
-tests/test_mlp_cpu.py.
+tests/test_mlp_cpu.py.  The optimiser step is Adam (Kingma and Ba, 2015,
+their Algorithm 1), pinned there by its closed forms and by torch.optim.Adam.
 """
 import numpy as np
 
@@ -58,3 +59,16 @@ def loss_grad(p, X, T, M, nfeat, hidden, nout):
     gb1 = dz1.sum(0)
     g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
     return loss, g
+
+
+def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update at step t >= 1 (Kingma and Ba, 2015, Algorithm 1), fp64:
+    moving averages of g and g^2, each divided by its bias correction
+    1 - beta^t, then p <- p - lr * mhat / (sqrt(vhat) + eps).
+    Returns (p, m, v) as new arrays."""
+    p, g, m, v = (np.asarray(a, dtype=np.float64) for a in (p, g, m, v))
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v

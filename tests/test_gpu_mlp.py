@@ -40,6 +40,29 @@ def test_gradients_match_reference(n):
     assert np.max(np.abs(g - rg)) <= 1e-4 * max(1e-6, np.max(np.abs(rg)))
 
 
+def test_adam_steps_match_reference():
+    """Three Adam steps of gett_mlp_fit (one sample, so the minibatch order
+    cannot change the gradient) against the fp64 Adam step fed the same GPU
+    gradient: parameters within fp32 rounding of the update, and the reported
+    loss that of the parameters before the step."""
+    m = gb.MLP(NF, H, NO, seed=9)
+    X, T, M = data(1, 11)
+    p = m.get_params().astype(np.float64)
+    mom = np.zeros_like(p)
+    vel = np.zeros_like(p)
+    lr = 1e-3
+    for t in range(1, 4):
+        loss, g = m.loss_grad(X, T, M)
+        fit_loss = m.fit(X, T, M, epochs=1, batch=1, lr=lr, seed=t)
+        assert fit_loss == loss
+        p, mom, vel = mlp_oracle.adam_step(p, g.astype(np.float64), mom, vel, t, lr)
+        got = m.get_params().astype(np.float64)
+        # fp32 rounding of p at each step, and the fp32 betas and bias
+        # corrections (relative 1.3e-5 on 1 - beta2) on an update of at most
+        # about 3 lr
+        assert np.all(np.abs(got - p) <= 4 * t * 2.0 ** -24 * np.abs(p) + 1e-4 * t * lr)
+
+
 def test_training_reduces_loss_and_is_deterministic():
     X, T, M = data(2000, 5)
     losses = []
