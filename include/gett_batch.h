@@ -56,7 +56,10 @@ typedef struct gett_batch_options {
     int select;               /* gett_batch_select                          */
     int config;               /* for SELECT_FIXED                           */
     const int *configs;       /* for SELECT_TABLE: n entries (-1 = heuristic) */
-    int ctas_per_sm;          /* persistent CTAs per SM (0 = 2)             */
+    int ctas_per_sm;          /* persistent CTAs per SM (0 = 4); 1-2, 3 and
+                                 4 use kernels compiled for 2, 3 and 4
+                                 resident CTAs (128, 80, 64 registers a
+                                 thread), more than 4 the 4 one            */
 } gett_batch_options;
 
 typedef struct gett_batch gett_batch;

@@ -41,7 +41,12 @@ struct BCfg {
 // CTAs fit on an SM without spills: the gathers are latency bound and need
 // warps in flight).
 constexpr BCfg kB[NCFG] = {{64, 64, 16, 4, 4}, {32, 64, 16, 2, 4}, {32, 32, 16, 2, 2}, {64, 32, 16, 4, 2}};
-constexpr int kCtasPerSm = 2;
+// Resident CTAs per SM: the kernel is compiled for 2, 3 and 4 (register caps
+// 128, 80 and 64 per thread; the lower caps trade spills for warps in
+// flight).  The gathers are latency bound, so warps win: on the 4096-problem
+// workload 2 / 3 / 4 CTAs per SM take 8.74 / 7.97 / 7.37 ms.
+constexpr int kCtasPerSm = 4;
+constexpr int kMaxCtasPerSm = 4;
 
 struct BatchProb {
     const void *A;
@@ -199,9 +204,10 @@ constexpr int smem_ints()
 
 // Work item i is work[i % wrap]; normal launches pass wrap == nwork, the
 // autotuner's throughput mode replicates one problem's items to fill the GPU.
-__global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *__restrict__ probs, const uint2 *__restrict__ work,
-                                                   int64_t nwork, int64_t wrap, const int64_t *__restrict__ tables,
-                                                   unsigned long long *counter)
+template <int CPS>
+__global__ void __launch_bounds__(BT, CPS) batch_kernel(const BatchProb *__restrict__ probs, const uint2 *__restrict__ work,
+                                                       int64_t nwork, int64_t wrap, const int64_t *__restrict__ tables,
+                                                       unsigned long long *counter)
 {
     __shared__ float smem_f[smem_floats()];
     __shared__ int64_t smem_i[smem_ints()];
@@ -249,6 +255,15 @@ __global__ void __launch_bounds__(BT, kCtasPerSm) batch_kernel(const BatchProb *
         __syncthreads();
         it = s_item;
     }
+}
+
+// the instantiation whose register cap lets `cps` CTAs reside on an SM
+void launch_batch_kernel(int cps, int ctas, cudaStream_t s, const BatchProb *probs, const uint2 *work,
+                         int64_t nwork, int64_t wrap, const int64_t *tables, unsigned long long *counter)
+{
+    if (cps >= 4) batch_kernel<4><<<ctas, BT, 0, s>>>(probs, work, nwork, wrap, tables, counter);
+    else if (cps == 3) batch_kernel<3><<<ctas, BT, 0, s>>>(probs, work, nwork, wrap, tables, counter);
+    else batch_kernel<2><<<ctas, BT, 0, s>>>(probs, work, nwork, wrap, tables, counter);
 }
 
 // Adds the K-slice partial tiles of every split problem into C, slices in
@@ -318,6 +333,7 @@ struct gett_batch {
     int config_count[8] = {};
     int fallbacks = 0;
     int ctas = 0;
+    int cps = 4;  // kernel instantiation (resident CTAs per SM it is compiled for)
     gett::BatchProb *d_probs = nullptr;
     uint2 *d_work = nullptr;
     int64_t *d_tables = nullptr;
@@ -468,7 +484,8 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
         set_last_cuda_error(e);
         return GETT_ERR_CUDA;
     }
-    const int ctas = sms * (o.ctas_per_sm > 0 ? o.ctas_per_sm : kCtasPerSm);
+    const int cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : kCtasPerSm;
+    const int ctas = sms * cps;
 
     // K slices: a tile whose work is far above the average share of a CTA is
     // split along K so the longest work item stays short (tail effects), and
@@ -558,6 +575,7 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
     b->nwork = (int64_t)sorted.size();
 
     b->ctas = ctas;
+    b->cps = std::min(cps, kMaxCtasPerSm);
     e = cudaMalloc(&b->d_partial, sizeof(float) * (size_t)std::max<int64_t>(partial_floats, 1));
     if (e == cudaSuccess)
         for (size_t j = 0; j < hp.size(); ++j)
@@ -591,7 +609,7 @@ static cudaError_t enqueue(gett_batch *b, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess || b->nwork == 0) return e;
     const int ctas = (int)std::min<int64_t>(b->ctas, b->nwork);
-    batch_kernel<<<ctas, BT, 0, s>>>(b->d_probs, b->d_work, b->nwork, b->nwork, b->d_tables, b->d_counter);
+    launch_batch_kernel(b->cps, ctas, s, b->d_probs, b->d_work, b->nwork, b->nwork, b->d_tables, b->d_counter);
     if (b->nreduce > 0)
         batch_reduce_kernel<<<std::min(b->nreduce, b->ctas), 256, 0, s>>>(b->d_probs, b->d_reduce, b->nreduce,
                                                                           b->d_tables);
@@ -656,7 +674,7 @@ extern "C" int gett_batch_profile(gett_batch *b, int reps, int mode, float *ms_o
         const int red = b->reduce_of[i];
         auto one = [&] {
             cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
-            batch_kernel<<<ctas, BT, 0, s>>>(b->d_probs, w, items, cnt, b->d_tables, b->d_counter);
+            launch_batch_kernel(b->cps, ctas, s, b->d_probs, w, items, cnt, b->d_tables, b->d_counter);
             if (red >= 0) batch_reduce_kernel<<<1, 256, 0, s>>>(b->d_probs, b->d_reduce + red, 1, b->d_tables);
         };
         one();  // warm-up

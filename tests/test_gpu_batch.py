@@ -72,6 +72,21 @@ def test_batch_matches_oracle(select, config):
     b.close()
 
 
+@pytest.mark.parametrize("ctas_per_sm", [1, 3, 4, 6])
+def test_batch_residency_variants(ctas_per_sm):
+    """The kernels compiled for 3 and 4 resident CTAs per SM (and grids of 1
+    or 6 CTAs per SM, the last with CTAs that start only when others finish)
+    give the same parity; graph launch."""
+    import torch
+    probs = make_batch_problems(150, 20 + ctas_per_sm)
+    dev, descs = upload_all(probs)
+    b = gb.Batch(descs, ctas_per_sm=ctas_per_sm)
+    b.launch(graph=True)
+    torch.cuda.synchronize()
+    check_all(probs, dev)
+    b.close()
+
+
 def test_batch_graph_replay_accumulates():
     import torch
     probs = make_batch_problems(100, 7)
