@@ -115,7 +115,10 @@ class Batch:
         bad = ctypes.c_int(-1)
         st = L.gett_batch_create(n, arr, ctypes.byref(o), ctypes.byref(h), ctypes.byref(bad))
         if st != 0:
-            raise gett.GettError(st, f"gett_batch_create failed at problem {bad.value}", L.gett_last_error_arg())
+            err = gett.GettError(st, f"gett_batch_create failed at problem {bad.value}", L.gett_last_error_arg(),
+                                 L.gett_last_cuda_error())
+            err.bad_index = bad.value
+            raise err
         self.h = h
         self.n = n
 
