@@ -265,8 +265,6 @@ def traffic_entry(kernel_key: str):
 
 
 def gpu_arm(args, dist: Dist):
-    import ctypes
-
     import torch
 
     from paper_2410_06770_gb300 import build, gett, synth

@@ -3,7 +3,7 @@ learned planner's network (gett_learn.h).  Argument marshalling only."""
 from __future__ import annotations
 
 import ctypes
-from typing import List, Optional, Sequence
+from typing import Sequence
 
 import numpy as np
 

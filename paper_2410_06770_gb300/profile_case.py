@@ -13,8 +13,6 @@ copied once, then the call is made N times (default 2) and synchronised.
 import argparse
 import sys
 
-import numpy as np
-
 
 def main(argv=None):
     ap = argparse.ArgumentParser()

@@ -10,7 +10,6 @@ import pytest
 
 import oracle
 from paper_2410_06770_gb300 import gett, synth
-from tests._einsum_ref import einsum_logical
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 

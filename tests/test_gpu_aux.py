@@ -8,8 +8,7 @@ the normwise tolerance of the type; integer data bit-exact."""
 import numpy as np
 import pytest
 
-import oracle
-from paper_2410_06770_gb300 import gett, synth
+from paper_2410_06770_gb300 import gett
 from tests._aux_ref import reduction_problem, transpose_problem
 from tests._gpu_util import download, problem_for, upload
 from tests.test_gpu_scaled import _nan_c, compare_scaled

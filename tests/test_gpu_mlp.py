@@ -84,7 +84,6 @@ def test_installed_model_drives_host_prediction():
     std = np.ones(NF, dtype=np.float32)
     gb.install_model(p, mean, std, H, NO)
     X, _, _ = data(8, 1)
-    import ctypes
     L = gb._bind()
     ref, _ = mlp_oracle.forward(p, X, NF, H, NO)
     for i in range(8):

@@ -99,7 +99,6 @@ def test_host_inference_matches_reference():
     """gett_learn_predict normalises the raw features with the installed mean
     and std and runs the network on the host: the fp64 reference forward on the
     normalised input, to fp32 rounding."""
-    import ctypes
     gb = _lib()
     L = gb._bind()
     nf, h, no = gb.NFEAT, 16, 4
