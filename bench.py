@@ -564,7 +564,7 @@ def measure_split_forms():
     return out
 
 
-MODEL_PATH = os.path.join(ROOT, "paper_2410_06770_gb300", "models", "planner_mlp.npz")
+MODEL_PATH = os.path.join(ROOT, "paper_2410_06770_gb300", "planner_mlp.npz")
 
 
 def measure_batched(n=4096, ffma_tflops=None):
