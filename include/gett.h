@@ -377,6 +377,21 @@ int gett_version(void);              /* major*10000 + minor*100 + patch      */
  * the CUDA context still usable.  Synchronous. */
 int gett_check_wait_timeout(long long limit_cycles);
 
+/* Parameters of the split-precision form GETT_ALGO_OZAKI_BF16 for a
+ * contraction with K summed terms (the modular form of the Ozaki scheme,
+ * Ozaki, Uchino and Imamura 2025; the thesis names no split method).  Host
+ * only: no device work.  moduli_wanted = 0 picks the smallest count whose
+ * product P leaves at least 50 bits a operand; counts below 2 are raised to
+ * 2.  *L receives the count, *bits the bits each operand's scaled integers
+ * keep (the largest b <= 52 with K * 2^(2b) < P / 2, so the exact sum is
+ * recovered from its residues), and moduli[0..L) (if not NULL, at least
+ * GETT_OZAKI_MAX_MODULI entries) the odd, pairwise coprime moduli, each at
+ * most 255 so that symmetric residues are exact in bfloat16.  A complex
+ * contraction sums 2K real products (pass 2K).  GETT_ERR_ARG: K < 0,
+ * moduli_wanted outside [0, GETT_OZAKI_MAX_MODULI], L or bits NULL. */
+#define GETT_OZAKI_MAX_MODULI 20
+int gett_ozaki_params(int64_t K, int moduli_wanted, int *L, int *bits, int *moduli);
+
 #ifdef __cplusplus
 }
 #endif

@@ -473,3 +473,15 @@ extern "C" int gett_check_wait_timeout(long long limit_cycles)
 }
 
 extern "C" int gett_version(void) { return 100; }
+
+extern "C" int gett_ozaki_params(int64_t K, int moduli_wanted, int *L, int *bits, int *moduli)
+{
+    static_assert(GETT_OZAKI_MAX_MODULI == gett::OZ_MAX_L, "modulus table size");
+    if (K < 0 || moduli_wanted < 0 || moduli_wanted > GETT_OZAKI_MAX_MODULI || !L || !bits) return GETT_ERR_ARG;
+    const int l = gett::ozaki_moduli_for(K, moduli_wanted);
+    *L = l;
+    *bits = gett::ozaki_bits_for(K, l);
+    if (moduli)
+        for (int i = 0; i < l; ++i) moduli[i] = gett::kOzModuli[i];
+    return GETT_OK;
+}

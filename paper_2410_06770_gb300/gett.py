@@ -113,6 +113,8 @@ def lib():
     L.gett_status_string.restype = ctypes.c_char_p
     L.gett_device_status.restype = ctypes.c_int
     L.gett_version.restype = ctypes.c_int
+    L.gett_ozaki_params.argtypes = [ctypes.c_int64, ctypes.c_int, _ip, _ip, _ip]
+    L.gett_ozaki_params.restype = ctypes.c_int
     L.gett_options_init.argtypes = [ctypes.POINTER(Options)]
     L.gett_options_init.restype = None
     _lib = L
@@ -213,6 +215,16 @@ def plan_describe(RANKA, EXTA, INCA, RANKB, EXTB, INCB, CONTS, CONTA, CONTB, PER
                               int(CONTS), _i32(CONTA), _i32(CONTB), _i32(PERM), _i64(INCC),
                               ctypes.byref(info))
     return st, (info.as_dict() if st == GETT_OK else None)
+
+
+def ozaki_params(K: int, moduli: int = 0):
+    """gett_ozaki_params: (count, bits a operand, moduli) of the split form
+    for K summed terms.  Host only."""
+    L = lib()
+    n, bits = ctypes.c_int(0), ctypes.c_int(0)
+    mods = (ctypes.c_int * 20)()
+    check(L.gett_ozaki_params(int(K), int(moduli), ctypes.byref(n), ctypes.byref(bits), mods))
+    return n.value, bits.value, list(mods[: n.value])
 
 
 def last_error_arg() -> int:
