@@ -405,10 +405,12 @@ cudaError_t launch_residues(const double *src, const int64_t *rowT, const int64_
 }
 
 // n = i / M for 32-bit i through a precomputed multiplier (Granlund and
-// Montgomery's round-up method): the multiplier is 2^32 + mul = ceil(2^(32 +
-// shift) / M) with shift = ceil(log2 M), exact for every i < 2^32 and
-// 1 <= M < 2^31 (the launcher's condition; checked exhaustively near 0, near
-// 2^32 and around every multiple of M for divisors up to 2^31).
+// Montgomery's round-up method, 1994): the multiplier is m = 2^32 + mul =
+// ceil(2^(32 + shift) / M) with shift = ceil(log2 M).  Its excess m M -
+// 2^(32 + shift) is below M <= 2^shift, which is their condition for
+// floor(m i / 2^(32 + shift)) = floor(i / M) at every i < 2^32; shift <= 31
+// keeps 2^(32 + shift) within 64 bits, so M <= 2^31 (the launcher asks for
+// M < 2^31).
 struct Div32 {
     uint32_t d, mul, shift;
 };
