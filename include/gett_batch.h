@@ -13,9 +13,10 @@
  * a CUDA graph captured on first use and replayed afterwards.
  *
  * Ownership: the EXT/INC/CONT/PERM arrays are read during create only; the
- * device pointers A, B, C must stay valid while the handle is launched.  C of
- * different problems must not overlap (checked with the same sufficient
- * test as single calls for each C, and pairwise by address range).
+ * device pointers A, B, C must stay valid while the handle is launched.  Each
+ * C must be injective (the same sufficient test as single calls), and the C
+ * of one problem may overlap neither another problem's C nor any problem's A
+ * or B (address ranges; GETT_ERR_ALIAS).  Operands may be shared.
  * Launches of one handle are stream ordered; concurrent launches of the same
  * handle on different streams race on its work counter.
  */
@@ -86,7 +87,11 @@ int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const int64_t *I
 
 /* Returns GETT_OK or the first failing problem's status; *bad_index (may be
  * NULL) receives that problem's index and gett_last_error_arg() its
- * argument position. */
+ * argument position (1..14 as in gett.h; 0 for an unknown dtype).
+ * GETT_ERR_ARG also for a NULL out, n < 0, SELECT_FIXED with a config
+ * outside [0, gett_batch_num_configs()) or SELECT_TABLE without configs.
+ * Validation touches no device; GETT_ERR_CUDA / GETT_ERR_NOMEM come from
+ * the uploads that follow it. */
 int gett_batch_create(int n, const gett_problem_desc *probs, const gett_batch_options *opt,
                       gett_batch **out, int *bad_index);
 int gett_batch_launch(gett_batch *b, void *stream);
