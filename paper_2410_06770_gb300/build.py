@@ -46,9 +46,12 @@ def _compile(src: str, hdr_mtime: float, verbose: bool) -> str:
     obj = os.path.join(OUT, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_mtime):
         return obj
-    cmd = [nvcc()] + ARCH + COMMON + ["-c", src, "-o", obj + ".tmp"]
+    # per-process temporary: ranks that build at the same time never write
+    # the same file, and each publishes its object with an atomic rename
+    tmp = obj + f".tmp{os.getpid()}"
+    cmd = [nvcc()] + ARCH + COMMON + ["-c", src, "-o", tmp]
     if src.endswith(".cpp"):
-        cmd = [nvcc(), "-x", "cu"] + ARCH + COMMON + ["-c", src, "-o", obj + ".tmp"]
+        cmd = [nvcc(), "-x", "cu"] + ARCH + COMMON + ["-c", src, "-o", tmp]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -56,7 +59,7 @@ def _compile(src: str, hdr_mtime: float, verbose: bool) -> str:
         raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
     if verbose and (r.stderr.strip() or r.stdout.strip()):
         print(r.stdout, r.stderr, flush=True)
-    os.replace(obj + ".tmp", obj)
+    os.replace(tmp, obj)
     return obj
 
 
