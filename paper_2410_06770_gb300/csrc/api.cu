@@ -187,7 +187,9 @@ int run(DType t, const Args &a, const void *A, const void *B, void *C, const get
     if (e == cudaSuccess && sync) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
-        return GETT_ERR_CUDA;
+        // the workspace (offset tables, split-K partials, packed operands,
+        // residue planes) did not fit
+        return e == cudaErrorMemoryAllocation ? GETT_ERR_NOMEM : GETT_ERR_CUDA;
     }
     if (sync && ch.family == GETT_FAMILY_TC) {
         int word = 0;
