@@ -56,7 +56,8 @@
  * overlaps A or B, or C's layout maps two coordinates to the same element
  * (checked by a sufficient test on sorted increments).  GETT_ERR_UNSUPPORTED:
  * more than GETT_MAX_MODES modes of extent > 1 remain in one class after
- * mode fusion.  GETT_ERR_CUDA: a CUDA call failed (gett_last_cuda_error()
+ * mode fusion, or one class (A-free, B-free or contracted modes) counts more
+ * than 2^62 indices (possible only with broadcast, increment-0, modes).  GETT_ERR_CUDA: a CUDA call failed (gett_last_cuda_error()
  * gives the cudaError_t).  GETT_ERR_NOMEM: the call's device workspace
  * (offset tables, split-K partial tiles, packed operands or residue planes,
  * taken from the stream-ordered pool) could not be allocated.  GETT_ERR_TIMEOUT: a device-side wait exceeded its

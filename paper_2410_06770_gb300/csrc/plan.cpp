@@ -85,7 +85,8 @@ int fuse_and_sort(Mode *m, int n, bool sort_by_s1_first)
         for (int i = 0; i < n && !merged; ++i) {
             for (int j = 0; j < n && !merged; ++j) {
                 if (i == j) continue;
-                if (m[j].s0 == m[i].s0 * m[i].ext && m[j].s1 == m[i].s1 * m[i].ext) {
+                if ((__int128)m[j].s0 == (__int128)m[i].s0 * m[i].ext &&
+                    (__int128)m[j].s1 == (__int128)m[i].s1 * m[i].ext) {
                     m[i].ext *= m[j].ext;
                     for (int t = j; t + 1 < n; ++t) m[t] = m[t + 1];
                     --n;
@@ -213,6 +214,18 @@ int make_plan(const Args &a, Plan *p, int *bad_arg)
     nm = squeeze(mm, nm);
     nn_ = squeeze(nn, nn_);
     nk = squeeze(kk, nk);
+    // index counts of the classes: bounded by the spans for modes that move
+    // through memory, but broadcast modes (increment 0 in every tensor that
+    // holds them) are not, so a class may not count more than 2^62 indices
+    auto count_fits = [](const Mode *m, int n) {
+        __int128 P = 1;
+        for (int i = 0; i < n; ++i) {
+            P *= m[i].ext;
+            if (P > ((__int128)1 << 62)) return false;
+        }
+        return true;
+    };
+    if (!count_fits(mm, nm) || !count_fits(nn, nn_) || !count_fits(kk, nk)) return GETT_ERR_UNSUPPORTED;
 
     // (ii) flips: free modes get a positive C increment, contracted modes a
     // non-negative A increment (B's if A's is zero)

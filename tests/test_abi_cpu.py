@@ -301,3 +301,16 @@ def test_rank_limit_as_passed(L):
     assert st == gett.GETT_OK and info["K"] == 5 and info["nm"] == 0
     st, _ = _call(L, RANKA=65, EXTA=(1,) * 65, INCA=(1,) * 65)
     assert st == gett.GETT_ERR_ARG and gett.last_error_arg() == 1
+
+
+@pytest.mark.parametrize("ext,ok", [(1 << 31, True), ((1 << 31) + 1, False), (1 << 40, False)])
+def test_broadcast_index_count_limit(L, ext, ok):
+    """Contracted modes with increment 0 in both operands (broadcast) occupy
+    no memory, so the spans do not bound their index count: two of extent
+    `ext` give K = ext^2, accepted up to 2^62 and GETT_ERR_UNSUPPORTED above,
+    before any device work and with no overflow in the planner."""
+    st, info = gett.plan_describe(2, (ext, ext), (0, 0), 2, (ext, ext), (0, 0), 2, (0, 1), (0, 1), (), ())
+    if ok:
+        assert st == gett.GETT_OK and info["K"] == ext * ext and info["nk"] == 1
+    else:
+        assert st == gett.GETT_ERR_UNSUPPORTED
