@@ -1,7 +1,8 @@
 """Parity at the full workload sizes, in the launch configuration bench.py
 times, on sampled outputs the oracle computes one by one: each sampled output
 element of C is the oracle's contraction of the sub-problem with every free
-index fixed (Alg. 1 for one output position)."""
+index fixed (Alg. 1 for one output position); for the batched workload, whole
+sampled problems of the full batch."""
 import numpy as np
 import pytest
 
@@ -87,3 +88,44 @@ def test_small_split_precision_logu_full():
     ref = synth.gather(p.lc, oracle.gett_problem(p, "ld", nthreads=8))
     g = synth.gather(p.lc, got)
     assert np.linalg.norm(g - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_batched_full_size_sampled():
+    """The batched workload at full size (4096 contractions, seed 7) in the
+    launch the bench times (one graph replay, heuristic tile choice, default
+    residency): 64 sampled problems -- the 16 with the longest sums and 48
+    drawn at random -- against the oracle element by element, within the fp32
+    bound 2 (K+2) 2^-24 (|C0| + sum |A||B|), their C gaps untouched."""
+    import torch
+
+    from paper_2410_06770_gb300 import batch as gb
+    from paper_2410_06770_gb300 import tune
+    from tests._gpu_util import abs_bound
+    probs = tune.draw_problems(4096, 7, 64)
+    bufs = tune.DeviceBuffers(probs, values=True)
+    Ks = [int(np.prod([pr["sig"].exta[m] for m in pr["sig"].conta], dtype=np.int64)) for pr in probs]
+    rng = np.random.default_rng(8)
+    pick = sorted(set(np.argsort(Ks)[-16:].tolist()) | set(rng.choice(len(probs), 48, replace=False).tolist()))
+
+    def host(t, bf16):
+        t = t.cpu()
+        return t.view(torch.int16).numpy().view(np.uint16).copy() if bf16 else t.numpy().copy()
+
+    before = {i: host(bufs.keep[i][2], False) for i in pick}
+    b = gb.Batch(bufs.descs, select="heuristic")
+    b.launch(graph=True)
+    torch.cuda.synchronize()
+    for i in pick:
+        pr = probs[i]
+        bf16 = pr["dtype"] == "bf16"
+        dA, dB, dC = bufs.keep[i]
+        q = synth.Problem(pr["sig"], pr["la"], pr["lb"], pr["lc"], host(dA, bf16), host(dB, bf16), before[i])
+        ref = oracle.gett_problem(q, "f64", nthreads=8)
+        got = host(dC, False)
+        gaps = synth.gap_mask(q.lc)
+        assert np.array_equal(got[gaps], q.C[gaps]), f"problem {i}: C gaps were modified"
+        g = synth.gather(q.lc, got).astype(np.float64)
+        r = synth.gather(q.lc, ref)
+        bound = 2.0 * (Ks[i] + 2) * 2.0 ** -24 * abs_bound(q)
+        assert np.all(np.abs(g - r) <= bound + 1e-30), f"problem {i} ({pr['sig']})"
+    b.close()
