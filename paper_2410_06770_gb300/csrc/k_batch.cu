@@ -19,6 +19,8 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <numeric>
 #include <vector>
 
@@ -376,8 +378,16 @@ extern "C" int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const
     return GETT_OK;
 }
 
-extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const gett_batch_options *opt,
-                                 gett_batch **out, int *bad_index)
+namespace {
+
+// Limits of one batch's host-side planning (checked before allocating):
+// indices per class and offset-table entries over all problems (2^31
+// entries = 16 GB of int64 tables).
+constexpr int64_t kMaxClassIndices = (int64_t)1 << 31;
+constexpr int64_t kMaxTableEntries = (int64_t)1 << 31;
+
+int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_options *opt, gett_batch **out,
+                      int *bad_index)
 {
     if (bad_index) *bad_index = -1;
     if (!out || n < 0 || (n > 0 && !probs)) return GETT_ERR_ARG;
@@ -392,7 +402,7 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
     std::vector<int> hp_index;
     int64_t table_len = 0;
     struct Span {
-        intptr_t lo, hi;
+        __int128 lo, hi;  // byte range; 128-bit so broadcast spans cannot wrap
         int idx;
     };
     std::vector<Span> cspans, inspans;
@@ -414,6 +424,16 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
         }
         const Plan &p = plans[i];
         if (p.empty) continue;
+        // host and device offset tables hold 2 (M + N + K) entries per problem
+        // and a problem's tiles are counted in 32 bits: bound both before any
+        // allocation (a class may count up to 2^62 indices through broadcast
+        // modes, which the address spans do not bound)
+        if (p.M > kMaxClassIndices || p.N > kMaxClassIndices || p.K > kMaxClassIndices ||
+            table_len + 2 * (p.M + p.N + p.K) > kMaxTableEntries) {
+            set_last_error_arg(0);
+            if (bad_index) *bad_index = i;
+            return GETT_ERR_UNSUPPORTED;
+        }
         const size_t esz = d.dtype == GETT_BATCH_F32 ? 4 : 2;
         if (!d.A || !d.B || !d.C) {
             set_last_error_arg(!d.A ? 4 : (!d.B ? 8 : 14));
@@ -421,8 +441,8 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
             return GETT_ERR_ARG;
         }
         auto span = [](const void *ptr, int64_t lo, int64_t hi, size_t e, int idx) {
-            intptr_t b = reinterpret_cast<intptr_t>(ptr);
-            return Span{b + (intptr_t)(lo * (int64_t)e), b + (intptr_t)((hi + 1) * (int64_t)e), idx};
+            const __int128 b = reinterpret_cast<intptr_t>(ptr);
+            return Span{b + (__int128)lo * (int64_t)e, b + ((__int128)hi + 1) * (int64_t)e, idx};
         };
         cspans.push_back(span(d.C, p.c_lo, p.c_hi, 4, i));
         inspans.push_back(span(d.A, p.a_lo, p.a_hi, esz, i));
@@ -445,8 +465,16 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
         b.tab = table_len;
         b.cfg = cfg;
         b.dtype = d.dtype;
-        b.tiles_m = (int)((p.M + kB[cfg].bm - 1) / kB[cfg].bm);
-        b.tiles_n = (int)((p.N + kB[cfg].bn - 1) / kB[cfg].bn);
+        {
+            const int64_t tm = (p.M + kB[cfg].bm - 1) / kB[cfg].bm, tn = (p.N + kB[cfg].bn - 1) / kB[cfg].bn;
+            if (tm * tn > (int64_t)INT32_MAX) {  // M, N <= 2^31 each: the product fits int64
+                set_last_error_arg(0);
+                if (bad_index) *bad_index = i;
+                return GETT_ERR_UNSUPPORTED;
+            }
+            b.tiles_m = (int)tm;
+            b.tiles_n = (int)tn;
+        }
         const int64_t am = first_abs(p.m, p.m.s0), ak = first_abs(p.k, p.k.s0);
         const int64_t bnn = first_abs(p.n, p.n.s0), bk = first_abs(p.k, p.k.s1);
         const int64_t cm = first_abs(p.m, p.m.s1), cn = first_abs(p.n, p.n.s1);
@@ -466,7 +494,7 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
         }
     for (const Span &s : inspans) {
         auto it = std::upper_bound(cspans.begin(), cspans.end(), s.lo,
-                                   [](intptr_t v, const Span &c) { return v < c.lo; });
+                                   [](__int128 v, const Span &c) { return v < c.lo; });
         if (it != cspans.begin() && std::prev(it)->hi > s.lo) {
             if (bad_index) *bad_index = s.idx;
             return GETT_ERR_ALIAS;
@@ -602,6 +630,22 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
     }
     *out = b;
     return GETT_OK;
+}
+
+}  // namespace
+
+// The planning above uses host containers: a failed host allocation maps to
+// GETT_ERR_NOMEM instead of an exception crossing the C boundary.
+extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const gett_batch_options *opt,
+                                 gett_batch **out, int *bad_index)
+{
+    try {
+        return batch_create_impl(n, probs, opt, out, bad_index);
+    } catch (const std::bad_alloc &) {
+        return GETT_ERR_NOMEM;
+    } catch (const std::length_error &) {
+        return GETT_ERR_NOMEM;
+    }
 }
 
 static cudaError_t enqueue(gett_batch *b, cudaStream_t s)

@@ -72,7 +72,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint64_t *empty = full + STAGES;
     uint64_t *accf = empty + STAGES;
     uint64_t *acce = accf + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
+    uint64_t *tdone = acce + 2;  // teardown: the MMAs issued before a give-up have completed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tdone + 1);
 
     constexpr uint32_t NCOLS = 512;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -93,6 +94,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             tc::mbar_init(&accf[b], 1);
             tc::mbar_init(&acce[b], NUM_EPI_WARPS);
         }
+        tc::mbar_init(tdone, 1);
         tc::fence_barrier_init();
     }
     if (warp == 1) tc::tmem_alloc(tmem_slot, NCOLS);
@@ -114,9 +116,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 tc::tma_load_3d(sa + A_BYTES, &tmB, &full[s], kt * BK, tn * BN, z);
             }
             if (kt < nkt) {
-                // gave up: let the copies already issued land before the CTA exits
+                // gave up: let the copies already issued land before the CTA
+                // exits (clock-bounded waits; the error word is already set)
                 for (int j = (kt > STAGES ? kt - STAGES : 0); j < kt; ++j)
-                    tc::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, p.err, tc::ERR_WAIT_FULL);
+                    tc::mbar_drain(&full[j % STAGES], (j / STAGES) & 1);
             }
         }
     } else if (warp == 1) {
@@ -154,6 +157,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
                 if (!ok) break;
                 tc::umma_commit(&accf[buf]);
+            }
+            if (!ok) {
+                // gave up with MMAs possibly still writing TMEM: one more commit
+                // tracks every tcgen05 operation this thread issued; wait for it
+                // (clock-bounded) before the common teardown frees TMEM
+                tc::umma_commit(tdone);
+                tc::mbar_drain(tdone, 0);
             }
         }
     } else {
@@ -213,10 +223,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
             } else {
                 float *C = p.C + (int64_t)z * p.c_slice + p.rowC[m];
+                const bool row_marked = p.flagA && p.flagA[m];
 #pragma unroll
                 for (int i = 0; i < 128; ++i) {
                     const int64_t n = (int64_t)tn * BN + h * 128 + i;
-                    if (n < p.N) {
+                    if (n < p.N && !row_marked && !(p.flagB && p.flagB[n])) {
                         float *dst = C + p.colC[n];
                         if (p.smode == SCALE_ACC) *dst = *dst + res[i];
                         else if (p.smode == SCALE_AX) *dst = p.alpha * res[i];

@@ -81,12 +81,14 @@ int noalloc_device(NoallocDev **out)
     return GETT_OK;
 }
 
+// byte ranges in 128-bit arithmetic: element spans up to 2^62 times 8 bytes
+// do not fit 64 bits
 bool overlap(const void *p, int64_t lo, int64_t hi, const void *q, int64_t qlo, int64_t qhi)
 {
-    const intptr_t a0 = reinterpret_cast<intptr_t>(p) + (intptr_t)(lo * 8);
-    const intptr_t a1 = reinterpret_cast<intptr_t>(p) + (intptr_t)((hi + 1) * 8);
-    const intptr_t b0 = reinterpret_cast<intptr_t>(q) + (intptr_t)(qlo * 8);
-    const intptr_t b1 = reinterpret_cast<intptr_t>(q) + (intptr_t)((qhi + 1) * 8);
+    const __int128 a0 = (__int128)reinterpret_cast<intptr_t>(p) + (__int128)lo * 8;
+    const __int128 a1 = (__int128)reinterpret_cast<intptr_t>(p) + ((__int128)hi + 1) * 8;
+    const __int128 b0 = (__int128)reinterpret_cast<intptr_t>(q) + (__int128)qlo * 8;
+    const __int128 b1 = (__int128)reinterpret_cast<intptr_t>(q) + ((__int128)qhi + 1) * 8;
     return a0 < b1 && b0 < a1;
 }
 
@@ -127,8 +129,12 @@ extern "C" int dgett_noalloc(int RANKA, const int64_t *EXTA, const int64_t *INCA
     if (!C || reinterpret_cast<uintptr_t>(C) % 8) { set_last_error_arg(14); return GETT_ERR_ARG; }
     if (overlap(C, p.c_lo, p.c_hi, A, p.a_lo, p.a_hi) || overlap(C, p.c_lo, p.c_hi, B, p.b_lo, p.b_hi))
         return GETT_ERR_ALIAS;
-    // the offset tables of the three classes must fit the fixed array
-    if (p.M + p.N + p.K > (int64_t)GETT_NOALLOC_MAX_INDEX_SUM) {
+    // the offset tables of the three classes must fit the fixed array; each
+    // class may count up to 2^62 indices (broadcast modes), so the terms are
+    // bounded one by one before they are added (the sum then stays below
+    // 3 * GETT_NOALLOC_MAX_INDEX_SUM)
+    const int64_t lim = (int64_t)GETT_NOALLOC_MAX_INDEX_SUM;
+    if (p.M > lim || p.N > lim || p.K > lim || p.M + p.N + p.K > lim) {
         set_last_error_arg(0);
         return GETT_ERR_UNSUPPORTED;
     }

@@ -72,6 +72,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
     }
 }
 
+// Teardown wait after a give-up: waits for the phase with a clock limit only
+// (the error word is already set, so mbar_wait would return at once).  Used
+// to let TMA copies and tensor-core operations that are already in flight
+// complete before shared memory or TMEM is released.
+constexpr long long kDrainLimitCycles = 200000000LL;  // ~0.1 s
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity, long long limit = kDrainLimitCycles)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+
 // ---- TMA -----------------------------------------------------------------
 __device__ __forceinline__ void tma_load_2d(void *smem_dst, const void *tmap, uint64_t *bar, int x, int y)
 {

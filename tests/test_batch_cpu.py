@@ -139,3 +139,14 @@ def test_selection_options_validated():
     assert rejected(descs, select="fixed", config=gb.num_configs()).status == gett.GETT_ERR_ARG
     assert rejected(descs, select="fixed", config=-1).status == gett.GETT_ERR_ARG
     assert rejected(descs, select="table", configs=None).status == gett.GETT_ERR_ARG
+
+
+def test_broadcast_class_beyond_the_table_limit():
+    """A contracted mode with increment 0 in both operands occupies no memory,
+    so its extent is not bounded by the address spans; a class of 2^40
+    indices would need terabytes of host offset tables.  The batch rejects it
+    with GETT_ERR_UNSUPPORTED and the problem's index, before allocating."""
+    big = 1 << 40
+    descs = [desc(0), desc(1, EXTA=(8, big), INCA=(1, 0), EXTB=(big, 6), INCB=(0, 5))]
+    e = rejected(descs)
+    assert e.status == gett.GETT_ERR_UNSUPPORTED and e.bad_index == 1
