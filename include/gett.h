@@ -171,13 +171,25 @@ typedef enum gett_family {
     GETT_FAMILY_TC = 6        /* tensor-core (tcgen05) GEMM on packed data */
 } gett_family;
 
+/* Conjugation of complex operands (an option of xGEMM-style interfaces; the
+ * thesis's contraction never conjugates, Sec. 5).  conj = 0 is Alg. 1.  With
+ * GETT_CONJ_A the sum uses conj(A[...]) in place of A[...], with GETT_CONJ_B
+ * conj(B[...]); both may be set.  Ignored for the real types (s, d, sb), where
+ * conjugation is the identity.  A conjugated operand is first copied, with
+ * its imaginary parts negated, into workspace in the planned order (M * K or
+ * N * K elements from the stream-ordered pool: GETT_ERR_NOMEM if it does not
+ * fit); the contraction then reads that copy. */
+#define GETT_CONJ_A 1
+#define GETT_CONJ_B 2
+
 typedef struct gett_options {
     int algo;        /* gett_algo                                          */
     int family;      /* gett_family; AUTO lets the selector decide         */
     int config;      /* kernel configuration id within the family; -1 auto */
     int split_k;     /* DENSE: number of K slices (0 = auto, 1 = none)     */
     int moduli;      /* OZAKI_BF16: number of moduli (0 = auto)            */
-    int reserved[3];
+    int conj;        /* GETT_CONJ_A | GETT_CONJ_B (complex types), 0 = none */
+    int reserved[2];
 } gett_options;
 
 typedef struct gett_report {
@@ -189,6 +201,10 @@ typedef struct gett_report {
     int selector;    /* 0 heuristic, 1 tuning table, 2 learned model, 3 forced */
     int64_t M, N, K; /* products of the class extents                      */
     double flops;    /* 2*M*N*K real (8*M*N*K complex)                      */
+    double time_ms;  /* device time of the call's work on `stream` (CUDA   */
+                     /* events around every launch and workspace step of   */
+                     /* the call, read after it completed); 0 when nothing */
+                     /* was launched                                       */
 } gett_report;
 
 void gett_options_init(gett_options *opt);
@@ -265,7 +281,7 @@ int sbgett_scaled(int RANKA, const int64_t *EXTA, const int64_t *INCA, const uin
 
 /* ---------------------------------------------------------------------- */
 /* Transpose and reduction.  The thesis lists both among the operations a  */
-/* full BLAS-like tensor interface would need next (Sec. 8, future work);  */
+/* full BLAS-like tensor interface would need next (Sec. 9, future work);  */
 /* their arguments follow xGETT's conventions (Secs. 5.4-5.7: extents and  */
 /* increments per mode, 0-based mode indices, PERM[p] = output position of */
 /* free mode p, one INCC per output mode, negative increments point at     */

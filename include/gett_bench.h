@@ -22,6 +22,11 @@ typedef struct gett_peaks {
     double ffma_tflops;          /* FP32 FMA on CUDA cores                 */
     double copy_gbs;             /* device-to-device copy, read + write    */
     int sms;
+    double imma_s8_tops;         /* mma.sync s8 -> s32 (INT8 tensor path), */
+                                 /* tera-operations/s                      */
+    double tc_bf16_tflops;       /* tcgen05.mma kind::f16, bf16 operands,  */
+                                 /* 128 x 256 tiles, one CTA per SM        */
+    double tc_e4m3_tflops;       /* tcgen05.mma kind::f8f6f4, e4m3 operands */
 } gett_peaks;
 
 /* Runs the microbenchmarks on the current device (synchronous; allocates

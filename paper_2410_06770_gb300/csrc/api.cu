@@ -67,13 +67,15 @@ size_t out_elem_size(DType t) { return t == DT_BF16 ? 4 : dtype_size(t); }
 size_t in_align(DType t) { return t == DT_C64 ? 16 : (t == DT_C32 ? 8 : dtype_size(t)); }
 size_t out_align(DType t) { return t == DT_BF16 ? 4 : in_align(t); }
 
+// byte ranges in 128-bit arithmetic (spans of broadcast-heavy layouts may
+// exceed 2^63 bytes)
 bool ranges_overlap(const void *p, int64_t lo, int64_t hi, size_t esz, const void *q, int64_t qlo,
                     int64_t qhi, size_t qesz)
 {
-    auto a0 = reinterpret_cast<intptr_t>(p) + (intptr_t)(lo * (int64_t)esz);
-    auto a1 = reinterpret_cast<intptr_t>(p) + (intptr_t)((hi + 1) * (int64_t)esz);
-    auto b0 = reinterpret_cast<intptr_t>(q) + (intptr_t)(qlo * (int64_t)qesz);
-    auto b1 = reinterpret_cast<intptr_t>(q) + (intptr_t)((qhi + 1) * (int64_t)qesz);
+    const __int128 a0 = (__int128)reinterpret_cast<intptr_t>(p) + (__int128)lo * (int64_t)esz;
+    const __int128 a1 = (__int128)reinterpret_cast<intptr_t>(p) + ((__int128)hi + 1) * (int64_t)esz;
+    const __int128 b0 = (__int128)reinterpret_cast<intptr_t>(q) + (__int128)qlo * (int64_t)qesz;
+    const __int128 b1 = (__int128)reinterpret_cast<intptr_t>(q) + ((__int128)qhi + 1) * (int64_t)qesz;
     return a0 < b1 && b0 < a1;
 }
 
@@ -135,6 +137,68 @@ int run_scale_only(DType t, const Plan &p, void *C, cudaStream_t s, bool sync)
     return GETT_OK;
 }
 
+// Conjugated complex operands (gett_options.conj): each is copied, with its
+// imaginary parts negated, into workspace in the planned (row, k) order, and
+// the plan is rewritten to read the copy: rows at unit increment, k at R
+// times the packed increment of its modes.  Only the operand's own class
+// increments change; C's and the other operand's stay.
+void pack_increments(ModeList &rows, ModeList &ks, int k_slot, int64_t R)
+{
+    int64_t st = 1;
+    for (int i = 0; i < rows.n; ++i) {
+        rows.s0[i] = st;
+        st *= rows.ext[i];
+    }
+    st = R;
+    for (int i = 0; i < ks.n; ++i) {
+        (k_slot == 0 ? ks.s0 : ks.s1)[i] = st;
+        st *= ks.ext[i];
+    }
+}
+
+cudaError_t conj_operands(Plan &p, DType t, int conj, const void **A, const void **B, int sms, cudaStream_t s,
+                          void **ws_out)
+{
+    *ws_out = nullptr;
+    const bool ca = (conj & GETT_CONJ_A) != 0, cb = (conj & GETT_CONJ_B) != 0;
+    if (!ca && !cb) return cudaSuccess;
+    const size_t esz = dtype_size(t);
+    auto elems = [](int64_t r, int64_t k) -> __int128 { return (__int128)r * k; };
+    const __int128 na = ca ? elems(p.M, p.K) : 0, nb = cb ? elems(p.N, p.K) : 0;
+    const __int128 tab = (__int128)16 * (p.M + p.N + p.K);
+    const __int128 bytes = tab + 256 + (na + nb) * (__int128)esz + 256;
+    if (bytes > ((__int128)1 << 46)) return cudaErrorMemoryAllocation;  // 64 TB: cannot fit
+    char *w = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&w), (size_t)bytes, s);
+    if (e != cudaSuccess) return e;
+    *ws_out = w;
+    int64_t *rowA = reinterpret_cast<int64_t *>(w);
+    int64_t *rowC = rowA + p.M, *colB = rowC + p.M, *colC = colB + p.N, *kA = colC + p.N, *kB = kA + p.K;
+    size_t off = ((size_t)tab + 255) & ~size_t(255);
+    e = launch_build_tables(p, rowA, rowC, colB, colC, kA, kB, s);
+    if (e != cudaSuccess) return e;
+    const char *Ab = static_cast<const char *>(*A) + p.offA * (int64_t)esz;
+    const char *Bb = static_cast<const char *>(*B) + p.offB * (int64_t)esz;
+    if (ca) {
+        void *dst = w + off;
+        off += (((size_t)na * esz + 255) & ~size_t(255));
+        e = launch_conj_pack(t, Ab, rowA, kA, p.M, p.K, dst, sms, s);
+        if (e != cudaSuccess) return e;
+        pack_increments(p.m, p.k, 0, p.M);
+        p.offA = 0;
+        *A = dst;
+    }
+    if (cb) {
+        void *dst = w + off;
+        e = launch_conj_pack(t, Bb, colB, kB, p.N, p.K, dst, sms, s);
+        if (e != cudaSuccess) return e;
+        pack_increments(p.n, p.k, 1, p.N);
+        p.offB = 0;
+        *B = dst;
+    }
+    return cudaSuccess;
+}
+
 int run(DType t, const Args &a, const void *A, const void *B, void *C, const gett_options *opt,
         gett_report *rep, cudaStream_t s, bool sync, const Scale *scale = nullptr, bool alpha_zero = false)
 {
@@ -163,12 +227,51 @@ int run(DType t, const Args &a, const void *A, const void *B, void *C, const get
         ranges_overlap(C, p.c_lo, p.c_hi, osz, B, p.b_lo, p.b_hi, esz))
         return GETT_ERR_ALIAS;
 
+    if (opt && (opt->conj & ~(GETT_CONJ_A | GETT_CONJ_B))) {
+        set_last_error_arg(0);
+        return GETT_ERR_ARG;
+    }
     DevState *st = nullptr;
     rc = dev_state(&st);
     if (rc != GETT_OK) return rc;
+    const int conj = (opt && (t == DT_C32 || t == DT_C64)) ? opt->conj : 0;
+    // the report's time: events around every launch and workspace step
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (rep && sync) {
+        if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess ||
+            cudaEventRecord(ev[0], s) != cudaSuccess) {
+            if (ev[0]) cudaEventDestroy(ev[0]);
+            if (ev[1]) cudaEventDestroy(ev[1]);
+            ev[0] = ev[1] = nullptr;
+        }
+    }
+    auto finish_timing = [&]() {
+        if (!ev[0]) return;
+        float ms = 0.f;
+        if (cudaEventRecord(ev[1], s) == cudaSuccess && cudaEventSynchronize(ev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess && rep)
+            rep->time_ms = ms;
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        ev[0] = ev[1] = nullptr;
+    };
+    void *conj_ws = nullptr;
+    if (conj) {
+        cudaError_t ce = conj_operands(p, t, conj, &A, &B, st->sms, s, &conj_ws);
+        if (ce != cudaSuccess) {
+            if (conj_ws) cudaFreeAsync(conj_ws, s);
+            finish_timing();
+            set_last_cuda_error(ce);
+            return ce == cudaErrorMemoryAllocation ? GETT_ERR_NOMEM : GETT_ERR_CUDA;
+        }
+    }
     Choice ch;
     rc = choose(p, t, opt, st->sms, &ch);
-    if (rc != GETT_OK) return rc;
+    if (rc != GETT_OK) {
+        if (conj_ws) cudaFreeAsync(conj_ws, s);
+        finish_timing();
+        return rc;
+    }
     if (rep) {
         rep->family = ch.family;
         rep->config = ch.config;
@@ -184,6 +287,11 @@ int run(DType t, const Args &a, const void *A, const void *B, void *C, const get
         rep->flops = (t == DT_C32 || t == DT_C64 ? 8.0 : 2.0) * (double)p.M * (double)p.N * (double)p.K;
     }
     cudaError_t e = run_family(p, t, ch, A, B, C, *st, s);
+    if (conj_ws) {
+        const cudaError_t f = cudaFreeAsync(conj_ws, s);
+        if (e == cudaSuccess) e = f;
+    }
+    finish_timing();
     if (e == cudaSuccess && sync) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
@@ -288,7 +396,7 @@ int getr_pos(int pos)
 
 }  // namespace
 
-// Transpose (Sec. 8 future work): the contraction with a rank-0 B of value 1,
+// Transpose (Sec. 9 future work): the contraction with a rank-0 B of value 1,
 // run by the transpose kernel.
 int run_transpose(DType t, int RANKA, const int64_t *EXTA, const int64_t *INCA, const void *A, const int *PERM,
                   const int64_t *INCC, void *C, const Scale &sc, bool alpha_zero, cudaStream_t s)
@@ -317,7 +425,7 @@ int run_transpose(DType t, int RANKA, const int64_t *EXTA, const int64_t *INCA, 
     return GETT_OK;
 }
 
-// Reduction (Sec. 8 future work): the contraction of A with a B of ones over
+// Reduction (Sec. 9 future work): the contraction of A with a B of ones over
 // the reduced modes (extents EXTA[RED[t]], every increment 0, so B is the one
 // element unit_operand gives); the selector and kernels are the contraction's.
 int run_reduce(DType t, int RANKA, const int64_t *EXTA, const int64_t *INCA, const void *A, int NRED,

@@ -1,6 +1,6 @@
 // k_aux.cu -- the tensor transpose and the unit operand of the tensor
 // reduction (two of the operations the thesis lists as future work for a
-// BLAS-like tensor interface, Sec. 8).
+// BLAS-like tensor interface, Sec. 9).
 //
 // Transpose: C[o permuted by PERM] <- alpha * A[o] + beta * C (or C += A).
 // It is the contraction with a rank-0 B equal to 1, planned the same way (M =
@@ -304,6 +304,41 @@ cudaError_t unit_operand(DType t, const void **out)
     }
     *out = o.p[t];
     return cudaSuccess;
+}
+
+namespace {
+
+// dst[r + R k] = conj(src[rowT[r] + kT[k]]): the operand's used elements in
+// the planned (row, k) order, imaginary parts negated (a sign flip, exact).
+template <class T>
+__global__ void __launch_bounds__(256) conj_pack_kernel(const T *__restrict__ src, const int64_t *__restrict__ rowT,
+                                                        const int64_t *__restrict__ kT, int64_t R, int64_t K,
+                                                        T *__restrict__ dst)
+{
+    const int64_t n = R * K;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i % R, k = i / R;
+        T v = src[rowT[r] + kT[k]];
+        v.im = -v.im;
+        dst[i] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_conj_pack(DType t, const void *src, const int64_t *rowT, const int64_t *kT, int64_t R, int64_t K,
+                             void *dst, int num_sms, cudaStream_t s)
+{
+    const int64_t n = R * K;
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 16));
+    if (t == DT_C32)
+        conj_pack_kernel<cf><<<blocks, 256, 0, s>>>(static_cast<const cf *>(src), rowT, kT, R, K, static_cast<cf *>(dst));
+    else if (t == DT_C64)
+        conj_pack_kernel<zd><<<blocks, 256, 0, s>>>(static_cast<const zd *>(src), rowT, kT, R, K, static_cast<zd *>(dst));
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 }  // namespace gett

@@ -19,6 +19,14 @@
 //     64-bit limbs, one correctly rounded conversion to fp64, scaling by
 //     2^{-(s_m+t_n)} and C[m,n] += value.  When the exact sum fits in 53 bits
 //     (integer data, for instance) the added value is exact.
+// Non-finite inputs.  Alg. 1 forms every product in the operand type, so an
+// Inf or NaN in A[m, :] or B[:, n] reaches C[m, n] as IEEE arithmetic makes
+// it.  The integer form cannot carry them, so the scale scan marks such a row
+// or column (kNonFinite in its maximum); the marked rows and columns get
+// all-zero residues, and the recombination computes every output in a marked
+// row or column by the definition instead (the fp64 sum over k in order,
+// read through the same offset tables), so those outputs propagate Inf and
+// NaN exactly as the plain form does.  Unmarked outputs are unaffected.
 // Moduli: pairwise coprime odd numbers <= 255 (largest first).  The error
 // per element is at most about 2^-ka |A_m|max sum_k |B[k,n]| + 2^-kb
 // sum_k |A[m,k]| |B_n|max (the rounding of A' and B'), far below fp64
@@ -95,10 +103,21 @@ __device__ __forceinline__ int ilog2_bits(uint64_t bits)
     return -1074 + (63 - __clzll((long long)mant));
 }
 
+// Row maximum of a row or column holding an Inf or NaN: above every finite
+// |x| pattern, so atomicMax keeps it.
+constexpr unsigned long long kNonFinite = 1ull << 63;
+
 // shift s such that max * 2^s lies in [2^(k-1), 2^k); 0 for an all-zero row
 __device__ __forceinline__ int shift_for(uint64_t maxbits, int k)
 {
     return maxbits == 0 ? 0 : (k - 1 - ilog2_bits(maxbits));
+}
+
+// the residue kernel's shift: a marked row gets one that rounds every value
+// to zero (scaled_int returns 0 for a shift below -1100)
+__device__ __forceinline__ int residue_shift(uint64_t maxbits, int k)
+{
+    return (maxbits & kNonFinite) ? -4096 : shift_for(maxbits, k);
 }
 
 // round(|x| * 2^s) for |x| * 2^s < 2^53 (bit manipulation, no fp64 math)
@@ -198,7 +217,7 @@ __global__ void __launch_bounds__(PT) oz_maxbits_kernel(const double *__restrict
             if (ROW_FAST) { r = e % TR; k = e / TR; }
             else { k = e % TKP; r = e / TKP; }
             unsigned long long b = tile(buf, r, k) & 0x7FFFFFFFFFFFFFFFull;
-            if ((b >> 52) == 0x7FF) b = 0;  // inf / nan do not set the scale
+            if ((b >> 52) == 0x7FF) b = kNonFinite;  // inf / nan mark the row
             if (ROW_FAST) {
                 mine = b > mine ? b : mine;
                 myrow = r;
@@ -241,12 +260,15 @@ __global__ void __launch_bounds__(256) oz_maxbits_rows_kernel(const double *__re
 #pragma unroll
             for (int u = 0; u < 4; ++u) b[u] = __ldg(x + (k + 8 * u) * sk) & 0x7FFFFFFFFFFFFFFFull;
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if ((b[u] >> 52) != 0x7FF && b[u] > mine) mine = b[u];  // inf / nan do not set the scale
+            for (int u = 0; u < 4; ++u) {
+                const unsigned long long v = (b[u] >> 52) == 0x7FF ? kNonFinite : b[u];  // inf / nan mark the row
+                mine = v > mine ? v : mine;
+            }
         }
         for (; k < k1; k += 8) {
             const unsigned long long b = __ldg(x + k * sk) & 0x7FFFFFFFFFFFFFFFull;
-            if ((b >> 52) != 0x7FF && b > mine) mine = b;
+            const unsigned long long v = (b >> 52) == 0x7FF ? kNonFinite : b;
+            mine = v > mine ? v : mine;
         }
     }
     red[warp][lane] = mine;
@@ -280,7 +302,7 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
     auto issue = [&](int64_t t, int buf) {
         const int64_t r0 = (t / tiles_k) * RTR, k0 = (t % tiles_k) * RTKP;
         if (threadIdx.x < RTR)
-            sshift[buf][threadIdx.x] = r0 + threadIdx.x < rows ? shift_for(maxbits[r0 + threadIdx.x], kbits) : 0;
+            sshift[buf][threadIdx.x] = r0 + threadIdx.x < rows ? residue_shift(maxbits[r0 + threadIdx.x], kbits) : 0;
 #pragma unroll
         for (int j = 0; j < RTR * RTKP / PT; ++j) {
             const int e = threadIdx.x + j * PT;
@@ -430,13 +452,41 @@ __device__ __forceinline__ uint32_t div32(const Div32 &q, uint32_t i)
     return (uint32_t)(t >> q.shift);
 }
 
+// The operands as the residue kernels read them, for the outputs of marked
+// (non-finite) rows and columns: row r of the (real-form) A is
+// A[rowA[r] + kA_r[k]] with kA_r = kA0 for r < split_row and kA1 above (the
+// im-rows of a complex real form), negated for k >= neg_from when r <
+// split_row; column n of B is B[colB[n] + kB[k]].
+struct OzNative {
+    const double *A, *B;
+    const int64_t *rowA, *kA0, *kA1, *colB, *kB;
+    int64_t K, split_row, neg_from;
+};
+
+// C[m, n] of a marked row or column by the definition: the products summed
+// in fp64 in k order, so Inf and NaN propagate as in the plain form.
+__device__ __noinline__ double oz_native_value(const OzNative &nv, int64_t m, int64_t n)
+{
+    const bool lower = m < nv.split_row;
+    const int64_t *kA = lower ? nv.kA0 : nv.kA1;
+    const double *a = nv.A + nv.rowA[m];
+    const double *b = nv.B + nv.colB[n];
+    double s = 0.0;
+    for (int64_t k = 0; k < nv.K; ++k) {
+        const double x = a[kA[k]], y = b[nv.kB[k]];
+        s = fma((lower && k >= nv.neg_from) ? -x : x, y, s);
+    }
+    return s;
+}
+
 template <int L, bool IDX32>
 __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ R, int64_t M, int64_t N,
                                                     const unsigned long long *__restrict__ maxA,
                                                     const unsigned long long *__restrict__ maxB,
                                                     const int64_t *__restrict__ rowC,
                                                     const int64_t *__restrict__ colC, double *__restrict__ C,
-                                                    OzConsts c, int64_t shift_rows, Scale sc, Div32 divM)
+                                                    OzConsts c, int64_t shift_rows, Scale sc, Div32 divM,
+                                                    OzNative nv)
 {
     const int64_t MN = M * N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
@@ -447,6 +497,18 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
         } else {
             m = i % M;
             n = i / M;
+        }
+        // row of the scale: m, or m - shift_rows for the imaginary rows of the
+        // complex real form (M is shift_rows or twice it)
+        const int64_t ms = m >= shift_rows ? m - shift_rows : m;
+        const unsigned long long ma = maxA[ms], mb = maxB[n];
+        if ((ma | mb) & kNonFinite) {
+            const double val = oz_native_value(nv, m, n);
+            double *dst = C + rowC[m] + colC[n];
+            if (sc.mode == SCALE_ACC) *dst = *dst + val;
+            else if (sc.mode == SCALE_AX) *dst = sc.ar * val;
+            else *dst = sc.ar * val + sc.br * *dst;
+            continue;
         }
         // Garner's mixed-radix digits: X = v_0 + p_0 v_1 + p_0 p_1 v_2 + ...,
         // v_a = (r_a - sum_{b<a} v_b (p_0..p_{b-1} mod p_a)) (p_0..p_{a-1})^{-1} mod p_a.
@@ -536,10 +598,7 @@ __global__ void __launch_bounds__(256) oz_crt_kernel(const int8_t *__restrict__ 
             drop = 0;
         }
         const double mag = __ull2double_rn(top);
-        // row of the scale: m, or m - shift_rows for the imaginary rows of the
-        // complex real form (M is shift_rows or twice it)
-        const int64_t ms = m >= shift_rows ? m - shift_rows : m;
-        const int e = drop - (shift_for(maxA[ms], c.ka) + shift_for(maxB[n], c.kb));
+        const int e = drop - (shift_for(ma, c.ka) + shift_for(mb, c.kb));
         // mag * 2^e in two exact power-of-two steps (no overflow of the factors)
         const int e1 = e / 2, e2 = e - e1;
         const double f1 = __longlong_as_double((long long)(e1 + 1023) << 52);
@@ -684,28 +743,30 @@ void oz_setup(int64_t K, int want_L, OzConsts *c)
 template <int L>
 void launch_crt_t(const int8_t *R, int64_t M, int64_t N, const unsigned long long *maxA,
                   const unsigned long long *maxB, const int64_t *rowC, const int64_t *colC, double *C,
-                  const OzConsts &c, int num_sms, cudaStream_t s, int64_t shift_rows, const Scale &sc)
+                  const OzConsts &c, int num_sms, cudaStream_t s, int64_t shift_rows, const Scale &sc,
+                  const OzNative &nv)
 {
     const int64_t MN = M * N;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((MN + 255) / 256, (int64_t)num_sms * 16));
     if (MN < (1LL << 32) && M < (1LL << 31)) {
         // every grid-stride index stays below 2^32 + 2^31: i < MN < 2^32 when it is used
         oz_crt_kernel<L, true><<<blocks, 256, 0, s>>>(R, M, N, maxA, maxB, rowC, colC, C, c, shift_rows, sc,
-                                                       make_div32((uint32_t)M));
+                                                       make_div32((uint32_t)M), nv);
     } else {
         oz_crt_kernel<L, false><<<blocks, 256, 0, s>>>(R, M, N, maxA, maxB, rowC, colC, C, c, shift_rows, sc,
-                                                        Div32{1, 0, 0});
+                                                        Div32{1, 0, 0}, nv);
     }
 }
 
 cudaError_t launch_crt(const int8_t *R, int64_t M, int64_t N, const unsigned long long *maxA,
                        const unsigned long long *maxB, const int64_t *rowC, const int64_t *colC, double *C,
-                       const OzConsts &c, int num_sms, cudaStream_t s, const Scale &sc, int64_t shift_rows = -1)
+                       const OzConsts &c, int num_sms, cudaStream_t s, const Scale &sc, const OzNative &nv,
+                       int64_t shift_rows = -1)
 {
     if (shift_rows <= 0) shift_rows = M;
-#define CASE(L)                                                                           \
-    case L:                                                                               \
-        launch_crt_t<L>(R, M, N, maxA, maxB, rowC, colC, C, c, num_sms, s, shift_rows, sc); \
+#define CASE(L)                                                                               \
+    case L:                                                                                   \
+        launch_crt_t<L>(R, M, N, maxA, maxB, rowC, colC, C, c, num_sms, s, shift_rows, sc, nv); \
         break;
     switch (c.L) {
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
@@ -864,7 +925,8 @@ cudaError_t launch_ozaki(const Plan &pl, int L_req, const void *A, const void *B
     p.R = o.R;
     e = launch_tc_gemm(TC_MODE_MOD, o.RA, o.RB, c.L, p, s);
     if (e != cudaSuccess) return e;
-    return launch_crt(o.R, pl.M, pl.N, o.maxA, o.maxB, o.rowC, o.colC, Cb, c, num_sms, s, pl.sc);
+    const OzNative nv{Ab, Bb, o.rowA, o.kA, o.kA, o.colB, o.kB, pl.K, pl.M, pl.K};
+    return launch_crt(o.R, pl.M, pl.N, o.maxA, o.maxB, o.rowC, o.colC, Cb, c, num_sms, s, pl.sc, nv);
 }
 
 namespace {
@@ -981,15 +1043,18 @@ cudaError_t launch_ozaki_complex(const Plan &pl, int L_req, const void *A, const
     p.R = o.R;
     e = launch_tc_gemm(TC_MODE_MOD, o.RA, o.RB, c.L, p, s);
     if (e != cudaSuccess) return e;
+    // marked rows and columns: re-rows are [Re | -Im] through kAre, im-rows
+    // [Im | Re] through kAim, B is [Re; Im] through kB2
+    const OzNative nv{Ab, Bb, o.rowA2, o.kAre, o.kAim, o.colB2, o.kB2, K2, pl.M, pl.K};
     if (!complex_scale_via_temp(pl.sc))  // real alpha and beta act on each part alone
-        return launch_crt(o.R, M2, pl.N, o.maxA, o.maxB, o.rowC2, o.colC2, Cb, c, num_sms, s, pl.sc, pl.M);
+        return launch_crt(o.R, M2, pl.N, o.maxA, o.maxB, o.rowC2, o.colC2, Cb, c, num_sms, s, pl.sc, nv, pl.M);
     {
         const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((std::max(M2, pl.N) + 255) / 256, 4096));
         iota_kernel<<<blocks, 256, 0, s>>>(o.rowT, M2, 1);
         iota_kernel<<<blocks, 256, 0, s>>>(o.colT, pl.N, M2);
     }
     const Scale store{SCALE_AX, 1.0, 0.0, 0.0, 0.0};
-    e = launch_crt(o.R, M2, pl.N, o.maxA, o.maxB, o.rowT, o.colT, o.T, c, num_sms, s, store, pl.M);
+    e = launch_crt(o.R, M2, pl.N, o.maxA, o.maxB, o.rowT, o.colT, o.T, c, num_sms, s, store, nv, pl.M);
     if (e != cudaSuccess) return e;
     const int64_t MN = pl.M * pl.N;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((MN + 255) / 256, (int64_t)num_sms * 16));

@@ -12,8 +12,17 @@
 //
 // Packing reads a 32 x 64 (row x k) tile through shared memory along
 // whichever index has the unit increment and writes packed rows along k.
+//
+// Values the pieces cannot carry -- Inf, NaN, and finite fp32 values beyond
+// the bf16 range, whose hi piece would round to Inf -- are packed as zeros and
+// their row of A (column of B) is marked.  The GEMM epilogue skips every
+// output in a marked row or column, and a fix-up kernel computes those outputs
+// by the definition (the fp32 products summed in k order, as the plain form
+// does), so Inf and NaN reach C as Alg. 1's arithmetic makes them.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -53,7 +62,8 @@ template <class T>
 __global__ void __launch_bounds__(PT) pack_pieces_kernel(const T *__restrict__ src, const int64_t *__restrict__ rowT,
                                                         const int64_t *__restrict__ kT, int64_t rows, int64_t K,
                                                         int64_t Kb, int row_fast, PieceMap pm,
-                                                        uint16_t *__restrict__ out, int64_t ld)
+                                                        uint16_t *__restrict__ out, int64_t ld,
+                                                        uint32_t *__restrict__ flags, uint32_t *__restrict__ any)
 {
     __shared__ float tile[TR][TKP + 1];
     __shared__ int64_t srow[TR];
@@ -82,8 +92,16 @@ __global__ void __launch_bounds__(PT) pack_pieces_kernel(const T *__restrict__ s
             int e = threadIdx.x + j * PT;
             int k = e % TKP, r = e / TKP;
             if (r0 + r >= rows || k0 + k >= Kb) continue;
-            const float x = tile[r][k];  // zero for k >= K
-            const uint16_t hb = f2bf_bits(x);
+            float x = tile[r][k];  // zero for k >= K
+            uint16_t hb = f2bf_bits(x);
+            if ((hb & 0x7F80u) == 0x7F80u) {
+                // Inf / NaN, or beyond the bf16 range: mark the row, pack zeros
+                // (plain stores of one value: the races are benign)
+                flags[r0 + r] = 1u;
+                *any = 1u;
+                x = 0.f;
+                hb = 0;
+            }
             const float r1 = x - bf_bits2f(hb);
             const uint16_t mb = f2bf_bits(r1);
             const float r2 = r1 - bf_bits2f(mb);
@@ -94,6 +112,39 @@ __global__ void __launch_bounds__(PT) pack_pieces_kernel(const T *__restrict__ s
                 o[b * Kb] = pc == 0 ? hb : (pc == 1 ? mb : lb);
             }
         }
+    }
+}
+
+// Outputs of marked rows of A / columns of B (see above): the products in
+// fp32 summed in k order from zero, then met with C under the call's scale.
+// Returns at once when the packing marked nothing.
+template <class T>
+__global__ void __launch_bounds__(256) tc_nonfinite_fixup_kernel(const T *__restrict__ A, const T *__restrict__ B,
+                                                                 const int64_t *__restrict__ rowA,
+                                                                 const int64_t *__restrict__ colB,
+                                                                 const int64_t *__restrict__ kA,
+                                                                 const int64_t *__restrict__ kB,
+                                                                 const int64_t *__restrict__ rowC,
+                                                                 const int64_t *__restrict__ colC, float *C,
+                                                                 int64_t M, int64_t N, int64_t K,
+                                                                 const uint32_t *__restrict__ flagA,
+                                                                 const uint32_t *__restrict__ flagB,
+                                                                 const uint32_t *__restrict__ any, int smode,
+                                                                 float alpha, float beta)
+{
+    if (*any == 0u) return;
+    const int64_t MN = M * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MN; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i % M, n = i / M;
+        if (!flagA[m] && !flagB[n]) continue;
+        const T *a = A + rowA[m];
+        const T *b = B + colB[n];
+        float acc = 0.f;
+        for (int64_t k = 0; k < K; ++k) acc = fmaf(load_as_float<T>(a + kA[k]), load_as_float<T>(b + kB[k]), acc);
+        float *dst = C + rowC[m] + colC[n];
+        if (smode == SCALE_ACC) *dst = *dst + acc;
+        else if (smode == SCALE_AX) *dst = alpha * acc;
+        else *dst = alpha * acc + beta * *dst;
     }
 }
 
@@ -129,7 +180,7 @@ size_t tc_split_workspace_bytes(const Plan &p, int algo)
     const int64_t Kp = block_len(p.K) * tc_split_blocks(algo);
     const int64_t ld = tc_ld(Kp);
     return a256(sizeof(int64_t) * 2 * (size_t)(p.M + p.N + p.K)) + a256(2 * (size_t)p.M * ld) +
-           a256(2 * (size_t)p.N * ld);
+           a256(2 * (size_t)p.N * ld) + a256(4 * (size_t)(p.M + p.N + 1));
 }
 
 cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, const void *B, void *C, void *ws,
@@ -145,8 +196,16 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
     uint16_t *Ap = reinterpret_cast<uint16_t *>(w);
     w += a256(2 * (size_t)pl.M * ld);
     uint16_t *Bp = reinterpret_cast<uint16_t *>(w);
+    w += a256(2 * (size_t)pl.N * ld);
+    // marks of rows of A and columns of B the pieces cannot carry, and a
+    // word that is nonzero when any is marked
+    uint32_t *flagA = reinterpret_cast<uint32_t *>(w);
+    uint32_t *flagB = flagA + pl.M;
+    uint32_t *any = flagB + pl.N;
 
     cudaError_t e = launch_build_tables(pl, rowA, rowC, colB, colC, kA, kB, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(flagA, 0, 4 * (size_t)(pl.M + pl.N + 1), s);
     if (e != cudaSuccess) return e;
     const size_t esz = dtype_size(t);
     const char *Ab = static_cast<const char *>(A) + pl.offA * (int64_t)esz;
@@ -165,14 +224,14 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
     };
     if (t == DT_F32) {
         pack_pieces_kernel<float><<<blocks_for(pl.M), PT, 0, s>>>((const float *)Ab, rowA, kA, pl.M, pl.K,
-                                                                   Kb, a_row_fast, pa, Ap, ld);
+                                                                   Kb, a_row_fast, pa, Ap, ld, flagA, any);
         pack_pieces_kernel<float><<<blocks_for(pl.N), PT, 0, s>>>((const float *)Bb, colB, kB, pl.N, pl.K,
-                                                                   Kb, b_row_fast, pb, Bp, ld);
+                                                                   Kb, b_row_fast, pb, Bp, ld, flagB, any);
     } else {
         pack_pieces_kernel<uint16_t><<<blocks_for(pl.M), PT, 0, s>>>((const uint16_t *)Ab, rowA, kA, pl.M, pl.K,
-                                                                      Kb, a_row_fast, pa, Ap, ld);
+                                                                      Kb, a_row_fast, pa, Ap, ld, flagA, any);
         pack_pieces_kernel<uint16_t><<<blocks_for(pl.N), PT, 0, s>>>((const uint16_t *)Bb, colB, kB, pl.N, pl.K,
-                                                                      Kb, b_row_fast, pb, Bp, ld);
+                                                                      Kb, b_row_fast, pb, Bp, ld, flagB, any);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -201,7 +260,20 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
     p.smode = pl.sc.mode;
     p.alpha = (float)pl.sc.ar;
     p.beta = (float)pl.sc.br;
-    return launch_tc_gemm(TC_MODE_F32, Ap, Bp, 1, p, s);
+    p.flagA = flagA;
+    p.flagB = flagB;
+    e = launch_tc_gemm(TC_MODE_F32, Ap, Bp, 1, p, s);
+    if (e != cudaSuccess) return e;
+    const int fblocks = (int)std::max<int64_t>(1, std::min<int64_t>((pl.M * pl.N + 255) / 256, (int64_t)num_sms * 8));
+    if (t == DT_F32)
+        tc_nonfinite_fixup_kernel<float><<<fblocks, 256, 0, s>>>((const float *)Ab, (const float *)Bb, rowA, colB, kA,
+                                                                 kB, rowC, colC, Cb, pl.M, pl.N, pl.K, flagA, flagB,
+                                                                 any, p.smode, p.alpha, p.beta);
+    else
+        tc_nonfinite_fixup_kernel<uint16_t><<<fblocks, 256, 0, s>>>((const uint16_t *)Ab, (const uint16_t *)Bb, rowA,
+                                                                    colB, kA, kB, rowC, colC, Cb, pl.M, pl.N, pl.K,
+                                                                    flagA, flagB, any, p.smode, p.alpha, p.beta);
+    return cudaGetLastError();
 }
 
 }  // namespace gett

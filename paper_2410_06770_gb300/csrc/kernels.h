@@ -50,6 +50,10 @@ bool transpose_tiled(const Plan &p);
 cudaError_t launch_transpose(const Plan &p, DType t, const void *A, void *C, int num_sms, cudaStream_t s);
 // Device address of one element of value 1 of type t (the B of a reduction).
 cudaError_t unit_operand(DType t, const void **out);
+// Conjugated copy of a complex operand in planned order: dst[r + R k] =
+// conj(src[rowT[r] + kT[k]]) for r < R, k < K (c and z only).
+cudaError_t launch_conj_pack(DType t, const void *src, const int64_t *rowT, const int64_t *kT, int64_t R, int64_t K,
+                             void *dst, int num_sms, cudaStream_t s);
 
 // ---- tensor-core forms ----
 // s / bf16 inputs: packed bf16 pieces + one tcgen05 GEMM (k_tcpack.cu)

@@ -1,13 +1,18 @@
 // peaks.cu -- microbenchmarks of the arithmetic pipes and HBM the xGETT
 // kernels run on, so roofline fractions can use measured denominators:
 // FP64 FMA (DFMA), FP64 tensor MMA (mma.sync f64, DMMA) in three shapes,
-// FP32 FMA, and an HBM copy.  Each kernel keeps enough independent chains in
-// flight to saturate its pipe; the result is the best of several timed runs.
+// FP32 FMA, INT8 tensor MMA (mma.sync s8, the only INT8 tensor instruction
+// sm_103a offers), the 5th-generation tensor core (tcgen05.mma) with bf16
+// and with e4m3 operands, and an HBM copy.  Each kernel keeps enough
+// independent work in flight to saturate its pipe; the result is the best of
+// several timed runs.  These numbers decide which slice type the split
+// precision form uses.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "gett_bench.h"
+#include "tc_common.cuh"
 
 namespace {
 
@@ -70,6 +75,97 @@ __global__ void dmma_peak_kernel(double *out, int iters)
 #pragma unroll
         for (int i = 0; i < 4; ++i) s += c[j][i];
     if (s == -1.2345) out[threadIdx.x] = s;
+}
+
+// mma.sync s8 -> s32, m16n8k32: four independent accumulators a warp
+__global__ void imma_peak_kernel(int *out, int iters)
+{
+    uint32_t a[4], b[2];
+    int c[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = 0x01010101u * (uint32_t)(threadIdx.x + i);
+    b[0] = 0x01020304u;
+    b[1] = 0x04030201u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c[j][i] = 0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            asm volatile(
+                "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+r"(c[j][0]), "+r"(c[j][1]), "+r"(c[j][2]), "+r"(c[j][3])
+                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s += c[j][i];
+    if (s == 12345) out[threadIdx.x] = s;
+}
+
+// tcgen05.mma issue rate: one CTA per SM, one thread issues `iters` x 4
+// MMAs of 128 x 256 (x 16 bf16 or x 32 e4m3 along K) from two zeroed
+// 128-byte-swizzled shared tiles into one TMEM accumulator, commits and waits
+// (bounded) for completion.  KIND 0: kind::f16 with bf16 operands; KIND 1:
+// kind::f8f6f4 with e4m3 operands.  Both read 32 bytes of every operand row
+// per instruction.
+constexpr int TCP_M = 128, TCP_N = 256;
+constexpr int TCP_A_BYTES = TCP_M * 128, TCP_B_BYTES = TCP_N * 128;
+constexpr int TCP_SMEM = TCP_A_BYTES + TCP_B_BYTES + 1024;
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 1) tc_peak_kernel(int iters, int *err)
+{
+    extern __shared__ uint8_t tcp_raw[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t slot;
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tcp_raw) + 1023) & ~uintptr_t(1023));
+    for (int i = threadIdx.x; i < (TCP_A_BYTES + TCP_B_BYTES) / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(base)[i] = make_uint4(0, 0, 0, 0);
+    // the tensor core reads shared memory through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        gett::tc::mbar_init(&bar, 1);
+        gett::tc::fence_barrier_init();
+    }
+    if (threadIdx.x < 32) gett::tc::tmem_alloc(&slot, TCP_N);
+    __syncthreads();
+    gett::tc::tc_fence_after();
+    const uint32_t tmem = slot;
+    if (threadIdx.x == 0) {
+        const uint64_t ad = gett::tc::smem_desc_sw128(gett::tc::smem_u32(base));
+        const uint64_t bd = gett::tc::smem_desc_sw128(gett::tc::smem_u32(base + TCP_A_BYTES));
+        constexpr uint32_t idesc = KIND == 0 ? gett::tc::idesc_bf16_f32(TCP_M, TCP_N)
+                                             : ((1u << 4) | ((uint32_t)(TCP_N >> 3) << 17) |
+                                                ((uint32_t)(TCP_M >> 4) << 24));  // D f32, A, B e4m3 (0)
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t acc = (it > 0 || j > 0) ? 1u : 0u;
+                if constexpr (KIND == 0) {
+                    gett::tc::umma_bf16(tmem, ad + (uint64_t)(j * 2), bd + (uint64_t)(j * 2), idesc, acc);
+                } else {
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad + (uint64_t)(j * 2)), "l"(bd + (uint64_t)(j * 2)), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+            }
+        }
+        gett::tc::umma_commit(&bar);
+        if (!gett::tc::mbar_wait(&bar, 0, err, gett::tc::ERR_WAIT_ACC_FULL)) gett::tc::mbar_drain(&bar, 0);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        gett::tc::tc_fence_after();
+        gett::tc::tmem_dealloc(tmem, TCP_N);
+    }
 }
 
 __global__ void copy_kernel(const float4 *__restrict__ src, float4 *__restrict__ dst, size_t n)
@@ -136,6 +232,26 @@ extern "C" int gett_measure_peaks(gett_peaks *out, size_t copy_bytes)
     {
         float ms = best_ms([&] { dmma_peak_kernel<2><<<blocks, threads>>>(scratch, dit); }, 5);
         out->dmma_m16n8k8_tflops = 4.0 * dit * warps * (2.0 * 16 * 8 * 8) / (ms * 1e-3) / 1e12;
+    }
+    {
+        float ms = best_ms([&] { imma_peak_kernel<<<blocks, threads>>>((int *)scratch, dit); }, 5);
+        out->imma_s8_tops = 4.0 * dit * warps * (2.0 * 16 * 8 * 32) / (ms * 1e-3) / 1e12;
+    }
+    {
+        // tcgen05: one CTA per SM; a wait that gave up leaves a nonzero word
+        int *err = reinterpret_cast<int *>(scratch) + 2048;
+        cudaMemset(err, 0, sizeof(int));
+        const int tit = 4096;
+        cudaFuncSetAttribute(tc_peak_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCP_SMEM);
+        cudaFuncSetAttribute(tc_peak_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCP_SMEM);
+        const double per_cta = 4.0 * tit * 2.0 * TCP_M * TCP_N;
+        float ms = best_ms([&] { tc_peak_kernel<0><<<sms, 128, TCP_SMEM>>>(tit, err); }, 5);
+        out->tc_bf16_tflops = per_cta * 16 * sms / (ms * 1e-3) / 1e12;
+        ms = best_ms([&] { tc_peak_kernel<1><<<sms, 128, TCP_SMEM>>>(tit, err); }, 5);
+        out->tc_e4m3_tflops = per_cta * 32 * sms / (ms * 1e-3) / 1e12;
+        int word = 0;
+        cudaMemcpy(&word, err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (word) out->tc_bf16_tflops = out->tc_e4m3_tflops = 0;  // a wait gave up: no figure
     }
     cudaFree(scratch);
     out->copy_gbs = 0;

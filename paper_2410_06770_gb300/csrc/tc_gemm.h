@@ -31,6 +31,10 @@ struct TcGemmParams {
     // SCALE_AXPBY writes alpha * D + beta * C (real alpha, beta)
     int smode;
     float alpha, beta;
+    // MODE_F32, optional: rows of A / columns of B that hold a value the
+    // bf16 pieces cannot carry (Inf, NaN, or beyond the bf16 range); the
+    // epilogue leaves their outputs to the non-finite fix-up kernel
+    const uint32_t *flagA, *flagB;
 };
 
 // Row pitch (elements) of a packed operand with K columns: multiple of 8

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgett.so")
 
 GETT_OK, GETT_ERR_ARG, GETT_ERR_ALIAS, GETT_ERR_UNSUPPORTED = 0, -1, -2, -3
 GETT_ERR_CUDA, GETT_ERR_TIMEOUT, GETT_ERR_NOMEM = -4, -5, -6
+GETT_CONJ_A, GETT_CONJ_B = 1, 2
 MAX_MODES = 24
 
 ALGO = {"default": 0, "native": 1, "ozaki_bf16": 2, "bf16x3": 3, "bf16x6": 4}
@@ -35,14 +36,16 @@ class GettError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("family", ctypes.c_int), ("config", ctypes.c_int),
-                ("split_k", ctypes.c_int), ("moduli", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("split_k", ctypes.c_int), ("moduli", ctypes.c_int), ("conj", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class Report(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int), ("config", ctypes.c_int), ("split_k", ctypes.c_int),
                 ("moduli", ctypes.c_int), ("nm", ctypes.c_int), ("nn", ctypes.c_int),
                 ("nk", ctypes.c_int), ("selector", ctypes.c_int), ("M", ctypes.c_int64),
-                ("N", ctypes.c_int64), ("K", ctypes.c_int64), ("flops", ctypes.c_double)]
+                ("N", ctypes.c_int64), ("K", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("time_ms", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -150,7 +153,8 @@ def check(status: int):
     return status
 
 
-def options(algo="default", family="auto", config=-1, split_k=0, moduli=0) -> Options:
+def options(algo="default", family="auto", config=-1, split_k=0, moduli=0, conj=0) -> Options:
+    """gett_options; conj is a GETT_CONJ_A | GETT_CONJ_B mask (complex types)."""
     o = Options()
     lib().gett_options_init(ctypes.byref(o))
     o.algo = ALGO[algo] if isinstance(algo, str) else int(algo)
@@ -158,6 +162,7 @@ def options(algo="default", family="auto", config=-1, split_k=0, moduli=0) -> Op
     o.config = int(config)
     o.split_k = int(split_k)
     o.moduli = int(moduli)
+    o.conj = int(conj)
     return o
 
 

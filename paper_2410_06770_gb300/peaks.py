@@ -7,7 +7,9 @@ from . import gett
 class _Peaks(ctypes.Structure):
     _fields_ = [("dfma_tflops", ctypes.c_double), ("dmma_m8n8k4_tflops", ctypes.c_double),
                 ("dmma_m16n8k4_tflops", ctypes.c_double), ("dmma_m16n8k8_tflops", ctypes.c_double),
-                ("ffma_tflops", ctypes.c_double), ("copy_gbs", ctypes.c_double), ("sms", ctypes.c_int)]
+                ("ffma_tflops", ctypes.c_double), ("copy_gbs", ctypes.c_double), ("sms", ctypes.c_int),
+                ("imma_s8_tops", ctypes.c_double), ("tc_bf16_tflops", ctypes.c_double),
+                ("tc_e4m3_tflops", ctypes.c_double)]
 
 
 def measure(copy_bytes: int = 1 << 30) -> dict:
