@@ -183,11 +183,13 @@ def bytes_of(p) -> float:
 # ---------------------------------------------------------------------------
 # the CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample(p, seconds: float):
+def oracle_sample(p, seconds: float, want_values=False):
     """Time the oracle on a sample of output elements of `p`: the sub-problem
     that keeps A whole and restricts B (hence C) to its first j columns of the
     last B free mode (or, for a full outer product, the first columns).
-    Returns (tflops, cores, description)."""
+    Returns (tflops, cores, description, seconds); with want_values also the
+    sampled outputs' buffer positions in C (the sub-problem shares C's
+    layout) and the oracle's values there, summed from zero."""
     import oracle
     cores = os.cpu_count() or 1
     s = p.sig
@@ -215,6 +217,7 @@ def oracle_sample(p, seconds: float):
         dt = time.perf_counter() - t0
         assert rc == 0
         K = int(np.prod([s.exta[m] for m in s.conta], dtype=np.int64)) if s.conta else 1
+        sub.last = (extc, C)
         return dt, 2.0 * n * K, n
 
     # calibrate on one column (bounded further by shrinking A's sample if needed)
@@ -227,7 +230,12 @@ def oracle_sample(p, seconds: float):
     desc = (f"{n} of {int(np.prod(s.extc(), dtype=np.int64))} output elements "
             f"(first {ncols} of {s.extb[lastb]} values of B's last free mode), full sums, "
             f"{f / 1e9:.1f} GFLOP in {dt:.1f} s")
-    return f / dt / 1e12, cores, desc, dt
+    if not want_values:
+        return f / dt / 1e12, cores, desc, dt
+    from paper_2410_06770_gb300 import synth
+    extc, C = sub.last
+    pos = synth._positions_f(extc, p.lc.inc, p.lc.off)
+    return f / dt / 1e12, cores, desc, dt, pos, C[pos]
 
 
 # ---------------------------------------------------------------------------
@@ -363,19 +371,78 @@ def gpu_arm(args, dist: Dist):
 
     if not args.no_e2e:
         result["e2e"] = e2e_measure(p, flops, call_host=None, dA=dA, dB=dB, dC=dC, a=a, stream=stream,
-                                    steps=max(2, min(args.steps, 3)))
+                                    steps=args.steps)
+    held = {}
     if not args.no_forms and dist.world == 1:
         del dA, dB, dC
         torch.cuda.empty_cache()
         result["forms"] = measure_forms(args.workload)
-        result["forms"].update(measure_split_forms())
+        result["forms"].update(measure_split_forms(held))
         result["forms"].update(measure_streaming_forms(pk.get("dfma_tflops")))
         result["forms"]["batched"] = measure_batched(ffma_tflops=pk.get("ffma_tflops"))
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
-        v, cores, desc, dt = oracle_sample(p, args.cpu_seconds)
-        result["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                                  "sample": desc}
+        cpu, split = cpu_baseline_leg(p, args.cpu_seconds, held, value)
+        result["cpu_baseline"] = cpu
+        if split:
+            # last key of the line: the driver keeps the line's tail
+            result["split"] = split
     return result
+
+
+def _r(x, d=4):
+    """Round to d significant digits (keeps the JSON line short)."""
+    return float(f"{x:.{d}g}") if x is not None else None
+
+
+def cpu_baseline_leg(p, seconds, held, plain_tflops):
+    """The oracle on the host cores: timed on a bounded sample of the CC
+    workload (the cpu_baseline), and its sampled outputs -- plus the oracle
+    on the small log-uniform workload and on a one-column sample of the fp32
+    CC inputs -- serve as the reference of every precision form's normwise
+    error.  Returns (cpu_baseline dict, compact split summary or None)."""
+    import oracle
+    v, cores, desc, dt, pos, ref = oracle_sample(p, seconds, want_values=True)
+    cpu = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc}
+    if "cc_fp64" not in held:
+        return cpu, None
+
+    def rel(x, r):
+        nr = float(np.linalg.norm(r))
+        return float(np.linalg.norm(np.asarray(x, dtype=np.float64) - r) / (nr if nr else 1.0))
+
+    cc = held["cc_fp64"]
+    ms = held["cc_fp64_ms"]
+    f = flops_of(p)
+    split = {
+        "cc_fp64": {"algo": "ozaki_bf16", "moduli": held["cc_fp64_moduli"], "ms": _r(ms),
+                    "tflops_eff": _r(f / (ms * 1e-3) / 1e12),
+                    "vs_plain": _r(f / (ms * 1e-3) / 1e12 / plain_tflops),
+                    "err": _r(rel(cc["ozaki_bf16"][pos], ref), 3),
+                    "plain_err": _r(rel(cc["native"][pos], ref), 3), "tol": 1e-13},
+        "err_ref": "normwise vs the FP64 oracle over the cpu_baseline sample",
+    }
+    # SGETT forms on the CC workload in fp32: oracle of the fp32 values on one
+    # column of B's last free mode
+    if "cc_fp32" in held:
+        p32 = held["cc_fp32"]["problem"]
+        q = p32.copy()
+        q.A, q.B, q.C = p32.A.astype(np.float64), p32.B.astype(np.float64), p32.C.astype(np.float64)
+        _, _, desc32, _, pos32, ref32 = oracle_sample(q, 1e-9, want_values=True)
+        split["cc_fp32"] = {a: {"ms": _r(e["ms"]), "tflops": _r(e["tflops"]),
+                                "err": _r(rel(held["cc_fp32"][a][pos32], ref32), 3)}
+                            for a, e in held["cc_fp32_timing"].items()}
+        split["cc_fp32_tol"] = 1e-5
+    # every form on the small log-uniform workload, all outputs
+    if "small" in held:
+        from paper_2410_06770_gb300 import synth
+        errs = {}
+        for key, (q, got) in held["small"].items():
+            q64 = q.copy()
+            q64.A, q64.B, q64.C = q.A.astype(np.float64), q.B.astype(np.float64), q.C.astype(np.float64)
+            r = synth.gather(q64.lc, oracle.gett_problem(q64, "f64", nthreads=cores))
+            errs[key] = _r(rel(synth.gather(q.lc, got), r), 3)
+        split["small_logu_err"] = errs
+    return cpu, split
 
 
 def e2e_measure(p, flops, call_host, dA, dB, dC, a, stream, steps):
@@ -455,11 +522,12 @@ def time_calls(call, reps, warm=2):
     return min(times), statistics.median(times)
 
 
-def measure_split_forms():
-    """Split-precision DGETT on the CC workload and every precision form on the
-    small workload with log-uniform magnitudes.  Accuracy is measured over
-    every output against the native FP64 path on the GPU (whose own parity
-    with the oracle the tests check), so the bench itself runs no oracle."""
+def measure_split_forms(held):
+    """Split-precision DGETT on the CC workload, SGETT's forms on the CC
+    workload in fp32, and every precision form on the small workload with
+    log-uniform magnitudes.  Timing only, plus each form's difference from
+    the native FP64 path on the GPU; the results are kept in `held` so the
+    CPU-baseline leg can state every form's error against the oracle."""
     import torch
     from paper_2410_06770_gb300 import gett, synth
     out = {}
@@ -487,9 +555,10 @@ def measure_split_forms():
     dA = torch.from_numpy(p.A).cuda()
     dB = torch.from_numpy(p.B).cuda()
     C0 = torch.from_numpy(p.C).cuda()
-    ref, _ = run("d", p, "native", dA, dB, C0)
+    ref, rep_plain = run("d", p, "native", dA, dB, C0)
     dC, rep = run("d", p, "ozaki_bf16", dA, dB, C0)
     diff = rel(dC, ref)
+    held["cc_fp64"] = {"native": ref.cpu().numpy(), "ozaki_bf16": dC.cpu().numpy()}
     del dC, ref
 
     def call():
@@ -500,6 +569,8 @@ def measure_split_forms():
     best, med = time_calls(call, 5)
     f = flops_of(p)
     L = rep["moduli"]
+    held["cc_fp64_ms"] = best
+    held["cc_fp64_moduli"] = L
     out["cc_split_fp64"] = {
         "workload": desc, "algo": "ozaki_bf16 (modular, bf16 tcgen05)", "moduli": L,
         "ms": best, "ms_median": med, "tflops_effective": f / (best * 1e-3) / 1e12,
@@ -507,9 +578,37 @@ def measure_split_forms():
         "normwise_diff_vs_native_fp64": diff, "compared": "all 16.8M outputs against the native FP64 call on the GPU"}
     del dA, dB, C0
     torch.cuda.empty_cache()
+    # SGETT at scale: the CC contraction in fp32, native FFMA against the bf16
+    # split forms on tcgen05 (C from zero for each call)
+    p32 = p.copy()
+    p32.A, p32.B, p32.C = p.A.astype(np.float32), p.B.astype(np.float32), p.C.astype(np.float32)
+    dA, dB = torch.from_numpy(p32.A).cuda(), torch.from_numpy(p32.B).cuda()
+    C0 = torch.from_numpy(p32.C).cuda()
+    held["cc_fp32"] = {"problem": p32}
+    sf = {}
+    for algo in ("native", "bf16x3", "bf16x6"):
+        got, rep32 = run("s", p32, algo, dA, dB, C0)
+        held["cc_fp32"][algo] = got.cpu().numpy()
+        del got
+
+        dCt = C0.clone()  # the timed calls accumulate here, not into C0
+
+        def c32():
+            return gett.xgett("s", len(p32.sig.exta), p32.sig.exta, p32.la.inc, dA, len(p32.sig.extb),
+                              p32.sig.extb, p32.lb.inc, dB, p32.sig.conts, p32.sig.conta, p32.sig.contb,
+                              p32.sig.perm, p32.lc.inc, dCt, mode="ex", opts=gett.options(algo=algo),
+                              stream=stream.cuda_stream)
+        b32, m32 = time_calls(c32, 5)
+        del dCt
+        sf[algo] = {"ms": b32, "ms_median": m32, "tflops": f / (b32 * 1e-3) / 1e12, "family": rep32["family_name"]}
+        held.setdefault("cc_fp32_timing", {})[algo] = sf[algo]
+    out["cc_sgett_forms"] = {"workload": desc + ", fp32", "forms": sf}
+    del dA, dB, C0
+    torch.cuda.empty_cache()
     # small workload, log-uniform magnitudes: every form against native FP64 on
     # the same (for s: fp32-rounded) inputs
     ps = synth.cfg_small_dgett(dist="logu")
+    held["small"] = {}
     forms = {}
     for prefix, algo in (("d", "native"), ("d", "ozaki_bf16"), ("s", "native"), ("s", "bf16x3"), ("s", "bf16x6")):
         q = ps.copy()
@@ -526,6 +625,7 @@ def measure_split_forms():
         got, _ = run(prefix, q, algo, dA, dB, C0)
         pos = torch.from_numpy(synth.gather(q.lc, np.arange(q.C.size, dtype=np.int64))).cuda()
         err = rel(got[pos].double(), ref[pos])
+        held["small"][f"{prefix}gett/{algo}"] = (q, got.cpu().numpy())
 
         def c2():
             return gett.xgett(prefix, len(q.sig.exta), q.sig.exta, q.la.inc, dA, len(q.sig.extb), q.sig.extb,

@@ -314,3 +314,44 @@ def test_broadcast_index_count_limit(L, ext, ok):
         assert st == gett.GETT_OK and info["K"] == ext * ext and info["nk"] == 1
     else:
         assert st == gett.GETT_ERR_UNSUPPORTED
+
+
+def test_noalloc_bounds_each_class_before_adding(L):
+    """dgett_noalloc's fixed array bounds M + N + K.  Broadcast modes let two
+    classes count 2^62 indices each (M = K = 2^62, N = 1), whose sum does not
+    fit int64: the entry point must still answer GETT_ERR_UNSUPPORTED, before
+    any device work (the device pointers here are fake and never used).  C
+    spans 2^62 elements above both operands, so nothing overlaps."""
+    import ctypes
+    f = L.dgett_noalloc
+    f.argtypes = gett._ARGS14 + [ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    e31 = 1 << 31
+    st = f(4, gett._i64((e31, e31, e31, e31)), gett._i64((0, 0, 0, 0)), ctypes.c_void_p(4096),
+           2, gett._i64((e31, e31)), gett._i64((0, 0)), ctypes.c_void_p(8192),
+           2, gett._i32((2, 3)), gett._i32((0, 1)), gett._i32((0, 1)), gett._i64((1, e31)),
+           ctypes.c_void_p(1 << 40), ctypes.c_void_p(0))
+    assert st == gett.GETT_ERR_UNSUPPORTED
+    st, info = gett.plan_describe(4, (e31,) * 4, (0,) * 4, 2, (e31, e31), (0, 0), 2, (2, 3), (0, 1), (0, 1),
+                                  (1, e31))
+    assert st == gett.GETT_OK and info["M"] == 1 << 62 and info["K"] == 1 << 62 and info["N"] == 1
+
+
+def test_options_and_report_layout(L):
+    """gett_options carries the conjugation mask where three reserved ints
+    were (same size); gett_report ends with the call's device time."""
+    import ctypes
+    assert ctypes.sizeof(gett.Options) == 8 * 4
+    assert gett.Report.time_ms.offset == ctypes.sizeof(gett.Report) - 8
+    o = gett.options(conj=gett.GETT_CONJ_A | gett.GETT_CONJ_B)
+    assert o.conj == 3 and o.algo == 0 and o.config == -1
+
+
+def test_conj_mask_validated(L):
+    """Bits outside GETT_CONJ_A | GETT_CONJ_B are an argument error, before
+    any device work."""
+    a = _args()
+    st, _ = gett.xgett("z", a["RANKA"], a["EXTA"], a["INCA"], 4096, a["RANKB"], a["EXTB"], a["INCB"], 8192,
+                       a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], 1 << 40, mode="ex",
+                       opts=gett.options(conj=4), raise_on_error=False)
+    assert st == gett.GETT_ERR_ARG

@@ -1,6 +1,6 @@
 """GPU parity of the transpose (xGETP) and the reduction (xGETR) through the
 C ABI against the oracle's contraction with a unit / ones B (their
-definition; Sec. 8 lists both as future work).
+definition; Sec. 9 lists both as future work).
 
 A pure transpose (alpha = 1, beta = 0) moves values: bit-exact for every
 type.  Scaled forms and reductions: the element bound of the scaled form and

@@ -13,10 +13,15 @@ from tests._gpu_util import download, upload
 pytestmark = pytest.mark.gpu
 
 
-def sampled_elements(p, C_after, nsamples, seed):
+def sampled_elements(p, C_after, nsamples, seed, precision="f64", extremes=None):
+    """Per sampled output: (GPU value, oracle value, sum_k |A||B|).  With
+    `extremes` a list, also appends (max_k |A|, sum_k |A|, max_k |B|, sum_k
+    |B|) of the output's row of A and column of B for each sample."""
     s = p.sig
     rng = np.random.default_rng(seed)
     fps = s.free_modes()
+    kpos_a = synth._positions_f([s.exta[m] for m in s.conta], [p.la.inc[m] for m in s.conta], 0)
+    kpos_b = synth._positions_f([s.exta[m] for m in s.conta], [p.lb.inc[m] for m in s.contb], 0)
     out = []
     for _ in range(nsamples):
         o = [int(rng.integers(0, e)) for e in s.extc()]
@@ -29,7 +34,10 @@ def sampled_elements(p, C_after, nsamples, seed):
                 offb += x * p.lb.inc[m]
         r = s.conts
         c = np.zeros(1)
-        assert oracle.gett_raw("f64", r, [s.exta[m] for m in s.conta], [p.la.inc[m] for m in s.conta], p.A, offa,
+        if extremes is not None:
+            ra, cb = np.abs(p.A[offa + kpos_a]), np.abs(p.B[offb + kpos_b])
+            extremes.append((ra.max(), ra.sum(), cb.max(), cb.sum()))
+        assert oracle.gett_raw(precision, r, [s.exta[m] for m in s.conta], [p.la.inc[m] for m in s.conta], p.A, offa,
                                r, [s.exta[m] for m in s.conta], [p.lb.inc[m] for m in s.contb], p.B, offb,
                                r, list(range(r)), list(range(r)), [], [], c, 0) == 0
         terms = np.zeros(1)
@@ -52,12 +60,23 @@ def test_cc_full_size_sampled(algo, variant):
     gett.xgett("d", a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"], a["INCB"], dB, a["CONTS"],
                a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], dC, mode="ex", opts=gett.options(algo=algo))
     torch.cuda.synchronize()
-    res = sampled_elements(p, download(dC, np.float64), 96, 5)
+    ext = []
+    res = sampled_elements(p, download(dC, np.float64), 96, 5, precision="ld" if algo == "ozaki_bf16" else "f64",
+                           extremes=ext)
     got, ref, terms = res[:, 0], res[:, 1], res[:, 2]
     K = 128 * 128
     if algo == "native":
         # rounding bound of any summation order
         assert np.all(np.abs(got - ref) <= 2 * (K + 2) * 2.0 ** -53 * terms)
+    else:
+        # the split scheme's element bound against the long-double oracle:
+        # 2^-b (mA sB + sA mB) + K 2^-2b mA mB + 2^-52 (|C0| + sum |A||B|)
+        # (C0 is zero here), b the bits each operand keeps
+        _, bits, _ = gett.ozaki_params(K)
+        mA, sA, mB, sB = np.array(ext).T
+        u = 2.0 ** -bits
+        bound = u * (mA * sB + sA * mB) + K * u * u * mA * mB + 2.0 ** -52 * terms
+        assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) - bound)
     # normwise over the sample
     assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
 

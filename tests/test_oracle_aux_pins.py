@@ -1,6 +1,6 @@
 """Pins for the transpose and reduction references (the contraction with a
 unit / ones B, run by the oracle) against numpy.transpose and numpy.sum on the
-logical tensors.  Both operations are listed as future work in Sec. 8."""
+logical tensors.  Both operations are listed as future work in Sec. 9."""
 import numpy as np
 import pytest
 

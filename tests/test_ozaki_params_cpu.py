@@ -1,7 +1,7 @@
 """Host checks of the split-precision parameters (gett_ozaki_params) against
 the conditions that make the modular form exact (Ozaki, Uchino and Imamura
-2025; the thesis names no split method, Sec. 8 leaves precision to future
-work).  Scaled operands are integers of at most `bits` bits, so a sum of K
+2025; the thesis names no split method: its arithmetic is that of the
+operand types, Sec. 6).  Scaled operands are integers of at most `bits` bits, so a sum of K
 products has magnitude below K * 2^(2 bits); it is recovered exactly from its
 residues when that stays below P / 2, P the product of the moduli.  Every
 bound is checked here in exact integer arithmetic, not in the library's

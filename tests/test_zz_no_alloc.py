@@ -5,18 +5,20 @@ reserves its device memory up front, a latency-critical loop that cannot
 afford cudaFree's device-wide synchronisation, a framework whose allocator
 owns the device -- so this entry point keeps its scratch in a fixed device
 array of the library.  The tests call it through the C ABI and check its
-output against the regular dgett entry point on the same inputs, for two
-calls in a row (the second call accumulates onto the first and reuses the
-array the first call left behind).  This file is collected last, and works
-both alone in a fresh process and after the other tests.
+output, for two calls in a row (the second call accumulates onto the first
+and reuses the array the first call left behind), against the oracle element
+by element (the rounding bound of any summation order) and against the
+regular dgett entry point on the same inputs.  This file is collected last,
+and works both alone in a fresh process and after the other tests.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2410_06770_gb300 import gett, synth
-from tests._gpu_util import download, upload
+from tests._gpu_util import compare, download, upload
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +60,7 @@ def test_noalloc_matches_dgett_on_two_calls(case):
     dA, dB = upload(p.A), upload(p.B)
     dC_noalloc, dC_ref = upload(p.C), upload(p.C)
     a = p.args()
+    cur = p.copy()  # the oracle's C before this call
     for call in range(2):
         assert call_noalloc(f, p, dA, dB, dC_noalloc) == gett.GETT_OK
         gett.xgett("d", a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"], a["INCB"], dB,
@@ -66,6 +69,10 @@ def test_noalloc_matches_dgett_on_two_calls(case):
         torch.cuda.synchronize()
         got = download(dC_noalloc, np.float64)
         ref = download(dC_ref, np.float64)
+        # element by element against the oracle (Alg. 1 on the host)
+        expect = oracle.gett_problem(cur, "f64", nthreads=4)
+        compare("d", cur, got, expect)
+        cur.C = expect
         gaps = synth.gap_mask(p.lc)
         assert np.array_equal(got[gaps], p.C[gaps])
         g = synth.gather(p.lc, got)
