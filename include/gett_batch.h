@@ -5,12 +5,28 @@
  * Each problem is a full xGETT call (the 14 arguments of Sec. 5.7, same
  * meaning as in gett.h) with float C and either float or bfloat16 A and B;
  * products are accumulated in float.  gett_batch_create validates and plans
- * every problem on the host, chooses a tile configuration per problem,
- * uploads one descriptor table, one offset-table buffer and one tile work
- * list, and returns an opaque handle.  gett_batch_launch runs every tile of
- * every problem in ONE persistent kernel (one CTA per SM slot, tiles taken
- * from an atomic work counter); gett_batch_launch_graph does the same through
- * a CUDA graph captured on first use and replayed afterwards.
+ * every problem on the host, chooses a configuration per problem (a method
+ * and a tile shape, below), uploads one descriptor table, one offset-table
+ * buffer and the work lists, and returns an opaque handle.
+ * gett_batch_launch enqueues the whole batch as one fixed sequence of
+ * persistent kernels on one stream -- packing of the packed problems'
+ * operands, packed tiles, gathered tiles and short sums, skinny warp items,
+ * the ordered addition of K-slice partials -- with tiles taken from atomic
+ * work counters; gett_batch_launch_graph does the same through a CUDA graph
+ * captured on first use and replayed afterwards.
+ *
+ * Configurations (gett_batch_num_configs() of them):
+ *   0..3  GATHER with tile shape 0..3: tiles read A and B through the
+ *         planner's class offset tables (its logical mode fusion only);
+ *         sums of at most 8 terms form their outputs straight from gathered
+ *         loads whatever the method;
+ *   4..7  PACK with tile shape 0..3: A and B are first copied into
+ *         tile-blocked dense matrices (each class's modes physically fused
+ *         into one contiguous index; bf16 widened to float), which the tiles
+ *         then stream with bulk copies;
+ *   8     SKINNY: for a problem with a free class of at most 8 indices;
+ *         warp items along the long class or along the sum.
+ * gett_batch_config_shape and gett_batch_config_method describe an id.
  *
  * Ownership: the EXT/INC/CONT/PERM arrays are read during create only; the
  * device pointers A, B, C must stay valid while the handle is launched.  Each
@@ -65,21 +81,39 @@ typedef struct gett_batch_options {
 
 typedef struct gett_batch gett_batch;
 
+#define GETT_BATCH_MAX_CONFIGS 16
+
 typedef struct gett_batch_info {
     int n;                    /* problems                                   */
     int nonempty;             /* problems with work                         */
-    int64_t tiles;            /* work items of one launch                   */
+    int64_t tiles;            /* tile and warp work items of one launch     */
     double flops;             /* 2*M*N*K summed over problems               */
-    int config_count[8];      /* problems per tile configuration            */
+    int config_count[GETT_BATCH_MAX_CONFIGS]; /* problems per configuration */
     int fallbacks;            /* learned/table choices replaced by the heuristic */
+    int64_t gather_items;     /* work items of each kernel of a launch      */
+    int64_t packed_items;
+    int64_t pack_items;
+    int64_t skinny_items;
 } gett_batch_info;
 
-/* Number of tile configurations of the batched kernel and their shapes. */
+/* Number of configurations, the tile shape of an id (0 x 0 for SKINNY) and
+ * its method (0 GATHER, 1 PACK, 2 SKINNY); GETT_ERR_ARG for an unknown id. */
 int gett_batch_num_configs(void);
 int gett_batch_config_shape(int config, int *bm, int *bn);
+int gett_batch_config_method(int config);
+/* 1 if `config` can run the problem (14 xGETT arguments without pointers),
+ * 0 if not (SKINNY without a free class of at most 8 indices), or a
+ * negative status for invalid arguments.  Host only.  A table or learned
+ * choice that is not valid is replaced by the heuristic's (a fallback). */
+int gett_batch_config_valid(int RANKA, const int64_t *EXTA, const int64_t *INCA,
+                            int RANKB, const int64_t *EXTB, const int64_t *INCB,
+                            int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
+                            const int64_t *INCC, int config);
 
-/* The fixed heuristic's tile configuration for one problem (14 xGETT
- * arguments without pointers) -- the fallback of the other selectors. */
+/* The fixed heuristic's configuration for one problem (14 xGETT arguments
+ * without pointers) -- the fallback of the other selectors: sums of at most
+ * 8 terms GATHER (direct), a free class of at most 8 indices SKINNY,
+ * everything else PACK; the shape follows M and N. */
 int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const int64_t *INCA,
                                 int RANKB, const int64_t *EXTB, const int64_t *INCB,
                                 int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
@@ -91,7 +125,12 @@ int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const int64_t *I
  * GETT_ERR_ARG also for a NULL out, n < 0, SELECT_FIXED with a config
  * outside [0, gett_batch_num_configs()) or SELECT_TABLE without configs.
  * Validation touches no device; GETT_ERR_CUDA / GETT_ERR_NOMEM come from
- * the uploads that follow it. */
+ * the uploads that follow it.  GETT_ERR_UNSUPPORTED: a class of more than
+ * 2^31 indices, offset tables beyond 2^31 entries in all, or more than 2^31
+ * tiles in one problem.  A packed problem whose operands would take the
+ * packed buffer past 2^30 floats is gathered instead.  The packed tiles'
+ * bulk-copy waits are bounded; one that gives up records a code that
+ * gett_device_status() reports as GETT_ERR_TIMEOUT. */
 int gett_batch_create(int n, const gett_problem_desc *probs, const gett_batch_options *opt,
                       gett_batch **out, int *bad_index);
 int gett_batch_launch(gett_batch *b, void *stream);

@@ -29,9 +29,14 @@ class BatchOptions(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int)]
 
 
+MAX_CONFIGS = 16
+
+
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nonempty", ctypes.c_int), ("tiles", ctypes.c_int64),
-                ("flops", ctypes.c_double), ("config_count", ctypes.c_int * 8), ("fallbacks", ctypes.c_int)]
+                ("flops", ctypes.c_double), ("config_count", ctypes.c_int * MAX_CONFIGS),
+                ("fallbacks", ctypes.c_int), ("gather_items", ctypes.c_int64), ("packed_items", ctypes.c_int64),
+                ("pack_items", ctypes.c_int64), ("skinny_items", ctypes.c_int64)]
 
 
 _bound = False
@@ -56,6 +61,11 @@ def _bind():
     L.gett_batch_heuristic_config.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
                                               ctypes.c_int, _ip, _ip, _ip, _i64p, _ip]
     L.gett_batch_config_shape.argtypes = [ctypes.c_int, _ip, _ip]
+    L.gett_batch_config_method.argtypes = [ctypes.c_int]
+    L.gett_batch_config_method.restype = ctypes.c_int
+    L.gett_batch_config_valid.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
+                                          ctypes.c_int, _ip, _ip, _ip, _i64p, ctypes.c_int]
+    L.gett_batch_config_valid.restype = ctypes.c_int
     L.gett_problem_features.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
                                         ctypes.c_int, _ip, _ip, _ip, _i64p, ctypes.c_int, _fp]
     L.gett_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
@@ -139,7 +149,9 @@ class Batch:
         i = BatchInfo()
         L.gett_batch_get_info(self.h, ctypes.byref(i))
         return {"n": i.n, "nonempty": i.nonempty, "tiles": i.tiles, "flops": i.flops,
-                "config_count": list(i.config_count), "fallbacks": i.fallbacks}
+                "config_count": list(i.config_count), "fallbacks": i.fallbacks,
+                "gather_items": i.gather_items, "packed_items": i.packed_items, "pack_items": i.pack_items,
+                "skinny_items": i.skinny_items}
 
     def close(self):
         if getattr(self, "h", None):
@@ -165,6 +177,22 @@ def heuristic_config(args: dict) -> int:
                                              len(args["CONTA"]), gett._i32(args["CONTA"]), gett._i32(args["CONTB"]),
                                              gett._i32(args["PERM"]), gett._i64(args["INCC"]), ctypes.byref(c)))
     return c.value
+
+
+def config_method(config: int) -> int:
+    """0 GATHER, 1 PACK, 2 SKINNY."""
+    return _bind().gett_batch_config_method(int(config))
+
+
+def config_valid(args: dict, config: int) -> bool:
+    L = _bind()
+    st = L.gett_batch_config_valid(len(args["EXTA"]), gett._i64(args["EXTA"]), gett._i64(args["INCA"]),
+                                   len(args["EXTB"]), gett._i64(args["EXTB"]), gett._i64(args["INCB"]),
+                                   len(args["CONTA"]), gett._i32(args["CONTA"]), gett._i32(args["CONTB"]),
+                                   gett._i32(args["PERM"]), gett._i64(args["INCC"]), int(config))
+    if st < 0:
+        gett.check(st)
+    return st == 1
 
 
 def features(args: dict, dtype) -> np.ndarray:

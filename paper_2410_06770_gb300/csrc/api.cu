@@ -323,6 +323,13 @@ int device_sms()
     return st->sms;
 }
 
+int *device_error_word()
+{
+    DevState *st = nullptr;
+    if (dev_state(&st) != GETT_OK) return nullptr;
+    return st->err;
+}
+
 }  // namespace gett
 
 using gett::Args;

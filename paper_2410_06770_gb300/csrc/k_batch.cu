@@ -25,45 +25,23 @@
 #include <vector>
 
 #include "common.cuh"
+#include "batch_common.cuh"
 #include "dense_tile.cuh"
 #include "gett_batch.h"
 #include "internal.h"
 #include "learn.h"
+#include "select.h"
 
 namespace gett {
 
 namespace {
 
-constexpr int BT = 256;  // threads per CTA for every configuration
-constexpr int NCFG = 4;
-struct BCfg {
-    int bm, bn, bk, tm, tn;
-};
-// Tile shapes (all 256 threads, at most 4x4 accumulators a thread, so two
-// CTAs fit on an SM without spills: the gathers are latency bound and need
-// warps in flight).
-constexpr BCfg kB[NCFG] = {{64, 64, 16, 4, 4}, {32, 64, 16, 2, 4}, {32, 32, 16, 2, 2}, {64, 32, 16, 4, 2}};
-// Resident CTAs per SM: the kernel is compiled for 2, 3 and 4 (register caps
+// Resident CTAs per SM: the gather kernel is compiled for 2, 3 and 4 (register caps
 // 128, 80 and 64 per thread; the lower caps trade spills for warps in
 // flight).  The gathers are latency bound, so warps win: on the 4096-problem
 // workload 2 / 3 / 4 CTAs per SM take 8.74 / 7.97 / 7.37 ms.
 constexpr int kCtasPerSm = 4;
 constexpr int kMaxCtasPerSm = 4;
-
-struct BatchProb {
-    const void *A;
-    const void *B;
-    float *C;
-    int64_t M, N, K;
-    int64_t tab;  // offset of this problem's tables in the table buffer
-    int tiles_m, tiles_n;
-    int cfg, dtype;
-    int a_m_fast, b_n_fast, c_m_fast;
-    int splits;       // K slices (1: the tile is added into C directly)
-    int64_t kps;      // K per slice (multiple of the tile's BK)
-    float *partial;   // splits > 1: [splits][M*N] partial tiles
-    int tpi;          // tiles per work item (short sums: several; else 1)
-};
 
 // A short-sum problem (K <= 8, one slice) takes its outputs straight from
 // gathered loads; several of its tiles form one work item so that a few
@@ -130,8 +108,8 @@ __device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tab
 // Short sums (K <= 8, one K slice): each thread forms its TM x TN outputs
 // straight from gathered loads -- no shared-memory staging, no barriers, no
 // padding of K to the tile's BK.  Same thread-to-output mapping as the staged
-// tile (lanes along C's smaller increment) and the same summation order (k
-// ascending from zero, then added to C), so the results are identical.
+// tile (lanes along C's smaller increment); each output starts from C's value
+// and adds the products with k ascending, Alg. 1's order.
 template <class T, int CFG>
 __device__ __forceinline__ void run_direct(const BatchProb &pr, const int64_t *tables, int item)
 {
@@ -166,11 +144,13 @@ __device__ __forceinline__ void run_direct(const BatchProb &pr, const int64_t *t
         ob[j] = vn[j] ? colB[n] : 0;
         od[j] = vn[j] ? colC[n] : 0;
     }
+    // C is read before the sum (the batch only accumulates): its loads are
+    // in flight together with the operands' instead of after them
     Acc acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = R::zero();
+        for (int j = 0; j < TN; ++j) acc[i][j] = (vm[i] && vn[j]) ? pr.C[oc[i] + od[j]] : R::zero();
     for (int64_t k = 0; k < pr.K; ++k) {
         const int64_t ka = kA[k], kb = kB[k];
         Acc a[TM], b[TN];
@@ -187,20 +167,20 @@ __device__ __forceinline__ void run_direct(const BatchProb &pr, const int64_t *t
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j)
-            if (vm[i] && vn[j]) R::store_add(pr.C + oc[i] + od[j], acc[i][j]);
+            if (vm[i] && vn[j]) pr.C[oc[i] + od[j]] = acc[i][j];
 }
 
 // largest shared footprint over the configurations (floats / int64s)
 constexpr int smem_floats()
 {
     int m = 0;
-    for (int i = 0; i < NCFG; ++i) m = std::max(m, 2 * kB[i].bk * (kB[i].bm + kB[i].bn));
+    for (int i = 0; i < NSHAPE; ++i) m = std::max(m, 2 * kB[i].bk * (kB[i].bm + kB[i].bn));
     return m;
 }
 constexpr int smem_ints()
 {
     int m = 0;
-    for (int i = 0; i < NCFG; ++i) m = std::max(m, kB[i].bm + kB[i].bn);
+    for (int i = 0; i < NSHAPE; ++i) m = std::max(m, kB[i].bm + kB[i].bn);
     return m;
 }
 
@@ -225,7 +205,7 @@ __global__ void __launch_bounds__(BT, CPS) batch_kernel(const BatchProb *__restr
         if (threadIdx.x == 0) next = atomicAdd(counter, 1ull);
         const uint2 w = work[it % (unsigned long long)wrap];
         const BatchProb pr = probs[w.x];
-        const int key = pr.cfg * 2 + pr.dtype;
+        const int key = pr.shape * 2 + pr.dtype;
         if (batch_direct(pr)) {
             const int tend = min(pr.tiles_m * pr.tiles_n, ((int)w.y + 1) * pr.tpi);
             for (int tile = (int)w.y * pr.tpi; tile < tend; ++tile) {
@@ -316,13 +296,33 @@ int64_t first_abs(const ModeList &L, const int64_t *s) { return L.n ? (s[0] < 0 
 
 }  // namespace
 
-int batch_heuristic_config(int64_t M, int64_t N, int64_t K)
+// The fixed rule: short sums (K <= 8) take the gathered direct path; one
+// free class of at most 8 indices the skinny warp kernel; everything else is
+// packed.  The tile shape follows M and N.
+int batch_shape_rule(int64_t M, int64_t N)
 {
-    (void)K;
     if (M >= 64 && N >= 64) return 0;
     if (M < 64 && N >= 64) return 1;
     if (M >= 64 && N < 64) return 3;
     return 2;
+}
+
+bool batch_skinny_shape(int64_t M, int64_t N) { return std::min(M, N) <= SKINNY_MAX_SHORT; }
+
+int batch_heuristic_config(int64_t M, int64_t N, int64_t K)
+{
+    const int shape = batch_shape_rule(M, N);
+    if (K <= 8) return shape;
+    if (batch_skinny_shape(M, N)) return CFG_SKINNY;
+    return NSHAPE + shape;
+}
+
+// A configuration is valid for a problem unless it asks for the skinny
+// kernel on a problem without a free class of at most 8 indices.
+bool batch_config_valid(int cfg, int64_t M, int64_t N)
+{
+    if (cfg < 0 || cfg >= NCFG) return false;
+    return cfg != CFG_SKINNY || batch_skinny_shape(M, N);
 }
 
 }  // namespace gett
@@ -330,22 +330,35 @@ int batch_heuristic_config(int64_t M, int64_t N, int64_t K)
 struct gett_batch {
     int n = 0;
     int nonempty = 0;
-    int64_t nwork = 0;
+    int64_t nwork = 0;        // gathered tiles (work items of the gather kernel)
+    int64_t npacked = 0;      // packed tile items
+    int64_t npack = 0;        // packing items
+    int64_t nskinny = 0;      // skinny warp items
     double flops = 0;
-    int config_count[8] = {};
+    int config_count[GETT_BATCH_MAX_CONFIGS] = {};
     int fallbacks = 0;
     int ctas = 0;
-    int cps = 4;  // kernel instantiation (resident CTAs per SM it is compiled for)
+    int sms = 0;
+    int cps = 4;  // gather kernel instantiation (resident CTAs per SM it is compiled for)
     gett::BatchProb *d_probs = nullptr;
     uint2 *d_work = nullptr;
+    uint2 *d_packed_work = nullptr;
+    gett::PackItem *d_pack = nullptr;
+    gett::SkinnyItem *d_skinny = nullptr;
+    gett::SkinnyItem *d_skinny_by_problem = nullptr;
     int64_t *d_tables = nullptr;
-    unsigned long long *d_counter = nullptr;
-    uint2 *d_work_by_problem = nullptr;  // work items grouped by problem
-    float *d_partial = nullptr;          // K-slice partial tiles of split problems
+    float *d_packed = nullptr;           // tile-blocked operands of packed problems
+    unsigned long long *d_counter = nullptr;  // work counter of the gather kernel (and one spare)
+    // every list again grouped by problem (the autotuner times one problem)
+    uint2 *d_work_by_problem = nullptr;
+    uint2 *d_packed_by_problem = nullptr;
+    float *d_partial = nullptr;          // K-slice partials of split problems
     int *d_reduce = nullptr;             // indices (into the descriptor table) of split problems
+    int *d_err = nullptr;                // device error word (bounded waits)
     int nreduce = 0;
     std::vector<int> reduce_of;          // per user index: descriptor index if split, else -1
-    std::vector<int64_t> prob_start, prob_count;  // per user index (count 0: empty)
+    // per user index: start and count in each by-problem list
+    std::vector<int64_t> gw_start, gw_count, pw_start, pw_count, pk_start, pk_count, sk_start, sk_count;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap = nullptr;
@@ -358,9 +371,16 @@ extern "C" int gett_batch_num_configs(void) { return NCFG; }
 extern "C" int gett_batch_config_shape(int config, int *bm, int *bn)
 {
     if (config < 0 || config >= NCFG) return GETT_ERR_ARG;
-    if (bm) *bm = kB[config].bm;
-    if (bn) *bn = kB[config].bn;
+    const int m = cfg_method(config);
+    if (bm) *bm = m == BM_SKINNY ? 0 : kB[cfg_shape(config)].bm;
+    if (bn) *bn = m == BM_SKINNY ? 0 : kB[cfg_shape(config)].bn;
     return GETT_OK;
+}
+
+extern "C" int gett_batch_config_method(int config)
+{
+    if (config < 0 || config >= NCFG) return GETT_ERR_ARG;
+    return cfg_method(config);
 }
 
 extern "C" int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const int64_t *INCA, int RANKB,
@@ -378,13 +398,52 @@ extern "C" int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const
     return GETT_OK;
 }
 
+extern "C" int gett_batch_config_valid(int RANKA, const int64_t *EXTA, const int64_t *INCA, int RANKB,
+                                       const int64_t *EXTB, const int64_t *INCB, int CONTS, const int *CONTA,
+                                       const int *CONTB, const int *PERM, const int64_t *INCC, int config)
+{
+    Args a{RANKA, EXTA, INCA, RANKB, EXTB, INCB, CONTS, CONTA, CONTB, PERM, INCC};
+    Plan p;
+    int bad = 0;
+    int rc = make_plan(a, &p, &bad);
+    set_last_error_arg(bad);
+    if (rc != GETT_OK) return rc;
+    return batch_config_valid(config, p.M, p.N) ? 1 : 0;
+}
+
 namespace {
 
 // Limits of one batch's host-side planning (checked before allocating):
 // indices per class and offset-table entries over all problems (2^31
-// entries = 16 GB of int64 tables).
+// entries = 16 GB of int64 tables), packed operand floats (2^30 = 4 GB; a
+// problem whose packed operands would pass it is gathered instead).
 constexpr int64_t kMaxClassIndices = (int64_t)1 << 31;
 constexpr int64_t kMaxTableEntries = (int64_t)1 << 31;
+constexpr int64_t kMaxPackedFloats = (int64_t)1 << 30;
+constexpr int64_t kSkinnyLaneSlice = 256;   // K per warp item, lanes along the long class
+constexpr int64_t kSkinnySumSlice = 2048;   // K per warp item, lanes along the sum
+
+int64_t a64(int64_t x) { return (x + 63) & ~int64_t(63); }
+
+template <class T>
+cudaError_t upload(T **dst, const std::vector<T> &v)
+{
+    cudaError_t e = cudaMalloc(dst, sizeof(T) * std::max<size_t>(v.size(), 1));
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// items sorted by decreasing cost (long items first), stable
+template <class T>
+std::vector<T> by_cost(const std::vector<T> &items, const std::vector<double> &cost)
+{
+    std::vector<size_t> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<T> out(items.size());
+    for (size_t i = 0; i < order.size(); ++i) out[i] = items[order[i]];
+    return out;
+}
 
 int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_options *opt, gett_batch **out,
                       int *bad_index)
@@ -450,9 +509,13 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
         int cfg = -1;
         if (o.select == GETT_BATCH_SELECT_FIXED) cfg = o.config;
         else if (o.select == GETT_BATCH_SELECT_TABLE) cfg = o.configs[i];
-        else if (o.select == GETT_BATCH_SELECT_LEARNED) cfg = learned_batch_config(p, d.dtype, NCFG);
-        if (cfg < 0 || cfg >= NCFG) {
-            if (o.select == GETT_BATCH_SELECT_TABLE || o.select == GETT_BATCH_SELECT_LEARNED) ++fallbacks;
+        else if (o.select == GETT_BATCH_SELECT_LEARNED) {
+            bool valid[NCFG];
+            for (int c = 0; c < NCFG; ++c) valid[c] = batch_config_valid(c, p.M, p.N);
+            cfg = learned_batch_config(p, d.dtype, NCFG, valid);
+        }
+        if (!batch_config_valid(cfg, p.M, p.N)) {
+            if (o.select != GETT_BATCH_SELECT_HEURISTIC) ++fallbacks;
             cfg = batch_heuristic_config(p.M, p.N, p.K);
         }
         BatchProb b{};
@@ -465,8 +528,13 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
         b.tab = table_len;
         b.cfg = cfg;
         b.dtype = d.dtype;
+        b.shape = cfg_shape(cfg);
+        b.bm = kB[b.shape].bm;
+        b.bn = kB[b.shape].bn;
+        // short sums take the gathered direct path whatever the tile method
+        b.method = (p.K <= 8 && cfg_method(cfg) == BM_PACK) ? BM_GATHER : cfg_method(cfg);
         {
-            const int64_t tm = (p.M + kB[cfg].bm - 1) / kB[cfg].bm, tn = (p.N + kB[cfg].bn - 1) / kB[cfg].bn;
+            const int64_t tm = (p.M + b.bm - 1) / b.bm, tn = (p.N + b.bn - 1) / b.bn;
             if (tm * tn > (int64_t)INT32_MAX) {  // M, N <= 2^31 each: the product fits int64
                 set_last_error_arg(0);
                 if (bad_index) *bad_index = i;
@@ -515,41 +583,69 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     const int cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : kCtasPerSm;
     const int ctas = sms * cps;
 
-    // K slices: a tile whose work is far above the average share of a CTA is
-    // split along K so the longest work item stays short (tail effects), and
-    // so is any tile with more than kMaxSteps K steps whatever its area: a
-    // small tile with a long sum is a chain of dependent gathers, so its time
-    // grows with its K steps, not with its flops.  Slices of one tile are
-    // added into C in slice order by a second kernel.
+    // K slices.  Tiles (gathered or packed): a tile whose work is far above
+    // the average share of a CTA is split along K so the longest work item
+    // stays short (tail effects), and so is any tile with more than kMaxSteps
+    // K steps whatever its area (a small tile with a long sum is a chain of
+    // dependent steps).  Skinny warp items cover kSkinnyLaneSlice (lanes along
+    // the long class) or kSkinnySumSlice (lanes along the sum) contracted
+    // indices.  Slices of one problem are added into C in slice order by a
+    // second kernel.
     constexpr int64_t kMaxSteps = 96, kMaxSplits = 512;  // kMaxSteps * BK <= kStageK
     double total_cost = 0;
     for (const BatchProb &pr : hp)
-        total_cost += (double)pr.tiles_m * pr.tiles_n * kB[pr.cfg].bm * kB[pr.cfg].bn * (double)pr.K;
+        if (pr.method != BM_SKINNY) total_cost += (double)pr.tiles_m * pr.tiles_n * pr.bm * pr.bn * (double)pr.K;
     const double target = std::max(total_cost / (2.0 * ctas), 1.0);
-    int64_t partial_floats = 0;
-    std::vector<int64_t> partial_off(hp.size(), -1);
+    int64_t partial_floats = 0, packed_floats = 0;
+    std::vector<int64_t> partial_off(hp.size(), -1), packed_off(hp.size(), -1);
     for (size_t j = 0; j < hp.size(); ++j) {
         BatchProb &pr = hp[j];
-        const int bk = kB[pr.cfg].bk;
-        const double tile_cost = (double)kB[pr.cfg].bm * kB[pr.cfg].bn * (double)pr.K;
-        const int64_t steps = (pr.K + bk - 1) / bk;
-        int64_t S = std::max<int64_t>((int64_t)std::ceil(tile_cost / target), (steps + kMaxSteps - 1) / kMaxSteps);
-        S = std::min<int64_t>(S, kMaxSplits);
-        S = std::min<int64_t>(S, std::max<int64_t>(1, pr.K / 128));
-        if (S < 1) S = 1;
-        int64_t kps = (pr.K + S - 1) / S;
-        kps = (kps + bk - 1) / bk * bk;
-        S = (pr.K + kps - 1) / kps;
-        if (S > 1 && partial_floats + S * pr.M * pr.N > (int64_t)(1 << 28)) S = 1, kps = pr.K;
+        int64_t S = 1, kps = pr.K;
+        if (pr.method == BM_SKINNY) {
+            const int64_t L = std::max(pr.M, pr.N), Sh = std::min(pr.M, pr.N);
+            pr.long_is_a = pr.M >= pr.N ? 1 : 0;
+            pr.lanes_k = (L <= 4 && Sh <= 4) ? 1 : 0;
+            pr.kslice = pr.lanes_k ? kSkinnySumSlice : kSkinnyLaneSlice;
+            S = (pr.K + pr.kslice - 1) / pr.kslice;
+            if (S > 1 && partial_floats + S * pr.M * pr.N > (int64_t)(1 << 28)) {
+                pr.kslice = pr.K;  // one slice: long warp items, no partials
+                S = 1;
+            }
+            kps = pr.kslice;
+        } else {
+            const int bk = kB[pr.shape].bk;
+            const double tile_cost = (double)pr.bm * pr.bn * (double)pr.K;
+            const int64_t steps = (pr.K + bk - 1) / bk;
+            S = std::max<int64_t>((int64_t)std::ceil(tile_cost / target), (steps + kMaxSteps - 1) / kMaxSteps);
+            S = std::min<int64_t>(S, kMaxSplits);
+            S = std::min<int64_t>(S, std::max<int64_t>(1, pr.K / 128));
+            if (S < 1) S = 1;
+            kps = (pr.K + S - 1) / S;
+            kps = (kps + bk - 1) / bk * bk;
+            S = (pr.K + kps - 1) / kps;
+            if (S > 1 && partial_floats + S * pr.M * pr.N > (int64_t)(1 << 28)) S = 1, kps = pr.K;
+        }
         pr.splits = (int)S;
         pr.kps = S > 1 ? kps : pr.K;
         pr.tpi = 1;
         if (batch_direct(pr))
             pr.tpi = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)pr.tiles_m * pr.tiles_n,
-                                                                   32768 / (kB[pr.cfg].bm * kB[pr.cfg].bn)));
+                                                                   32768 / (pr.bm * pr.bn)));
         if (S > 1) {
             partial_off[j] = partial_floats;
             partial_floats += S * pr.M * pr.N;
+        }
+        if (pr.method == BM_PACK) {
+            // packed K is zero-padded to whole 16-steps: one slice covers Kp
+            pr.Kp = (pr.K + 15) / 16 * 16;
+            pr.kps = pr.splits > 1 ? std::min(pr.kps, pr.Kp) : pr.Kp;
+            const int64_t fa = a64(pr.Kp * pr.bm * (int64_t)pr.tiles_m), fb = a64(pr.Kp * pr.bn * (int64_t)pr.tiles_n);
+            if (packed_floats + fa + fb > kMaxPackedFloats) {
+                pr.method = BM_GATHER;  // the packed buffer is full: gather this one
+            } else {
+                packed_off[j] = packed_floats;
+                packed_floats += fa + fb;
+            }
         }
     }
 
@@ -557,26 +653,64 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     b->n = n;
     b->nonempty = (int)hp.size();
     b->fallbacks = fallbacks;
+    b->sms = sms;
     std::vector<int64_t> tables((size_t)std::max<int64_t>(table_len, 1));
-    std::vector<uint2> work;
-    std::vector<double> cost;
+    // per-problem lists (grouped) and their costs
+    std::vector<uint2> gwork, pwork;
+    std::vector<PackItem> pack;
+    std::vector<SkinnyItem> skinny;
+    std::vector<double> gcost, pcost, scost;
+    b->gw_start.assign(n, 0); b->gw_count.assign(n, 0);
+    b->pw_start.assign(n, 0); b->pw_count.assign(n, 0);
+    b->pk_start.assign(n, 0); b->pk_count.assign(n, 0);
+    b->sk_start.assign(n, 0); b->sk_count.assign(n, 0);
     for (size_t j = 0; j < hp.size(); ++j) {
         const Plan &p = plans[hp_index[j]];
         BatchProb &pr = hp[j];
+        const int ui = hp_index[j];
         int64_t *t = tables.data() + pr.tab;
         decode_host(p.m, p.M, t, t + p.M);
         decode_host(p.n, p.N, t + 2 * p.M, t + 2 * p.M + p.N);
         decode_host(p.k, p.K, t + 2 * p.M + 2 * p.N, t + 2 * p.M + 2 * p.N + p.K);
         b->flops += 2.0 * (double)p.M * (double)p.N * (double)p.K;
         b->config_count[pr.cfg]++;
-        const int nitems = batch_items(pr);
-        for (int tt = 0; tt < nitems; ++tt) {
-            work.push_back(make_uint2((unsigned)j, (unsigned)tt));
-            cost.push_back((double)kB[pr.cfg].bm * kB[pr.cfg].bn * (double)pr.kps * pr.tpi);
+        const double tile_area = (double)pr.bm * pr.bn;
+        if (pr.method == BM_GATHER) {
+            b->gw_start[ui] = (int64_t)gwork.size();
+            const int nitems = batch_items(pr);
+            for (int tt = 0; tt < nitems; ++tt) {
+                gwork.push_back(make_uint2((unsigned)j, (unsigned)tt));
+                gcost.push_back(tile_area * (double)pr.kps * pr.tpi);
+            }
+            b->gw_count[ui] = nitems;
+        } else if (pr.method == BM_PACK) {
+            b->pw_start[ui] = (int64_t)pwork.size();
+            const int nitems = pr.tiles_m * pr.tiles_n * pr.splits;
+            for (int tt = 0; tt < nitems; ++tt) {
+                pwork.push_back(make_uint2((unsigned)j, (unsigned)tt));
+                pcost.push_back(tile_area * (double)pr.kps);
+            }
+            b->pw_count[ui] = nitems;
+            b->pk_start[ui] = (int64_t)pack.size();
+            const int chunks = (int)((pr.Kp + 63) / 64);
+            for (int op = 0; op < 2; ++op) {
+                const int blocks = op == 0 ? pr.tiles_m : pr.tiles_n;
+                for (int bl = 0; bl < blocks; ++bl)
+                    for (int ch = 0; ch < chunks; ++ch) pack.push_back(PackItem{(int)j, op, bl, ch});
+            }
+            b->pk_count[ui] = (int64_t)pack.size() - b->pk_start[ui];
+        } else {
+            b->sk_start[ui] = (int64_t)skinny.size();
+            const int64_t L = std::max(pr.M, pr.N);
+            const int64_t lblocks = pr.lanes_k ? 1 : (L + 31) / 32;
+            for (int sl = 0; sl < pr.splits; ++sl)
+                for (int64_t lb = 0; lb < lblocks; ++lb) {
+                    skinny.push_back(SkinnyItem{(int)j, sl, lb * 32});
+                    scost.push_back((double)std::min(pr.kslice, pr.K - (int64_t)sl * pr.kslice));
+                }
+            b->sk_count[ui] = (int64_t)skinny.size() - b->sk_start[ui];
         }
     }
-    b->prob_start.assign(n, 0);
-    b->prob_count.assign(n, 0);
     b->reduce_of.assign(n, -1);
     std::vector<int> reduce_list;
     for (size_t j = 0; j < hp.size(); ++j)
@@ -585,44 +719,38 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
             reduce_list.push_back((int)j);
         }
     b->nreduce = (int)reduce_list.size();
-    {
-        int64_t pos = 0;
-        for (size_t j = 0; j < hp.size(); ++j) {
-            const int nt = batch_items(hp[j]);
-            b->prob_start[hp_index[j]] = pos;
-            b->prob_count[hp_index[j]] = nt;
-            pos += nt;
-        }
-    }
-    // longest tiles first
-    std::vector<size_t> order(work.size());
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
-    std::vector<uint2> sorted(work.size());
-    for (size_t i = 0; i < order.size(); ++i) sorted[i] = work[order[i]];
-    b->nwork = (int64_t)sorted.size();
-
+    const std::vector<uint2> gsorted = by_cost(gwork, gcost), psorted = by_cost(pwork, pcost);
+    const std::vector<SkinnyItem> ssorted = by_cost(skinny, scost);
+    b->nwork = (int64_t)gsorted.size();
+    b->npacked = (int64_t)psorted.size();
+    b->npack = (int64_t)pack.size();
+    b->nskinny = (int64_t)ssorted.size();
     b->ctas = ctas;
     b->cps = std::min(cps, kMaxCtasPerSm);
+
     e = cudaMalloc(&b->d_partial, sizeof(float) * (size_t)std::max<int64_t>(partial_floats, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_packed, sizeof(float) * (size_t)std::max<int64_t>(packed_floats, 1));
     if (e == cudaSuccess)
-        for (size_t j = 0; j < hp.size(); ++j)
+        for (size_t j = 0; j < hp.size(); ++j) {
             hp[j].partial = partial_off[j] >= 0 ? b->d_partial + partial_off[j] : nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_reduce, sizeof(int) * std::max<size_t>(reduce_list.size(), 1));
-    if (e == cudaSuccess && !reduce_list.empty())
-        e = cudaMemcpy(b->d_reduce, reduce_list.data(), sizeof(int) * reduce_list.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, sizeof(BatchProb) * std::max<size_t>(hp.size(), 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_work, sizeof(uint2) * std::max<size_t>(sorted.size(), 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_tables, sizeof(int64_t) * tables.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_work_by_problem, sizeof(uint2) * std::max<size_t>(work.size(), 1));
-    if (e == cudaSuccess && !work.empty())
-        e = cudaMemcpy(b->d_work_by_problem, work.data(), sizeof(uint2) * work.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !hp.empty())
-        e = cudaMemcpy(b->d_probs, hp.data(), sizeof(BatchProb) * hp.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !sorted.empty())
-        e = cudaMemcpy(b->d_work, sorted.data(), sizeof(uint2) * sorted.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_tables, tables.data(), sizeof(int64_t) * tables.size(), cudaMemcpyHostToDevice);
+            if (packed_off[j] >= 0) {
+                hp[j].pA = b->d_packed + packed_off[j];
+                hp[j].pB = b->d_packed + packed_off[j] + a64(hp[j].Kp * hp[j].bm * (int64_t)hp[j].tiles_m);
+            }
+        }
+    if (e == cudaSuccess) e = upload(&b->d_reduce, reduce_list);
+    if (e == cudaSuccess) e = upload(&b->d_probs, hp);
+    if (e == cudaSuccess) e = upload(&b->d_work, gsorted);
+    if (e == cudaSuccess) e = upload(&b->d_packed_work, psorted);
+    if (e == cudaSuccess) e = upload(&b->d_pack, pack);
+    if (e == cudaSuccess) e = upload(&b->d_skinny, ssorted);
+    if (e == cudaSuccess) e = upload(&b->d_tables, tables);
+    if (e == cudaSuccess) e = upload(&b->d_work_by_problem, gwork);
+    if (e == cudaSuccess) e = upload(&b->d_packed_by_problem, pwork);
+    if (e == cudaSuccess) e = upload(&b->d_skinny_by_problem, skinny);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) b->d_err = device_error_word();
+    if (e == cudaSuccess && !b->d_err) e = cudaErrorInitializationError;
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
         gett_batch_destroy(b);
@@ -648,16 +776,59 @@ extern "C" int gett_batch_create(int n, const gett_problem_desc *probs, const ge
     }
 }
 
+namespace {
+
+// Item ranges of one launch: the whole batch, or one problem's items (the
+// autotuner), each list repeated `copies` times through the kernels' wrap.
+struct Ranges {
+    const uint2 *gw;
+    int64_t gn;
+    const uint2 *pw;
+    int64_t pn;
+    const PackItem *pk;
+    int64_t kn;
+    const SkinnyItem *sk;
+    int64_t sn;
+    const int *red;
+    int nred;
+    int64_t copies;
+};
+
+cudaError_t enqueue_ranges(gett_batch *b, const Ranges &r, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int64_t c = r.copies;
+    // 1. pack the operands of packed problems, 2. their tiles, 3. gathered
+    // tiles and short sums, 4. skinny warp items, 5. the ordered reduction of
+    // K-slice partials
+    if (r.kn > 0)
+        launch_batch_pack((int)std::min<int64_t>(r.kn * c, (int64_t)b->sms * 8), s, b->d_probs, r.pk, r.kn * c, r.kn,
+                          b->d_tables);
+    if (r.pn > 0) {
+        const int ctas = (int)std::min<int64_t>((int64_t)b->sms * batch_packed_ctas_per_sm(), r.pn * c);
+        launch_batch_packed_tiles(batch_packed_ctas_per_sm(), ctas, s, b->d_probs, r.pw, r.pn * c, r.pn, b->d_tables,
+                                  b->d_err);
+    }
+    if (r.gn > 0) {
+        const int ctas = (int)std::min<int64_t>(b->ctas, r.gn * c);
+        launch_batch_kernel(b->cps, ctas, s, b->d_probs, r.gw, r.gn * c, r.gn, b->d_tables, b->d_counter);
+    }
+    if (r.sn > 0)
+        launch_batch_skinny((int)std::min<int64_t>((r.sn * c + 7) / 8, (int64_t)b->sms * 4), s, b->d_probs, r.sk,
+                            r.sn * c, r.sn, b->d_tables);
+    if (r.nred > 0)
+        batch_reduce_kernel<<<std::min(r.nred, b->ctas), 256, 0, s>>>(b->d_probs, r.red, r.nred, b->d_tables);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 static cudaError_t enqueue(gett_batch *b, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess || b->nwork == 0) return e;
-    const int ctas = (int)std::min<int64_t>(b->ctas, b->nwork);
-    launch_batch_kernel(b->cps, ctas, s, b->d_probs, b->d_work, b->nwork, b->nwork, b->d_tables, b->d_counter);
-    if (b->nreduce > 0)
-        batch_reduce_kernel<<<std::min(b->nreduce, b->ctas), 256, 0, s>>>(b->d_probs, b->d_reduce, b->nreduce,
-                                                                          b->d_tables);
-    return cudaGetLastError();
+    const Ranges r{b->d_work, b->nwork, b->d_packed_work, b->npacked, b->d_pack, b->npack,
+                   b->d_skinny, b->nskinny, b->d_reduce, b->nreduce, 1};
+    return enqueue_ranges(b, r, s);
 }
 
 extern "C" int gett_batch_launch(gett_batch *b, void *stream)
@@ -707,25 +878,24 @@ extern "C" int gett_batch_profile(gett_batch *b, int reps, int mode, float *ms_o
     cudaEventCreate(&e1);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         ms_out[i] = 0.f;
-        const int64_t cnt = b->prob_count[i];
+        const int64_t cnt = b->gw_count[i] + b->pw_count[i] + b->sk_count[i];
         if (cnt == 0) continue;
-        const uint2 *w = b->d_work_by_problem + b->prob_start[i];
         // throughput mode: enough copies of the problem's items to give every
-        // persistent CTA several, so the time reflects its cost in a full GPU
-        const int64_t copies = mode == 1 ? std::min<int64_t>(64, std::max<int64_t>(1, (4LL * b->ctas + cnt - 1) / cnt)) : 1;
-        const int64_t items = cnt * copies;
-        const int ctas = (int)std::min<int64_t>(b->ctas, items);
+        // persistent CTA (skinny: every warp) several, so the time reflects
+        // its cost in a full GPU
+        const int64_t slots = b->sk_count[i] > 0 ? (int64_t)b->sms * 32 : (int64_t)b->ctas;
+        const int64_t copies = mode == 1 ? std::min<int64_t>(64, std::max<int64_t>(1, (4 * slots + cnt - 1) / cnt)) : 1;
         const int red = b->reduce_of[i];
-        auto one = [&] {
-            cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
-            launch_batch_kernel(b->cps, ctas, s, b->d_probs, w, items, cnt, b->d_tables, b->d_counter);
-            if (red >= 0) batch_reduce_kernel<<<1, 256, 0, s>>>(b->d_probs, b->d_reduce + red, 1, b->d_tables);
-        };
-        one();  // warm-up
+        const Ranges r{b->d_work_by_problem + b->gw_start[i], b->gw_count[i],
+                       b->d_packed_by_problem + b->pw_start[i], b->pw_count[i],
+                       b->d_pack + b->pk_start[i], b->pk_count[i],
+                       b->d_skinny_by_problem + b->sk_start[i], b->sk_count[i],
+                       red >= 0 ? b->d_reduce + red : nullptr, red >= 0 ? 1 : 0, copies};
+        e = enqueue_ranges(b, r, s);  // warm-up
         cudaEventRecord(e0, s);
-        for (int r = 0; r < reps; ++r) one();
+        for (int rr = 0; rr < reps && e == cudaSuccess; ++rr) e = enqueue_ranges(b, r, s);
         cudaEventRecord(e1, s);
-        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         ms_out[i] = ms / reps / (float)copies;
@@ -746,10 +916,14 @@ extern "C" int gett_batch_get_info(const gett_batch *b, gett_batch_info *info)
     std::memset(info, 0, sizeof(*info));
     info->n = b->n;
     info->nonempty = b->nonempty;
-    info->tiles = b->nwork;
+    info->tiles = b->nwork + b->npacked + b->nskinny;
     info->flops = b->flops;
-    for (int i = 0; i < 8; ++i) info->config_count[i] = b->config_count[i];
+    for (int i = 0; i < GETT_BATCH_MAX_CONFIGS; ++i) info->config_count[i] = b->config_count[i];
     info->fallbacks = b->fallbacks;
+    info->gather_items = b->nwork;
+    info->packed_items = b->npacked;
+    info->pack_items = b->npack;
+    info->skinny_items = b->nskinny;
     return GETT_OK;
 }
 
@@ -759,13 +933,11 @@ extern "C" int gett_batch_destroy(gett_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
-    if (b->d_probs) cudaFree(b->d_probs);
-    if (b->d_work) cudaFree(b->d_work);
-    if (b->d_tables) cudaFree(b->d_tables);
-    if (b->d_counter) cudaFree(b->d_counter);
-    if (b->d_work_by_problem) cudaFree(b->d_work_by_problem);
-    if (b->d_partial) cudaFree(b->d_partial);
-    if (b->d_reduce) cudaFree(b->d_reduce);
+    void *bufs[] = {b->d_probs, b->d_work, b->d_packed_work, b->d_pack, b->d_skinny, b->d_skinny_by_problem,
+                    b->d_tables, b->d_packed, b->d_counter, b->d_work_by_problem, b->d_packed_by_problem,
+                    b->d_partial, b->d_reduce};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
     delete b;
     return GETT_OK;
 }

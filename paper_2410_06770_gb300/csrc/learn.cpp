@@ -84,7 +84,7 @@ void plan_features(const Plan &p, int dtype, float *f)
     f[23] = 1.f;
 }
 
-int learned_batch_config(const Plan &p, int dtype, int ncfg)
+int learned_batch_config(const Plan &p, int dtype, int ncfg, const bool *valid)
 {
     std::lock_guard<std::mutex> lk(g_model_mu);
     if (!g_model.ok || g_model.nfeat != GETT_LEARN_NFEAT || g_model.nout < ncfg) return -1;
@@ -92,9 +92,9 @@ int learned_batch_config(const Plan &p, int dtype, int ncfg)
     plan_features(p, dtype, f);
     std::vector<float> out(g_model.nout);
     if (!model_forward(g_model, f, out.data())) return -1;
-    int best = 0;
-    for (int c = 1; c < ncfg; ++c)
-        if (out[c] < out[best]) best = c;
+    int best = -1;
+    for (int c = 0; c < ncfg; ++c)
+        if ((!valid || valid[c]) && (best < 0 || out[c] < out[best])) best = c;
     return best;
 }
 

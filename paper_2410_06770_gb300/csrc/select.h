@@ -22,5 +22,8 @@ int choose(const Plan &p, DType t, const gett_options *opt, int num_sms, Choice 
 Choice heuristic_choice(const Plan &p, DType t, int num_sms);
 
 int device_sms();
+// The current device's error word (bounded waits record a code there; read
+// and cleared by gett_device_status), or NULL without a usable device.
+int *device_error_word();
 
 }  // namespace gett

@@ -56,19 +56,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 
 // Bounded wait for the phase with the given parity to complete.  Returns
 // false (after recording `code` in *err) when `limit` clock cycles pass or
-// when another role already recorded an error.
+// when another role already recorded an error.  The clock and the error
+// word are looked at every 256 polls: the word is global memory, and a
+// volatile load of it on every poll by hundreds of waiting threads turns one
+// L2 line into a hot spot that delays every wait.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code,
                                           long long limit = kWaitLimitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (true) {
+    for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > limit) {
-            atomicCAS(err, 0, code);
-            return false;
+        if ((i & 255u) == 0) {
+            if (clock64() - t0 > limit) {
+                atomicCAS(err, 0, code);
+                return false;
+            }
+            if (*(volatile int *)err != 0) return false;
         }
-        if (*(volatile int *)err != 0) return false;
     }
 }
 

@@ -6,11 +6,13 @@
 1. Draws contraction signatures from the batched workload's distribution
    (ranks 2-5, extents up to --max-ext, 0-3 contracted modes, 25 % padded,
    fp32/bf16 operands, <= 2^18 elements per tensor).
-2. Autotuner: times every problem with every tile configuration of the
-   batched kernel (gett_batch_profile in throughput mode: the problem's tiles
-   repeated until the GPU is full, CUDA events around back-to-back launches,
-   time per copy) -> a table of costs; the exhaustive best configuration is
-   the tuned choice.
+2. Autotuner: times every problem with every configuration of the batched
+   launch -- tile shape x method: gathered tiles (logical mode fusion only),
+   packed tiles (the operands' modes physically fused by a packing copy) or
+   the skinny warp kernel where a free class has at most 8 indices
+   (gett_batch_profile in throughput mode: the problem's items repeated until
+   the GPU is full, CUDA events around back-to-back launches, time per copy)
+   -> a table of costs; the exhaustive best configuration is the tuned choice.
 3. Learned planner: features of each signature (gett_problem_features) ->
    MLP predicting normalised log times of all configurations, trained on the
    GPU by the library's own kernels (gett_mlp_fit).
@@ -91,11 +93,20 @@ class DeviceBuffers:
             self.descs.append(d)
 
 
+def valid_mask(probs):
+    """valid[i][c]: configuration c can run problem i (SKINNY needs a free
+    class of at most 8 indices)."""
+    nc = gb.num_configs()
+    return np.array([[gb.config_valid(args_of(pr), c) for c in range(nc)] for pr in probs], dtype=bool)
+
+
 def measure(probs, reps=3, chunk=1024, log=None):
-    """times[i][c]: mean ms of problem i alone with tile configuration c."""
+    """times[i][c]: mean ms of problem i alone with configuration c (NaN
+    where c cannot run problem i)."""
     import torch
     nc = gb.num_configs()
     T = np.zeros((len(probs), nc), dtype=np.float64)
+    V = valid_mask(probs)
     for s in range(0, len(probs), chunk):
         part = probs[s:s + chunk]
         bufs = DeviceBuffers(part)
@@ -103,6 +114,7 @@ def measure(probs, reps=3, chunk=1024, log=None):
             b = gb.Batch(bufs.descs, select="fixed", config=c)
             T[s:s + len(part), c] = b.profile(reps)
             b.close()
+        T[s:s + len(part)][~V[s:s + len(part)]] = np.nan
         del bufs
         torch.cuda.empty_cache()
         if log:
@@ -119,26 +131,31 @@ def train(X, T, hidden=128, epochs=60, batch=256, lr=1e-3, seed=0):
     std = X.std(0)
     std[std == 0] = 1.0
     Xn = (X - mean) / std
-    Y = np.log(np.maximum(T, 1e-6))
-    mu, sd = Y.mean(), Y.std() if Y.std() > 0 else 1.0
-    Yn = ((Y - mu) / sd).astype(np.float32)
-    M = np.ones_like(Yn, dtype=np.float32)
+    valid = np.isfinite(T)
+    Y = np.log(np.maximum(np.where(valid, T, 1.0), 1e-6))
+    mu, sd = Y[valid].mean(), Y[valid].std() if Y[valid].std() > 0 else 1.0
+    Yn = np.where(valid, (Y - mu) / sd, 0.0).astype(np.float32)
+    M = valid.astype(np.float32)  # masked loss: configurations that cannot run a problem teach nothing
     net = gb.MLP(X.shape[1], hidden, T.shape[1], seed=seed)
     loss = net.fit(Xn.astype(np.float32), Yn, M, epochs=epochs, batch=batch, lr=lr, seed=seed + 1)
     return dict(params=net.get_params(), mean=mean.astype(np.float32), std=std.astype(np.float32),
                 hidden=hidden, nout=T.shape[1], final_loss=loss, y_mean=mu, y_std=sd)
 
 
-def predict_configs(model, X):
+def predict_configs(model, X, valid=None):
+    """The network's choice: argmin of the predicted times over the valid
+    configurations; `finite` is False where a prediction is not finite."""
     net = gb.MLP(X.shape[1], model["hidden"], model["nout"], seed=0)
     net.set_params(model["params"])
     Y = net.predict(((X - model["mean"]) / model["std"]).astype(np.float32))
     finite = np.all(np.isfinite(Y), axis=1)
+    if valid is not None:
+        Y = np.where(valid, Y, np.inf)
     return np.argmin(Y, axis=1), finite
 
 
 def regret(choice, T):
-    best = T.min(axis=1)
+    best = np.nanmin(T, axis=1)
     r = T[np.arange(len(T)), choice] / best
     return {"geomean_regret": float(np.exp(np.mean(np.log(r))) - 1.0),
             "share_above_10pct": float(np.mean(r > 1.10)),
@@ -207,9 +224,9 @@ def main(argv=None):
     log("features done")
     model = train(Xtr, Ttr, epochs=args.epochs)
     log(f"trained, final loss {model['final_loss']:.4f}")
-    pred, finite = predict_configs(model, Xte)
+    pred, finite = predict_configs(model, Xte, np.isfinite(Tte))
     heur = np.array([gb.heuristic_config(args_of(pr)) for pr in te])
-    tuned = T_best = Tte.argmin(axis=1)
+    tuned = np.nanargmin(Tte, axis=1)
     pred_used = np.where(finite, pred, heur)
     rep = {
         "train": args.train, "test": args.test, "max_ext": args.max_ext, "epochs": args.epochs,

@@ -1,6 +1,7 @@
 """GPU parity of the batched persistent launch: every problem's C against the
 oracle (fp32 arithmetic: element bound 2 (K+2) 2^-24 (|C0| + sum |A||B|)),
-plain and graph launches, every tile configuration, alias rejection."""
+plain and graph launches, every configuration (tile shape x GATHER / PACK,
+and SKINNY), skinny-heavy batches with K slices, alias rejection."""
 import numpy as np
 import pytest
 
@@ -21,6 +22,31 @@ def make_batch_problems(n, seed, max_ext=12, pad_frac=0.25):
         rb = int(rng.integers(max(2, k), 6))
         sig = synth.capped_signature(rng, ra, rb, k, 2, max_ext, 1 << 16)
         kinds = ("padded",) * 3 if rng.random() < pad_frac else ("contig",) * 3
+        p = synth.make_problem(sig, rng, np.float64, "uniform", kinds, "uniform")
+        prefix = "sb" if rng.integers(0, 2) else "s"
+        probs.append((prefix, problem_for(prefix, p)))
+    return probs
+
+
+def make_skinny_problems(n, seed):
+    """Dot products (no free index), GEMV shapes (one free class of at most 8
+    indices) and few-output sums (both free classes of at most 4 indices,
+    sums long enough for several K slices), in random layouts."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for i in range(n):
+        kind = i % 3
+        k1, k2 = int(rng.integers(8, 90)), int(rng.integers(8, 90))
+        if kind == 0:
+            sig = synth.Signature((k1, k2), (k2, k1), (0, 1), (1, 0), ())
+        elif kind == 1:
+            m, s_ = int(rng.integers(20, 300)), int(rng.integers(1, 9))
+            sig = synth.Signature((k1, m, k2), (k2, s_, k1), (0, 2), (2, 0), (0, 1)) if rng.integers(0, 2) \
+                else synth.Signature((k1, s_, k2), (k2, m, k1), (0, 2), (2, 0), (1, 0))
+        else:
+            m, s_ = int(rng.integers(1, 5)), int(rng.integers(1, 5))
+            sig = synth.Signature((m, k1, k2), (k1, k2, s_), (1, 2), (0, 1), (1, 0))
+        kinds = tuple(rng.choice(["contig", "padded", "rowmajor", "negative"], 3))
         p = synth.make_problem(sig, rng, np.float64, "uniform", kinds, "uniform")
         prefix = "sb" if rng.integers(0, 2) else "s"
         probs.append((prefix, problem_for(prefix, p)))
@@ -58,7 +84,7 @@ def check_all(probs, dev, times=1):
         assert np.all(np.abs(g - r) <= 2.0 * (K + 2) * times * 2.0 ** -24 * bound + 1e-30)
 
 
-@pytest.mark.parametrize("select,config", [("heuristic", 0), ("fixed", 0), ("fixed", 1), ("fixed", 2), ("fixed", 3)])
+@pytest.mark.parametrize("select,config", [("heuristic", 0)] + [("fixed", c) for c in range(9)])
 def test_batch_matches_oracle(select, config):
     import torch
     probs = make_batch_problems(150, 1 + config)
@@ -66,10 +92,42 @@ def test_batch_matches_oracle(select, config):
     b = gb.Batch(descs, select=select, config=config)
     info = b.info()
     assert info["n"] == 150 and info["tiles"] > 0
+    if select == "fixed" and gb.config_method(config) == 1:
+        assert info["packed_items"] > 0 and info["pack_items"] > 0
+    if select == "heuristic":
+        assert info["packed_items"] > 0 and info["gather_items"] > 0
     b.launch()
     torch.cuda.synchronize()
     check_all(probs, dev)
     b.close()
+
+
+@pytest.mark.parametrize("select", ["heuristic", "pack", "gather"])
+def test_skinny_heavy_batch(select):
+    """Dot, GEMV-like and few-output problems: the skinny warp kernel (lanes
+    along the long class, and lanes along the sum with K slices added in
+    order by the reduction) under the heuristic, and the same problems as
+    packed or gathered tiles through a table."""
+    import torch
+    probs = make_skinny_problems(90, 31)
+    dev, descs = upload_all(probs)
+    if select == "heuristic":
+        b = gb.Batch(descs)
+        info = b.info()
+        assert info["skinny_items"] > 0 and info["config_count"][8] == 90
+    else:
+        cfg = 6 if select == "pack" else 2
+        b = gb.Batch(descs, select="table", configs=[cfg] * len(descs))
+        assert b.info()["config_count"][cfg] == 90
+    b.launch(graph=True)
+    torch.cuda.synchronize()
+    check_all(probs, dev)
+    b.close()
+
+
+def test_config_descriptions():
+    assert gb.num_configs() == 9
+    assert [gb.config_method(c) for c in range(9)] == [0] * 4 + [1] * 4 + [2]
 
 
 @pytest.mark.parametrize("ctas_per_sm", [1, 3, 4, 6])
