@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-tune-db", action="store_true", help="do not load the shipped tuning database")
     return ap.parse_args()
 
 
@@ -286,6 +287,12 @@ def gpu_arm(args, dist: Dist):
     from paper_2410_06770_gb300 import peaks as peaks_mod
     pk = peaks_mod.measure(copy_bytes=1 << 30)
 
+    # the tuned step of the configuration choice: the shipped tuning
+    # database (single-call entries of the bench workloads, measured by
+    # `python -m paper_2410_06770_gb300.tune --single`)
+    if not args.no_tune_db and os.path.exists(TUNE_DB):
+        gett.tune_db_load(TUNE_DB)
+
     p, wdesc = workload(args.workload)
     flops = flops_of(p)
     stream = torch.cuda.current_stream()
@@ -341,9 +348,10 @@ def gpu_arm(args, dist: Dist):
     fam = rep["family_name"]
     if fam == "dense":
         peak = pk["dfma_tflops"]
+        tiles = {0: "128,128,8,8,8", 1: "64,64,8,4,4", 2: "32,32,16,2,2"}
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "peak_source": "measured DFMA microbenchmark (FP64 FMA pipe)",
-                "kernel": "dense_kernel<double,128,128,8,8,8>"}
+                "kernel": f"dense_kernel<double,{tiles.get(rep['config'], '?')}>"}
     else:
         mp = measured_peaks()
         bw = mp.get("hbm_gbs", 6800.0)
@@ -362,6 +370,7 @@ def gpu_arm(args, dist: Dist):
         "config": {"workload": wdesc, "M": rep["M"], "N": rep["N"], "K": rep["K"],
                    "flops_per_step": flops, "algo": args.algo, "family": fam,
                    "tile_config": rep["config"], "split_k": rep["split_k"],
+                   "selector": {0: "heuristic", 1: "tuning database", 2: "learned", 3: "forced"}.get(rep["selector"]),
                    "l2": "inputs larger than L2 (A is 2.1 GB), no flush"},
         "roofline": roof,
         "gpu_launches": launches_per_call * args.steps,
@@ -384,7 +393,14 @@ def gpu_arm(args, dist: Dist):
         cpu, split = cpu_baseline_leg(p, args.cpu_seconds, held, value)
         result["cpu_baseline"] = cpu
         if split:
-            # last key of the line: the driver keeps the line's tail
+            # last keys of the line: the driver keeps the line's tail
+            bt = result.get("forms", {}).get("batched")
+            if bt:
+                result["batched"] = {k: _r(bt[k]["ms"]) for k in bt if k.startswith("batched_") or k == "per_call"}
+                result["batched"]["contractions_per_s_learned"] = _r(bt.get("batched_learned", {}).get(
+                    "contractions_per_s", 0.0))
+                if "roofline" in bt:
+                    result["batched"]["roofline_ms"] = _r(bt["roofline"]["ms"])
             result["split"] = split
     return result
 
@@ -665,6 +681,7 @@ def measure_split_forms(held):
 
 
 MODEL_PATH = os.path.join(ROOT, "paper_2410_06770_gb300", "planner_mlp.npz")
+TUNE_DB = os.path.join(ROOT, "paper_2410_06770_gb300", "tune_db.txt")
 
 
 def measure_batched(n=4096, ffma_tflops=None):
@@ -704,7 +721,7 @@ def measure_batched(n=4096, ffma_tflops=None):
     torch.cuda.empty_cache()
     out["batched_heuristic"] = tune.throughput(probs, "heuristic")
     T = tune.measure(probs, reps=2)
-    tuned = list(T.argmin(axis=1))
+    tuned = list(np.nanargmin(T, axis=1))
     out["batched_tuned"] = tune.throughput(probs, "table", configs=tuned)
     if os.path.exists(MODEL_PATH):
         tune.install(tune.load_model(MODEL_PATH))
@@ -712,16 +729,22 @@ def measure_batched(n=4096, ffma_tflops=None):
         gb.clear_model()
     out["speedup_batched_vs_per_call"] = out["per_call"]["ms"] / out["batched_heuristic"]["ms"]
     if ffma_tflops:
-        bw = measured_peaks().get("hbm_gbs", 6800.0) * 1e9
-        roof_s = 0.0
+        mp = measured_peaks()
+        bw = mp.get("hbm_gbs", 6800.0) * 1e9
+        bf16_peak = mp.get("bf16_tflops", 1900.0) * 1e12
+        roof_s = roof_dt = 0.0
         for pr in probs:
             esz = 2 if pr["dtype"] == "bf16" else 4
             nbytes = esz * (pr["la"].numel + pr["lb"].numel) + 8 * pr["lc"].numel
             roof_s += max(tune.flops(pr) / (ffma_tflops * 1e12), nbytes / bw)
+            peak = bf16_peak if pr["dtype"] == "bf16" else ffma_tflops * 1e12
+            roof_dt += max(tune.flops(pr) / peak, nbytes / bw)
         best = min(v["ms"] for k, v in out.items() if k.startswith("batched_"))
         out["roofline"] = {"ms": roof_s * 1e3, "frac_of_best": roof_s * 1e3 / best,
                            "definition": "sum over problems of max(flops / FFMA peak, bytes / HBM), "
-                                         "FFMA peak measured, HBM of MEASURED_PEAKS"}
+                                         "FFMA peak measured, HBM of MEASURED_PEAKS",
+                           "ms_bf16_on_tensor_peak": roof_dt * 1e3, "frac_of_best_bf16_on_tensor_peak":
+                           roof_dt * 1e3 / best}
     return out
 
 

@@ -66,7 +66,11 @@ typedef enum gett_batch_select {
     GETT_BATCH_SELECT_HEURISTIC = 0,  /* fixed rule on M, N, K                  */
     GETT_BATCH_SELECT_FIXED = 1,      /* every problem uses `config`            */
     GETT_BATCH_SELECT_TABLE = 2,      /* per-problem configs given in `configs` */
-    GETT_BATCH_SELECT_LEARNED = 3     /* the loaded MLP planner (gett_learn.h)  */
+    GETT_BATCH_SELECT_LEARNED = 3,    /* the loaded MLP planner (gett_learn.h),
+                                         then the tuning database, then the
+                                         heuristic                              */
+    GETT_BATCH_SELECT_TUNED = 4       /* the tuning database (gett_tune.h), then
+                                         the heuristic                          */
 } gett_batch_select;
 
 typedef struct gett_batch_options {
@@ -94,6 +98,7 @@ typedef struct gett_batch_info {
     int64_t packed_items;
     int64_t pack_items;
     int64_t skinny_items;
+    int tuned_hits;           /* problems configured by the tuning database */
 } gett_batch_info;
 
 /* Number of configurations, the tile shape of an id (0 x 0 for SKINNY) and
@@ -122,7 +127,7 @@ int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const int64_t *I
 /* Returns GETT_OK or the first failing problem's status; *bad_index (may be
  * NULL) receives that problem's index and gett_last_error_arg() its
  * argument position (1..14 as in gett.h; 0 for an unknown dtype).
- * GETT_ERR_ARG also for a NULL out, n < 0, SELECT_FIXED with a config
+ * GETT_ERR_ARG also for a NULL out, n < 0, an unknown select, SELECT_FIXED with a config
  * outside [0, gett_batch_num_configs()) or SELECT_TABLE without configs.
  * Validation touches no device; GETT_ERR_CUDA / GETT_ERR_NOMEM come from
  * the uploads that follow it.  GETT_ERR_UNSUPPORTED: a class of more than

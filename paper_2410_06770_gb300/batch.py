@@ -14,7 +14,7 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 _ip = ctypes.POINTER(ctypes.c_int)
 _fp = ctypes.POINTER(ctypes.c_float)
 
-SELECT = {"heuristic": 0, "fixed": 1, "table": 2, "learned": 3}
+SELECT = {"heuristic": 0, "fixed": 1, "table": 2, "learned": 3, "tuned": 4}
 
 
 class ProblemDesc(ctypes.Structure):
@@ -36,7 +36,7 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nonempty", ctypes.c_int), ("tiles", ctypes.c_int64),
                 ("flops", ctypes.c_double), ("config_count", ctypes.c_int * MAX_CONFIGS),
                 ("fallbacks", ctypes.c_int), ("gather_items", ctypes.c_int64), ("packed_items", ctypes.c_int64),
-                ("pack_items", ctypes.c_int64), ("skinny_items", ctypes.c_int64)]
+                ("pack_items", ctypes.c_int64), ("skinny_items", ctypes.c_int64), ("tuned_hits", ctypes.c_int)]
 
 
 _bound = False
@@ -151,7 +151,7 @@ class Batch:
         return {"n": i.n, "nonempty": i.nonempty, "tiles": i.tiles, "flops": i.flops,
                 "config_count": list(i.config_count), "fallbacks": i.fallbacks,
                 "gather_items": i.gather_items, "packed_items": i.packed_items, "pack_items": i.pack_items,
-                "skinny_items": i.skinny_items}
+                "skinny_items": i.skinny_items, "tuned_hits": i.tuned_hits}
 
     def close(self):
         if getattr(self, "h", None):

@@ -31,6 +31,8 @@
 #include "internal.h"
 #include "learn.h"
 #include "select.h"
+#include "gett_tune.h"
+#include "tunedb.h"
 
 namespace gett {
 
@@ -337,6 +339,7 @@ struct gett_batch {
     double flops = 0;
     int config_count[GETT_BATCH_MAX_CONFIGS] = {};
     int fallbacks = 0;
+    int tuned_hits = 0;
     int ctas = 0;
     int sms = 0;
     int cps = 4;  // gather kernel instantiation (resident CTAs per SM it is compiled for)
@@ -453,6 +456,7 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     *out = nullptr;
     gett_batch_options o{};
     if (opt) o = *opt;
+    if (o.select < GETT_BATCH_SELECT_HEURISTIC || o.select > GETT_BATCH_SELECT_TUNED) return GETT_ERR_ARG;
     if (o.select == GETT_BATCH_SELECT_FIXED && (o.config < 0 || o.config >= NCFG)) return GETT_ERR_ARG;
     if (o.select == GETT_BATCH_SELECT_TABLE && !o.configs) return GETT_ERR_ARG;
 
@@ -465,7 +469,7 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
         int idx;
     };
     std::vector<Span> cspans, inspans;
-    int fallbacks = 0;
+    int fallbacks = 0, tuned_hits = 0;
     for (int i = 0; i < n; ++i) {
         const gett_problem_desc &d = probs[i];
         if (d.dtype != GETT_BATCH_F32 && d.dtype != GETT_BATCH_BF16) {
@@ -506,6 +510,8 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
         cspans.push_back(span(d.C, p.c_lo, p.c_hi, 4, i));
         inspans.push_back(span(d.A, p.a_lo, p.a_hi, esz, i));
         inspans.push_back(span(d.B, p.b_lo, p.b_hi, esz, i));
+        // the choice chain: learned model -> tuning database -> heuristic
+        // (SELECT_LEARNED), database -> heuristic (SELECT_TUNED)
         int cfg = -1;
         if (o.select == GETT_BATCH_SELECT_FIXED) cfg = o.config;
         else if (o.select == GETT_BATCH_SELECT_TABLE) cfg = o.configs[i];
@@ -513,6 +519,14 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
             bool valid[NCFG];
             for (int c = 0; c < NCFG; ++c) valid[c] = batch_config_valid(c, p.M, p.N);
             cfg = learned_batch_config(p, d.dtype, NCFG, valid);
+        }
+        if ((o.select == GETT_BATCH_SELECT_TUNED || o.select == GETT_BATCH_SELECT_LEARNED) &&
+            !batch_config_valid(cfg, p.M, p.N)) {
+            int v0 = -1, v1 = 0, v2 = 0;
+            if (tune_db_lookup(GETT_TUNE_BATCH, d.dtype, p, &v0, &v1, &v2) && batch_config_valid(v0, p.M, p.N)) {
+                cfg = v0;
+                ++tuned_hits;
+            }
         }
         if (!batch_config_valid(cfg, p.M, p.N)) {
             if (o.select != GETT_BATCH_SELECT_HEURISTIC) ++fallbacks;
@@ -653,6 +667,7 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     b->n = n;
     b->nonempty = (int)hp.size();
     b->fallbacks = fallbacks;
+    b->tuned_hits = tuned_hits;
     b->sms = sms;
     std::vector<int64_t> tables((size_t)std::max<int64_t>(table_len, 1));
     // per-problem lists (grouped) and their costs
@@ -924,6 +939,7 @@ extern "C" int gett_batch_get_info(const gett_batch *b, gett_batch_info *info)
     info->packed_items = b->npacked;
     info->pack_items = b->npack;
     info->skinny_items = b->nskinny;
+    info->tuned_hits = b->tuned_hits;
     return GETT_OK;
 }
 

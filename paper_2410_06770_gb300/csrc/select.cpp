@@ -1,5 +1,9 @@
 // select.cpp -- which kernel family runs a planned contraction.
 //
+// Order: a caller's forced algorithm / family / configuration / split; else
+// an entry of the tuning database for the planned signature (gett_tune.h);
+// else the fixed heuristic below.
+//
 // Heuristic (the fixed planner every other selector falls back to):
 //  * K == 1 (no contracted extent > 1): OUTER streaming kernel;
 //  * at most 32 outputs and K >= 8192: REDUCE streaming kernel;
@@ -12,8 +16,10 @@
 //    SMs.
 #include <algorithm>
 
+#include "gett_tune.h"
 #include "kernels.h"
 #include "select.h"
+#include "tunedb.h"
 
 namespace gett {
 
@@ -100,9 +106,46 @@ Choice heuristic_choice(const Plan &p, DType t, int num_sms)
     return c;
 }
 
+// A tuning-database entry for single calls, if one exists and fits the
+// problem (gett_tune.h: v0 family, v1 configuration, v2 split_k).
+bool tuned_choice(const Plan &p, DType t, Choice *out)
+{
+    int fam = 0, cfg = 0, sk = 0;
+    if (!tune_db_lookup(GETT_TUNE_SINGLE, (int)t, p, &fam, &cfg, &sk)) return false;
+    Choice c;
+    c.family = fam;
+    c.config = cfg;
+    c.split_k = sk > 0 ? sk : 1;
+    c.selector = 1;
+    bool ok = false;
+    switch (fam) {
+    case GETT_FAMILY_DENSE: ok = dense_config_valid(t, cfg); break;
+    case GETT_FAMILY_OUTER: ok = p.K <= OUTER_MAX_SUM; break;
+    case GETT_FAMILY_SKINNY: ok = skinny_applicable(p); break;
+    case GETT_FAMILY_REDUCE: ok = p.M * p.N <= 4096; break;
+    case GETT_FAMILY_TC: ok = t == DT_BF16; c.algo = GETT_ALGO_NATIVE; break;
+    default: ok = false;
+    }
+    if (!ok) return false;
+    *out = c;
+    return true;
+}
+
 int choose(const Plan &p, DType t, const gett_options *opt, int num_sms, Choice *out)
 {
     Choice c = heuristic_choice(p, t, num_sms);
+    // tuned step of the chain: a database entry replaces the heuristic
+    // unless the caller forces an algorithm, family, configuration or split
+    const bool free_choice = !opt || ((opt->algo == GETT_ALGO_DEFAULT || opt->algo == GETT_ALGO_NATIVE) &&
+                                      opt->family == GETT_FAMILY_AUTO && opt->config < 0 && opt->split_k <= 0);
+    if (free_choice && !p.empty) {
+        Choice tc;
+        if (tuned_choice(p, t, &tc)) {
+            if (tc.family == GETT_FAMILY_DENSE) tc.split_k = dense_effective_split(p, tc.config, tc.split_k);
+            *out = tc;
+            return GETT_OK;
+        }
+    }
     if (opt && opt->algo == GETT_ALGO_OZAKI_BF16) {
         if (t != DT_F64 && t != DT_C64) return GETT_ERR_UNSUPPORTED;
         c = Choice{};

@@ -120,6 +120,17 @@ def lib():
     L.gett_ozaki_params.restype = ctypes.c_int
     L.gett_options_init.argtypes = [ctypes.POINTER(Options)]
     L.gett_options_init.restype = None
+    L.gett_tune_db_put.argtypes = [ctypes.c_int, ctypes.c_int] + _ARGS14[:3] + _ARGS14[4:7] + \
+        [ctypes.c_int, _ip, _ip, _ip, _i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.gett_tune_db_put.restype = ctypes.c_int
+    L.gett_tune_db_get.argtypes = [ctypes.c_int, ctypes.c_int] + _ARGS14[:3] + _ARGS14[4:7] + \
+        [ctypes.c_int, _ip, _ip, _ip, _i64p, _ip, _ip, _ip]
+    L.gett_tune_db_get.restype = ctypes.c_int
+    for n in ("gett_tune_db_clear", "gett_tune_db_size"):
+        getattr(L, n).restype = ctypes.c_int
+    for n in ("gett_tune_db_save", "gett_tune_db_load"):
+        getattr(L, n).argtypes = [ctypes.c_char_p]
+        getattr(L, n).restype = ctypes.c_int
     _lib = L
     return L
 
@@ -230,6 +241,52 @@ def ozaki_params(K: int, moduli: int = 0):
     mods = (ctypes.c_int * 20)()
     check(L.gett_ozaki_params(int(K), int(moduli), ctypes.byref(n), ctypes.byref(bits), mods))
     return n.value, bits.value, list(mods[: n.value])
+
+
+# ---------------------------------------------------------------------------
+# tuning database (gett_tune.h)
+# ---------------------------------------------------------------------------
+TUNE_BATCH, TUNE_SINGLE = 0, 1
+TUNE_DTYPE = {"s": 0, "d": 1, "c": 2, "z": 3, "sb": 4, "f32": 0, "bf16": 1}
+
+
+def _idx11(a: dict):
+    return [int(len(a["EXTA"])), _i64(a["EXTA"]), _i64(a["INCA"]), int(len(a["EXTB"])), _i64(a["EXTB"]),
+            _i64(a["INCB"]), int(len(a["CONTA"])), _i32(a["CONTA"]), _i32(a["CONTB"]), _i32(a["PERM"]),
+            _i64(a["INCC"])]
+
+
+def tune_db_put(kind: int, dtype, args: dict, v0: int, v1: int = 0, v2: int = 0) -> int:
+    """Record a tuned configuration for a problem (args: EXTA, INCA, EXTB,
+    INCB, CONTA, CONTB, PERM, INCC).  dtype: a TUNE_DTYPE key or its code."""
+    dt = TUNE_DTYPE[dtype] if isinstance(dtype, str) else int(dtype)
+    return check(lib().gett_tune_db_put(int(kind), dt, *_idx11(args), int(v0), int(v1), int(v2)))
+
+
+def tune_db_get(kind: int, dtype, args: dict):
+    """(v0, v1, v2) of the problem's entry, or None."""
+    dt = TUNE_DTYPE[dtype] if isinstance(dtype, str) else int(dtype)
+    v = [ctypes.c_int(0) for _ in range(3)]
+    st = lib().gett_tune_db_get(int(kind), dt, *_idx11(args), *[ctypes.byref(x) for x in v])
+    if st < 0:
+        check(st)
+    return tuple(x.value for x in v) if st == 1 else None
+
+
+def tune_db_clear():
+    lib().gett_tune_db_clear()
+
+
+def tune_db_size() -> int:
+    return lib().gett_tune_db_size()
+
+
+def tune_db_save(path: str):
+    check(lib().gett_tune_db_save(path.encode()))
+
+
+def tune_db_load(path: str):
+    check(lib().gett_tune_db_load(path.encode()))
 
 
 def last_error_arg() -> int:

@@ -1,6 +1,6 @@
 """Run one contraction of a named workload through the C ABI, for profilers.
 
-    python -m paper_2410_06770_gb300.profile_case WORKLOAD [SCALE] [--calls N] [--algo A]
+    python -m paper_2410_06770_gb300.profile_case WORKLOAD [SCALE] [--calls N] [--algo A] [--tuned]
 
 WORKLOAD: cc, cc_perm_transA (extents a..d = SCALE, i,j = SCALE/4), stream
 (A(SCALE, SCALE, 64) x B(64, 8)), small, gemv (A(SCALE, SCALE) x B(SCALE, 2),
@@ -9,6 +9,8 @@ mode contracted), transpose (xGETP of A(SCALE^4) with its modes reversed),
 batched (SCALE contractions of the batched workload, one
 persistent launch per call).  gemv and inner draw uniform values on the device.  Inputs are generated on the host,
 copied once, then the call is made N times (default 2) and synchronised.
+--tuned loads the package's tuning database first (the configuration the
+bench's calls use).
 """
 import argparse
 import sys
@@ -21,11 +23,16 @@ def main(argv=None):
     ap.add_argument("--calls", type=int, default=2)
     ap.add_argument("--algo", default="native")
     ap.add_argument("--prefix", default="d")
+    ap.add_argument("--tuned", action="store_true")
     args = ap.parse_args(argv)
+    import os
+
     import torch
 
     from . import build, gett, synth
     build.build()
+    if args.tuned:
+        gett.tune_db_load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_db.txt"))
     if args.workload == "batched":
         from . import batch as gb
         from . import tune

@@ -178,6 +178,74 @@ def install(model):
     gb.install_model(model["params"], model["mean"], model["std"], model["hidden"], model["nout"])
 
 
+def record_batch_db(probs, T):
+    """Tuning-database entries (kind GETT_TUNE_BATCH) of the exhaustive best
+    configuration of every measured problem."""
+    from . import gett
+    best = np.nanargmin(T, axis=1)
+    for pr, c in zip(probs, best):
+        gett.tune_db_put(gett.TUNE_BATCH, pr["dtype"], args_of(pr), int(c))
+
+
+def single_candidates(plan):
+    """Single-call configurations worth timing for a planned problem: every
+    dense tile configuration with split-K 1, 2, 4, 8, 16 (bounded by K), and
+    the streaming families the shape allows.  (family, config, split_k)."""
+    M, N, K = plan["M"], plan["N"], plan["K"]
+    out = [("dense", cfg, sk) for cfg in range(3) for sk in (1, 2, 4, 8, 16) if sk == 1 or K // sk >= 64]
+    if K <= 8:
+        out.append(("outer", 0, 1))
+    if min(M, N) <= 8:
+        out.append(("skinny", 0, 1))
+    if M * N <= 4096:
+        out.append(("reduce", 0, 1))
+    return out
+
+
+def tune_single(prefix, p, reps=5, record=True):
+    """Times every candidate configuration of one single call (xgett_ex with
+    the configuration forced, CUDA events, best of `reps` after a warm-up, C
+    accumulating in a scratch copy) and records the fastest in the tuning
+    database (kind GETT_TUNE_SINGLE).  Returns {candidate: ms} and the best."""
+    import torch
+    from . import gett
+    a = p.args()
+    st, plan = gett.plan_describe(a["RANKA"], a["EXTA"], a["INCA"], a["RANKB"], a["EXTB"], a["INCB"], a["CONTS"],
+                                  a["CONTA"], a["CONTB"], a["PERM"], a["INCC"])
+    gett.check(st)
+    dA, dB = torch.from_numpy(p.A).cuda(), torch.from_numpy(p.B).cuda()
+    dC = torch.zeros(p.lc.size, dtype=torch.float64, device="cuda") if p.meta.get("c_zero") \
+        else torch.from_numpy(p.C).cuda()
+    stream = torch.cuda.current_stream()
+    times = {}
+    for fam, cfg, sk in single_candidates(plan):
+        opts = gett.options(family=fam, config=cfg, split_k=sk)
+
+        def call():
+            return gett.xgett(prefix, a["RANKA"], a["EXTA"], a["INCA"], dA, a["RANKB"], a["EXTB"], a["INCB"], dB,
+                              a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], dC, a_off=p.la.off,
+                              b_off=p.lb.off, c_off=p.lc.off, mode="ex", opts=opts, stream=stream.cuda_stream,
+                              raise_on_error=False)[0]
+        if call() != gett.GETT_OK:
+            continue
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        times[(fam, cfg, sk)] = best
+    fam, cfg, sk = min(times, key=times.get)
+    if record:
+        gett.tune_db_put(gett.TUNE_SINGLE, prefix, dict(EXTA=a["EXTA"], INCA=a["INCA"], EXTB=a["EXTB"],
+                                                        INCB=a["INCB"], CONTA=a["CONTA"], CONTB=a["CONTB"],
+                                                        PERM=a["PERM"], INCC=a["INCC"]),
+                         gett.FAMILY[fam], cfg, sk)
+    return times, (fam, cfg, sk)
+
+
 def throughput(probs, select, configs=None, reps=10):
     """Contractions/s and TFLOP/s of one persistent launch (graph replay)."""
     import torch
@@ -211,7 +279,24 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--model", default=None)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--db", default=None, help="write the tuning database (exhaustive best of every measured "
+                                               "problem, and the single-call workloads with --single)")
+    ap.add_argument("--single", action="store_true",
+                    help="tune the single-call workloads (CC, its permuted / row-major-A variant, the small "
+                         "DGETT, the stream case) into the database and stop")
     args = ap.parse_args(argv)
+    if args.single:
+        from . import gett
+        rep = {}
+        for name, p in (("cc", synth.cfg_cc("plain")), ("cc_perm_transA", synth.cfg_cc("perm_transA")),
+                        ("small", synth.cfg_small_dgett()), ("stream", synth.cfg_stream(c_host=False))):
+            times, best = tune_single("d", p)
+            rep[name] = {"best": list(best), "ms": {f"{f}/{c}/{k}": t for (f, c, k), t in times.items()}}
+            print(f"{name}: {best} {times[best]:.3f} ms", file=sys.stderr, flush=True)
+        if args.db:
+            gett.tune_db_save(args.db)
+        print(json.dumps(rep))
+        return 0
     import torch
     t0 = time.time()
     log = lambda m: print(f"[{time.time() - t0:7.1f}s] {m}", file=sys.stderr, flush=True)
@@ -239,6 +324,11 @@ def main(argv=None):
     rep["throughput_learned"] = throughput(te, "learned")
     rep["throughput_heuristic"] = throughput(te, "heuristic")
     rep["throughput_tuned"] = throughput(te, "table", configs=list(tuned))
+    if args.db:
+        from . import gett
+        record_batch_db(tr + te, np.concatenate([Ttr, Tte]))
+        gett.tune_db_save(args.db)
+        rep["db_entries"] = gett.tune_db_size()
     rep["elapsed_s"] = time.time() - t0
     log(json.dumps(rep))
     if args.model:
