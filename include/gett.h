@@ -168,7 +168,13 @@ typedef enum gett_family {
     GETT_FAMILY_OUTER = 3,    /* streaming: no contracted extent > 1       */
     GETT_FAMILY_REDUCE = 4,   /* streaming: few outputs, long sums         */
     GETT_FAMILY_SKINNY = 5,   /* streaming: a free extent <= 8             */
-    GETT_FAMILY_TC = 6        /* tensor-core (tcgen05) GEMM on packed data */
+    GETT_FAMILY_TC = 6        /* tensor-core (tcgen05) GEMM: a bf16 operand */
+                              /* whose contracted modes fuse to one of      */
+                              /* increment 1 and whose free modes fuse to   */
+                              /* one with a pitch of whole 16 bytes (16-byte */
+                              /* aligned) is read in place by TMA; other    */
+                              /* operands, and the split forms' fp32 pieces, */
+                              /* are packed first                           */
 } gett_family;
 
 /* Conjugation of complex operands (an option of xGEMM-style interfaces; the
@@ -194,7 +200,9 @@ typedef struct gett_options {
 
 typedef struct gett_report {
     int family;      /* family that ran                                    */
-    int config;      /* configuration that ran                             */
+    int config;      /* configuration that ran; for GETT_FAMILY_TC without */
+                     /* the Ozaki form: bit 0 / bit 1 set when A / B was    */
+                     /* read in place by TMA (no packed copy)               */
     int split_k;
     int moduli;
     int nm, nn, nk;  /* modes per class after squeeze + fusion             */

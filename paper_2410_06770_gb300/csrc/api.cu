@@ -274,7 +274,9 @@ int run(DType t, const Args &a, const void *A, const void *B, void *C, const get
     }
     if (rep) {
         rep->family = ch.family;
-        rep->config = ch.config;
+        // tensor-core family: the configuration reports the in-place staging
+        rep->config = (ch.family == GETT_FAMILY_TC && ch.algo != GETT_ALGO_OZAKI_BF16)
+                          ? tc_in_place_mask(p, t, ch.algo, A, B) : ch.config;
         rep->split_k = ch.split_k;
         rep->moduli = ch.moduli;
         rep->selector = ch.selector;

@@ -285,7 +285,9 @@ bool make_map(CUtensorMap *map, const void *ptr, int64_t K, int64_t rows, int64_
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)Z};
-    cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(ld * 2 * rows)};
+    // the slice pitch matters only with several slices (a single slice never
+    // steps along z, and its pitch must still be a valid one)
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(Z > 1 ? ld * 2 * rows : ld * 2)};
     cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, estr,
@@ -305,8 +307,12 @@ cudaError_t launch_tc_gemm(int mode, const void *Ap, const void *Bp, int64_t Z, 
     if (Z > 65535 || (mode == TC_MODE_MOD && Z > OZ_MAX_L)) return cudaErrorInvalidValue;
     const int64_t ld = tc_ld(prm.K);
     if ((reinterpret_cast<uintptr_t>(Ap) | reinterpret_cast<uintptr_t>(Bp)) & 15) return cudaErrorInvalidValue;
+    // in-place operands: one slice, a pitch of whole 16-byte units
+    if ((prm.a_ld || prm.b_ld) && Z != 1) return cudaErrorInvalidValue;
+    if ((prm.a_ld & 7) || (prm.b_ld & 7) || prm.a_ld < 0 || prm.b_ld < 0) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Ap, prm.K, prm.M, ld, Z, BM) || !make_map(&mb, Bp, prm.K, prm.N, ld, Z, BN))
+    if (!make_map(&ma, Ap, prm.a_ld ? prm.a_kdim : prm.K, prm.M, prm.a_ld ? prm.a_ld : ld, Z, BM) ||
+        !make_map(&mb, Bp, prm.b_ld ? prm.b_kdim : prm.K, prm.N, prm.b_ld ? prm.b_ld : ld, Z, BN))
         return cudaErrorInvalidValue;
     TcGemmParams p = prm;
     p.tiles_m = (int)((p.M + BM - 1) / BM);

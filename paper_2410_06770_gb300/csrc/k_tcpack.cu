@@ -166,7 +166,34 @@ void pieces_for(int algo, bool is_a, PieceMap *pm)
     }
 }
 
+// In-place staging (TMA over the caller's tensor instead of a packed copy):
+// a bf16 operand whose contracted class is one mode of increment 1 and whose
+// row class is at most one mode with a positive increment of whole 16-byte
+// units, at a 16-byte-aligned address.  The planner has fused and flipped the
+// modes, so e.g. a column-major operand with its contracted modes first
+// qualifies.  *ld receives the row pitch in elements.
+bool stage_in_place(const ModeList &rows, const int64_t *row_inc, const ModeList &ks, const int64_t *k_inc,
+                    const void *base, int64_t K, int64_t *ld)
+{
+    if (ks.n != 1 || k_inc[0] != 1 || rows.n > 1) return false;
+    if (reinterpret_cast<uintptr_t>(base) & 15) return false;
+    const int64_t r = rows.n ? row_inc[0] : (K + 7) / 8 * 8;
+    if (r <= 0 || (r & 7)) return false;
+    *ld = r;
+    return true;
+}
+
 }  // namespace
+
+int tc_in_place_mask(const Plan &pl, DType t, int algo, const void *A, const void *B)
+{
+    if (t != DT_BF16 || algo == GETT_ALGO_BF16X3 || algo == GETT_ALGO_BF16X6) return 0;
+    int64_t ld = 0;
+    const char *Ab = static_cast<const char *>(A) + pl.offA * 2;
+    const char *Bb = static_cast<const char *>(B) + pl.offB * 2;
+    return (stage_in_place(pl.m, pl.m.s0, pl.k, pl.k.s0, Ab, pl.K, &ld) ? 1 : 0) |
+           (stage_in_place(pl.n, pl.n.s0, pl.k, pl.k.s1, Bb, pl.K, &ld) ? 2 : 0);
+}
 
 int tc_split_blocks(int algo)
 {
@@ -222,16 +249,23 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
         int64_t n = ((rows + TR - 1) / TR) * ((Kb + TKP - 1) / TKP);
         return (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * 8));
     };
+    // bf16 operands that TMA can read where they are skip the packing copy
+    // (their Inf / NaN then meet the tensor core's IEEE arithmetic directly)
+    int64_t a_ld = 0, b_ld = 0;
+    const bool a_direct = t == DT_BF16 && stage_in_place(pl.m, pl.m.s0, pl.k, pl.k.s0, Ab, pl.K, &a_ld);
+    const bool b_direct = t == DT_BF16 && stage_in_place(pl.n, pl.n.s0, pl.k, pl.k.s1, Bb, pl.K, &b_ld);
     if (t == DT_F32) {
         pack_pieces_kernel<float><<<blocks_for(pl.M), PT, 0, s>>>((const float *)Ab, rowA, kA, pl.M, pl.K,
                                                                    Kb, a_row_fast, pa, Ap, ld, flagA, any);
         pack_pieces_kernel<float><<<blocks_for(pl.N), PT, 0, s>>>((const float *)Bb, colB, kB, pl.N, pl.K,
                                                                    Kb, b_row_fast, pb, Bp, ld, flagB, any);
     } else {
-        pack_pieces_kernel<uint16_t><<<blocks_for(pl.M), PT, 0, s>>>((const uint16_t *)Ab, rowA, kA, pl.M, pl.K,
-                                                                      Kb, a_row_fast, pa, Ap, ld, flagA, any);
-        pack_pieces_kernel<uint16_t><<<blocks_for(pl.N), PT, 0, s>>>((const uint16_t *)Bb, colB, kB, pl.N, pl.K,
-                                                                      Kb, b_row_fast, pb, Bp, ld, flagB, any);
+        if (!a_direct)
+            pack_pieces_kernel<uint16_t><<<blocks_for(pl.M), PT, 0, s>>>((const uint16_t *)Ab, rowA, kA, pl.M, pl.K,
+                                                                          Kb, a_row_fast, pa, Ap, ld, flagA, any);
+        if (!b_direct)
+            pack_pieces_kernel<uint16_t><<<blocks_for(pl.N), PT, 0, s>>>((const uint16_t *)Bb, colB, kB, pl.N, pl.K,
+                                                                          Kb, b_row_fast, pb, Bp, ld, flagB, any);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -262,7 +296,16 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
     p.beta = (float)pl.sc.br;
     p.flagA = flagA;
     p.flagB = flagB;
-    e = launch_tc_gemm(TC_MODE_F32, Ap, Bp, 1, p, s);
+    if (a_direct) {
+        p.a_ld = a_ld;
+        p.a_kdim = pl.K;
+    }
+    if (b_direct) {
+        p.b_ld = b_ld;
+        p.b_kdim = pl.K;
+    }
+    e = launch_tc_gemm(TC_MODE_F32, a_direct ? static_cast<const void *>(Ab) : Ap,
+                       b_direct ? static_cast<const void *>(Bb) : Bp, 1, p, s);
     if (e != cudaSuccess) return e;
     const int fblocks = (int)std::max<int64_t>(1, std::min<int64_t>((pl.M * pl.N + 255) / 256, (int64_t)num_sms * 8));
     if (t == DT_F32)

@@ -58,6 +58,9 @@ cudaError_t launch_conj_pack(DType t, const void *src, const int64_t *rowT, cons
 // ---- tensor-core forms ----
 // s / bf16 inputs: packed bf16 pieces + one tcgen05 GEMM (k_tcpack.cu)
 int tc_split_blocks(int algo);
+// Which operands of a bf16 tensor-core call TMA reads in place (bit 0 A,
+// bit 1 B; the others are packed first).
+int tc_in_place_mask(const Plan &p, DType t, int algo, const void *A, const void *B);
 size_t tc_split_workspace_bytes(const Plan &p, int algo);
 cudaError_t launch_tc_split(const Plan &p, DType t, int algo, const void *A, const void *B, void *C, void *ws,
                             int num_sms, int *err, cudaStream_t s);

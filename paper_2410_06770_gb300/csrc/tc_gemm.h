@@ -35,6 +35,11 @@ struct TcGemmParams {
     // bf16 pieces cannot carry (Inf, NaN, or beyond the bf16 range); the
     // epilogue leaves their outputs to the non-finite fix-up kernel
     const uint32_t *flagA, *flagB;
+    // Operands staged in place (Z == 1): row pitch in elements of the
+    // caller's K-major bf16 operand, and its contracted extent (the tensor
+    // map's inner dimension; TMA fills k >= K with zeros).  0: packed
+    // operand with pitch tc_ld(K) and inner extent K.
+    int64_t a_ld, b_ld, a_kdim, b_kdim;
 };
 
 // Row pitch (elements) of a packed operand with K columns: multiple of 8

@@ -212,3 +212,41 @@ def test_ozaki_complex_thesis_families(family):
     r = synth.gather(p.lc, oracle_ref(p))
     nr = np.linalg.norm(r)
     assert np.linalg.norm(g - r) <= 1e-13 * (nr if nr else 1.0)
+
+
+def _explicit_problem(sig, inca, incb, seed):
+    """Integer-valued problem with explicit A / B increments, C contiguous."""
+    la = synth.layout_explicit(sig.exta, inca)
+    lb = synth.layout_explicit(sig.extb, incb)
+    lc = synth.layout_contiguous(sig.extc())
+    return synth.make_problem(sig, np.random.default_rng(seed), np.float64, "int", c_dist="int",
+                              layouts=(la, lb, lc))
+
+
+# (signature, INCA, INCB, expected in-place mask: bit 0 A, bit 1 B)
+IN_PLACE = [
+    # both K-major with 64-element pitches
+    (synth.Signature((64, 130), (64, 300), (0,), (0,), (0, 1)), (1, 64), (1, 64), 3),
+    # K = 70 (TMA fills k >= 70 with zeros) at pitches 72 and 80
+    (synth.Signature((70, 130), (70, 50), (0,), (0,), (1, 0)), (1, 72), (1, 80), 3),
+    # A row-major M x K is K-major too; two free modes of A fuse into one row mode
+    (synth.Signature((5, 7, 32), (32, 33), (2,), (0,), (1, 0, 2)), (224, 32, 1), (1, 40), 3),
+    # A M-major (packed), B K-major (in place)
+    (synth.Signature((130, 64), (64, 300), (1,), (0,), (0, 1)), (1, 130), (1, 64), 2),
+    # pitch 70 elements is not a whole number of 16-byte units: both packed
+    (synth.Signature((70, 30), (70, 20), (0,), (0,), (0, 1)), (1, 70), (1, 70), 0),
+    # two row modes that do not fuse (a gap between them): A packed
+    (synth.Signature((16, 5, 7), (16, 40), (0,), (0,), (0, 1, 2)), (1, 16, 96), (1, 16), 2),
+]
+
+
+@pytest.mark.parametrize("idx", range(len(IN_PLACE)))
+def test_bf16_in_place_staging(idx):
+    """bf16 operands read in place by TMA (no packed copy) where the planned
+    layout allows it, packed otherwise; integer data bit-exact either way."""
+    sig, inca, incb, mask = IN_PLACE[idx]
+    p = _explicit_problem(sig, inca, incb, 90 + idx)
+    q = problem_for("sb", p)
+    got, rep = run_gpu("sb", q, mode="ex", opts=gett.options(family="tc"))
+    assert rep["family_name"] == "tc" and rep["config"] == mask
+    compare("sb", q, got, oracle_ref(q), exact=True)
