@@ -27,6 +27,8 @@ typedef struct gett_peaks {
     double tc_bf16_tflops;       /* tcgen05.mma kind::f16, bf16 operands,  */
                                  /* 128 x 256 tiles, one CTA per SM        */
     double tc_e4m3_tflops;       /* tcgen05.mma kind::f8f6f4, e4m3 operands */
+    double fp64_mixed_tflops;    /* DMMA and DFMA warps side by side (do    */
+                                 /* the two FP64 paths add up?)             */
 } gett_peaks;
 
 /* Runs the microbenchmarks on the current device (synchronous; allocates

@@ -61,12 +61,150 @@ inline int batch_items(const BatchProb &pr)
 // operand): a K step then waits for one global round trip (the operands)
 // instead of two (the offset table, then the operands).
 constexpr int kStageK = 1536;
+constexpr int kGatherStages = 2;  // cp.async ring of the float gather tiles (double buffer)
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool valid)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gmem), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Gathered tile of float operands with the K offsets of its slice in shared
+// memory: every element's address comes from shared memory, so the tile is
+// staged by cp.async gathers (4 bytes each; an element outside the tile or
+// the slice is zero-filled) through a ring of kGatherStages buffers, with
+// kGatherStages - 1 K steps in flight and no registers holding them.  (bf16
+// operands cannot be gathered this way -- cp.async moves 4, 8 or 16 bytes --
+// and keep the register-staged tile.)  Same thread-to-output mapping,
+// summation order and epilogue as the register-staged tile.
+template <int CFG>
+__device__ __forceinline__ void gather_tile_async(const BatchProb &pr, const int64_t *tables, int item,
+                                                  float *smem_f, int64_t *smem_i, int64_t *skA, int64_t *skB)
+{
+    constexpr BCfg c = kB[CFG];
+    constexpr int BM = c.bm, BN = c.bn, BK = c.bk, TM = c.tm, TN = c.tn, S = kGatherStages;
+    constexpr int RM = BM / TM, RN = BN / TN, LA = BM * BK / BT, LB = BN * BK / BT;
+    const int tid = threadIdx.x;
+    const int tile = item / pr.splits, split = item % pr.splits;
+    const int tmi = tile / pr.tiles_n, tni = tile % pr.tiles_n;
+    const BatchTables t = batch_tables(pr, tables);
+    const int64_t m0 = (int64_t)tmi * BM, n0 = (int64_t)tni * BN;
+    const int64_t kbeg = (int64_t)split * pr.kps, kend = min(pr.K, kbeg + pr.kps), n = kend - kbeg;
+    int64_t *sRowA = smem_i, *sColB = smem_i + BM;
+    for (int64_t i = tid; i < n; i += BT) {
+        skA[i] = t.kA[kbeg + i];
+        skB[i] = t.kB[kbeg + i];
+    }
+    for (int i = tid; i < BM; i += BT) sRowA[i] = m0 + i < pr.M ? t.rowA[m0 + i] : 0;
+    for (int i = tid; i < BN; i += BT) sColB[i] = n0 + i < pr.N ? t.colB[n0 + i] : 0;
+    __syncthreads();
+    const float *A = static_cast<const float *>(pr.A);
+    const float *B = static_cast<const float *>(pr.B);
+    float *sA = smem_f, *sB = smem_f + S * BK * BM;
+    const int nkt = (int)((n + BK - 1) / BK);
+    auto issue = [&](int kt) {
+        const int st = kt % S;
+        const int64_t k0 = (int64_t)kt * BK;
+#pragma unroll
+        for (int r = 0; r < LA; ++r) {
+            const int e = tid + r * BT;
+            int mm, kk;
+            if (pr.a_m_fast) { mm = e % BM; kk = e / BM; }
+            else { kk = e % BK; mm = e / BK; }
+            const bool valid = m0 + mm < pr.M && k0 + kk < n;
+            cp_async4(&sA[(st * BK + kk) * BM + mm], valid ? A + sRowA[mm] + skA[k0 + kk] : A, valid);
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+            const int e = tid + r * BT;
+            int nn, kk;
+            if (pr.b_n_fast) { nn = e % BN; kk = e / BN; }
+            else { kk = e % BK; nn = e / BK; }
+            const bool valid = n0 + nn < pr.N && k0 + kk < n;
+            cp_async4(&sB[(st * BK + kk) * BN + nn], valid ? B + sColB[nn] + skB[k0 + kk] : B, valid);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int q = 0; q < S - 1; ++q) {
+        if (q < nkt) issue(q);
+        else cp_async_commit();  // empty groups keep the group count uniform
+    }
+    int tm, tn;
+    if (pr.c_m_fast) { tm = tid % RM; tn = tid / RM; }
+    else { tn = tid % RN; tm = tid / RN; }
+    float acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+    for (int kt = 0; kt < nkt; ++kt) {
+        cp_async_wait<S - 2>();
+        // stage kt has landed for every thread, and every thread has finished
+        // stage kt - 1, whose buffer the next issue refills
+        __syncthreads();
+        if (kt + S - 1 < nkt) issue(kt + S - 1);
+        else cp_async_commit();
+        const int cur = kt % S;
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = sA[(cur * BK + kk) * BM + tm + i * RM];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = sB[(cur * BK + kk) * BN + tn + j * RN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+    }
+    cp_async_wait<0>();
+    if (pr.splits > 1) {
+        float *P = pr.partial + (int64_t)split * pr.M * pr.N;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t m = m0 + tm + i * RM;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int64_t nn = n0 + tn + j * RN;
+                if (m < pr.M && nn < pr.N) P[pr.c_m_fast ? nn * pr.M + m : m * pr.N + nn] = acc[i][j];
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t m = m0 + tm + i * RM;
+        if (m >= pr.M) continue;
+        const int64_t rc = t.rowC[m];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int64_t nn = n0 + tn + j * RN;
+            if (nn < pr.N) {
+                float *dst = pr.C + rc + t.colC[nn];
+                *dst = *dst + acc[i][j];
+            }
+        }
+    }
+}
 
 template <class T, int CFG>
 __device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tables, int item, float *smem_f,
                                          int64_t *smem_i, int64_t *skA, int64_t *skB)
 {
     constexpr BCfg c = kB[CFG];
+    if constexpr (sizeof(T) == 4) {
+        // float operands: cp.async-staged gathers when the slice's K offsets fit
+        if (min(pr.K, (int64_t)(item % pr.splits) * pr.kps + pr.kps) - (int64_t)(item % pr.splits) * pr.kps <=
+            kStageK) {
+            gather_tile_async<CFG>(pr, tables, item, smem_f, smem_i, skA, skB);
+            return;
+        }
+    }
     const int tile = item / pr.splits, split = item % pr.splits;
     const int tm = tile / pr.tiles_n, tn = tile % pr.tiles_n;
     TileArgs a;
@@ -176,7 +314,7 @@ __device__ __forceinline__ void run_direct(const BatchProb &pr, const int64_t *t
 constexpr int smem_floats()
 {
     int m = 0;
-    for (int i = 0; i < NSHAPE; ++i) m = std::max(m, 2 * kB[i].bk * (kB[i].bm + kB[i].bn));
+    for (int i = 0; i < NSHAPE; ++i) m = std::max(m, kGatherStages * kB[i].bk * (kB[i].bm + kB[i].bn));
     return m;
 }
 constexpr int smem_ints()

@@ -77,6 +77,39 @@ __global__ void dmma_peak_kernel(double *out, int iters)
     if (s == -1.2345) out[threadIdx.x] = s;
 }
 
+// FP64 pipes side by side: even warps run the DMMA (m8n8k4) chains, odd warps
+// the DFMA chains, to see whether the two FP64 paths add up on this GPU.
+__global__ void fp64_mixed_kernel(double *out, int dmma_iters, int fma_iters)
+{
+    const int warp = threadIdx.x >> 5;
+    double s = 0;
+    if ((warp & 1) == 0) {
+        double a = 1.0 + 1e-9 * threadIdx.x, b = 0.5, c[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[j][0] = c[j][1] = 0.0;
+        for (int it = 0; it < dmma_iters; ++it) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                             : "+d"(c[j][0]), "+d"(c[j][1])
+                             : "d"(a), "d"(b));
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s += c[j][0] + c[j][1];
+    } else {
+        double acc[CHAINS];
+#pragma unroll
+        for (int c = 0; c < CHAINS; ++c) acc[c] = (double)(threadIdx.x + c);
+        for (int i = 0; i < fma_iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < CHAINS; ++c) acc[c] = acc[c] * 0.999 + 1e-3;
+        }
+#pragma unroll
+        for (int c = 0; c < CHAINS; ++c) s += acc[c];
+    }
+    if (s == -1.2345) out[threadIdx.x] = s;
+}
+
 // mma.sync s8 -> s32, m16n8k32: four independent accumulators a warp
 __global__ void imma_peak_kernel(int *out, int iters)
 {
@@ -232,6 +265,19 @@ extern "C" int gett_measure_peaks(gett_peaks *out, size_t copy_bytes)
     {
         float ms = best_ms([&] { dmma_peak_kernel<2><<<blocks, threads>>>(scratch, dit); }, 5);
         out->dmma_m16n8k8_tflops = 4.0 * dit * warps * (2.0 * 16 * 8 * 8) / (ms * 1e-3) / 1e12;
+    }
+    {
+        // the two FP64 paths together: half the warps each; the DMMA half's
+        // flops are scaled by the measured rate ratio so that, if the paths
+        // are independent, both halves take the same time.  A warp's DFMA
+        // work is 32 * 2 * CHAINS * fit flops, its DMMA work 4 * dmi * 512
+        const double ratio = out->dfma_tflops > 0 ? out->dmma_m8n8k4_tflops / out->dfma_tflops : 1.0;
+        const int fit = iters;
+        const int dmi = (int)std::max(1.0, fit * ratio * (32.0 * 2.0 * CHAINS) / (4.0 * 2.0 * 8 * 8 * 4));
+        float ms = best_ms([&] { fp64_mixed_kernel<<<blocks, threads>>>(scratch, dmi, fit); }, 5);
+        const double half_warps = warps / 2.0;
+        const double flops = half_warps * 4.0 * dmi * (2.0 * 8 * 8 * 4) + half_warps * 32.0 * 2.0 * CHAINS * fit;
+        out->fp64_mixed_tflops = flops / (ms * 1e-3) / 1e12;
     }
     {
         float ms = best_ms([&] { imma_peak_kernel<<<blocks, threads>>>((int *)scratch, dit); }, 5);

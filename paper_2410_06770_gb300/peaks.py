@@ -9,7 +9,7 @@ class _Peaks(ctypes.Structure):
                 ("dmma_m16n8k4_tflops", ctypes.c_double), ("dmma_m16n8k8_tflops", ctypes.c_double),
                 ("ffma_tflops", ctypes.c_double), ("copy_gbs", ctypes.c_double), ("sms", ctypes.c_int),
                 ("imma_s8_tops", ctypes.c_double), ("tc_bf16_tflops", ctypes.c_double),
-                ("tc_e4m3_tflops", ctypes.c_double)]
+                ("tc_e4m3_tflops", ctypes.c_double), ("fp64_mixed_tflops", ctypes.c_double)]
 
 
 def measure(copy_bytes: int = 1 << 30) -> dict:
