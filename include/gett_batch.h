@@ -9,10 +9,12 @@
  * and a tile shape, below), uploads one descriptor table, one offset-table
  * buffer and the work lists, and returns an opaque handle.
  * gett_batch_launch enqueues the whole batch as one fixed sequence of
- * persistent kernels on one stream -- packing of the packed problems'
+ * persistent kernels on one stream -- packing of the tensor-core problems'
+ * operands, their tensor-core tiles, packing of the packed problems'
  * operands, packed tiles, gathered tiles and short sums, skinny warp items,
- * the ordered addition of K-slice partials -- with tiles taken from atomic
- * work counters; gett_batch_launch_graph does the same through a CUDA graph
+ * the ordered addition of K-slice partials -- with the tiles of the
+ * gathered kernel taken from an atomic work counter and the others dealt to
+ * the CTAs statically; gett_batch_launch_graph does the same through a CUDA graph
  * captured on first use and replayed afterwards.
  *
  * Configurations (gett_batch_num_configs() of them):
@@ -25,7 +27,10 @@
  *         into one contiguous index; bf16 widened to float), which the tiles
  *         then stream with bulk copies;
  *   8     SKINNY: for a problem with a free class of at most 8 indices;
- *         warp items along the long class or along the sum.
+ *         warp items along the long class or along the sum;
+ *   9     TC: for bf16 operands; A and B are packed into 128 x 64 tiles laid
+ *         out as the tensor core reads them and multiplied by tcgen05 into
+ *         128 x 128 float tiles (fp32 accumulation in TMEM).
  * gett_batch_config_shape and gett_batch_config_method describe an id.
  *
  * Ownership: the EXT/INC/CONT/PERM arrays are read during create only; the
@@ -99,6 +104,8 @@ typedef struct gett_batch_info {
     int64_t pack_items;
     int64_t skinny_items;
     int tuned_hits;           /* problems configured by the tuning database */
+    int64_t tc_items;         /* tensor-core output tiles of one launch     */
+    int64_t tc_pack_items;    /* their packing items (128 x 64 tiles)       */
 } gett_batch_info;
 
 /* Number of configurations, the tile shape of an id (0 x 0 for SKINNY) and
@@ -106,23 +113,25 @@ typedef struct gett_batch_info {
 int gett_batch_num_configs(void);
 int gett_batch_config_shape(int config, int *bm, int *bn);
 int gett_batch_config_method(int config);
-/* 1 if `config` can run the problem (14 xGETT arguments without pointers),
- * 0 if not (SKINNY without a free class of at most 8 indices), or a
- * negative status for invalid arguments.  Host only.  A table or learned
- * choice that is not valid is replaced by the heuristic's (a fallback). */
+/* 1 if `config` can run the problem (14 xGETT arguments without pointers,
+ * dtype a gett_batch_dtype), 0 if not (SKINNY without a free class of at
+ * most 8 indices, TC with float operands), or a negative status for invalid
+ * arguments.  Host only.  A table or learned choice that is not valid is
+ * replaced by the heuristic's (a fallback). */
 int gett_batch_config_valid(int RANKA, const int64_t *EXTA, const int64_t *INCA,
                             int RANKB, const int64_t *EXTB, const int64_t *INCB,
                             int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
-                            const int64_t *INCC, int config);
+                            const int64_t *INCC, int dtype, int config);
 
 /* The fixed heuristic's configuration for one problem (14 xGETT arguments
- * without pointers) -- the fallback of the other selectors: sums of at most
- * 8 terms GATHER (direct), a free class of at most 8 indices SKINNY,
- * everything else PACK; the shape follows M and N. */
+ * without pointers, dtype a gett_batch_dtype) -- the fallback of the other
+ * selectors: sums of at most 8 terms GATHER (direct), a free class of at
+ * most 8 indices SKINNY, bf16 operands with M, N >= 128 and K >= 256 TC, everything
+ * else PACK; the shape follows M and N. */
 int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const int64_t *INCA,
                                 int RANKB, const int64_t *EXTB, const int64_t *INCB,
                                 int CONTS, const int *CONTA, const int *CONTB, const int *PERM,
-                                const int64_t *INCC, int *config);
+                                const int64_t *INCC, int dtype, int *config);
 
 /* Returns GETT_OK or the first failing problem's status; *bad_index (may be
  * NULL) receives that problem's index and gett_last_error_arg() its

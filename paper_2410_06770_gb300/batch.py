@@ -36,7 +36,8 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nonempty", ctypes.c_int), ("tiles", ctypes.c_int64),
                 ("flops", ctypes.c_double), ("config_count", ctypes.c_int * MAX_CONFIGS),
                 ("fallbacks", ctypes.c_int), ("gather_items", ctypes.c_int64), ("packed_items", ctypes.c_int64),
-                ("pack_items", ctypes.c_int64), ("skinny_items", ctypes.c_int64), ("tuned_hits", ctypes.c_int)]
+                ("pack_items", ctypes.c_int64), ("skinny_items", ctypes.c_int64), ("tuned_hits", ctypes.c_int),
+                ("tc_items", ctypes.c_int64), ("tc_pack_items", ctypes.c_int64)]
 
 
 _bound = False
@@ -59,12 +60,12 @@ def _bind():
     L.gett_batch_profile.restype = ctypes.c_int
     L.gett_batch_num_configs.restype = ctypes.c_int
     L.gett_batch_heuristic_config.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
-                                              ctypes.c_int, _ip, _ip, _ip, _i64p, _ip]
+                                              ctypes.c_int, _ip, _ip, _ip, _i64p, ctypes.c_int, _ip]
     L.gett_batch_config_shape.argtypes = [ctypes.c_int, _ip, _ip]
     L.gett_batch_config_method.argtypes = [ctypes.c_int]
     L.gett_batch_config_method.restype = ctypes.c_int
     L.gett_batch_config_valid.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
-                                          ctypes.c_int, _ip, _ip, _ip, _i64p, ctypes.c_int]
+                                          ctypes.c_int, _ip, _ip, _ip, _i64p, ctypes.c_int, ctypes.c_int]
     L.gett_batch_config_valid.restype = ctypes.c_int
     L.gett_problem_features.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _i64p, _i64p,
                                         ctypes.c_int, _ip, _ip, _ip, _i64p, ctypes.c_int, _fp]
@@ -151,7 +152,8 @@ class Batch:
         return {"n": i.n, "nonempty": i.nonempty, "tiles": i.tiles, "flops": i.flops,
                 "config_count": list(i.config_count), "fallbacks": i.fallbacks,
                 "gather_items": i.gather_items, "packed_items": i.packed_items, "pack_items": i.pack_items,
-                "skinny_items": i.skinny_items, "tuned_hits": i.tuned_hits}
+                "skinny_items": i.skinny_items, "tuned_hits": i.tuned_hits, "tc_items": i.tc_items,
+                "tc_pack_items": i.tc_pack_items}
 
     def close(self):
         if getattr(self, "h", None):
@@ -169,27 +171,32 @@ def num_configs() -> int:
     return _bind().gett_batch_num_configs()
 
 
-def heuristic_config(args: dict) -> int:
+def _dtype_code(dtype) -> int:
+    return 1 if dtype in ("bf16", 1) else 0
+
+
+def heuristic_config(args: dict, dtype="f32") -> int:
     L = _bind()
     c = ctypes.c_int(0)
     gett.check(L.gett_batch_heuristic_config(len(args["EXTA"]), gett._i64(args["EXTA"]), gett._i64(args["INCA"]),
                                              len(args["EXTB"]), gett._i64(args["EXTB"]), gett._i64(args["INCB"]),
                                              len(args["CONTA"]), gett._i32(args["CONTA"]), gett._i32(args["CONTB"]),
-                                             gett._i32(args["PERM"]), gett._i64(args["INCC"]), ctypes.byref(c)))
+                                             gett._i32(args["PERM"]), gett._i64(args["INCC"]), _dtype_code(dtype),
+                                             ctypes.byref(c)))
     return c.value
 
 
 def config_method(config: int) -> int:
-    """0 GATHER, 1 PACK, 2 SKINNY."""
+    """0 GATHER, 1 PACK, 2 SKINNY, 3 TC."""
     return _bind().gett_batch_config_method(int(config))
 
 
-def config_valid(args: dict, config: int) -> bool:
+def config_valid(args: dict, config: int, dtype="f32") -> bool:
     L = _bind()
     st = L.gett_batch_config_valid(len(args["EXTA"]), gett._i64(args["EXTA"]), gett._i64(args["INCA"]),
                                    len(args["EXTB"]), gett._i64(args["EXTB"]), gett._i64(args["INCB"]),
                                    len(args["CONTA"]), gett._i32(args["CONTA"]), gett._i32(args["CONTB"]),
-                                   gett._i32(args["PERM"]), gett._i64(args["INCC"]), int(config))
+                                   gett._i32(args["PERM"]), gett._i64(args["INCC"]), _dtype_code(dtype), int(config))
     if st < 0:
         gett.check(st)
     return st == 1

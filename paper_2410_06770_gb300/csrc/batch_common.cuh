@@ -27,13 +27,23 @@ constexpr BCfg kB[NSHAPE] = {{64, 64, 16, 4, 4}, {32, 64, 16, 2, 4}, {32, 32, 16
 //         index, [K][bm] blocks of A, [K][bn] of B), then the tiles stream
 //         them with bulk copies;
 //   8     SKINNY: one free class of at most 8 indices; warp items, lanes
-//         along the long free class or along the sum.
-enum BatchMethod : int { BM_GATHER = 0, BM_PACK = 1, BM_SKINNY = 2 };
-constexpr int NCFG = 2 * NSHAPE + 1;
+//         along the long free class or along the sum;
+//   9     TC (bf16 operands only): packed into 128 x 64 bf16 tiles laid out
+//         as the tensor core reads them, multiplied by tcgen05 (128 x 128
+//         output tiles, fp32 accumulators in TMEM).
+enum BatchMethod : int { BM_GATHER = 0, BM_PACK = 1, BM_SKINNY = 2, BM_TC = 3 };
+constexpr int NCFG = 2 * NSHAPE + 2;
 constexpr int CFG_SKINNY = 2 * NSHAPE;
+constexpr int CFG_TC = 2 * NSHAPE + 1;
 constexpr int SKINNY_MAX_SHORT = 8;
+// tensor-core method: output tile, K tile (one 128-byte swizzled row of bf16)
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;
+constexpr int TC_TILE_ELEMS = 128 * TC_BK;  // one packed 128 x 64 tile
 
-__host__ __device__ constexpr int cfg_method(int cfg) { return cfg >= CFG_SKINNY ? BM_SKINNY : cfg / NSHAPE; }
+__host__ __device__ constexpr int cfg_method(int cfg)
+{
+    return cfg == CFG_TC ? BM_TC : (cfg == CFG_SKINNY ? BM_SKINNY : cfg / NSHAPE);
+}
 __host__ __device__ constexpr int cfg_shape(int cfg) { return cfg >= CFG_SKINNY ? 0 : cfg % NSHAPE; }
 
 struct BatchProb {
@@ -59,6 +69,10 @@ struct BatchProb {
     // lanes_k: lanes run along the sum (L, S <= 4), else along the long class
     int long_is_a, lanes_k;
     int64_t kslice;   // contracted indices per warp item
+    // TC: packed bf16 tiles, tile (t, kt) of A at tA + (t * nkt + kt) *
+    // TC_TILE_ELEMS (B the same with tB), nkt = K tiles of 64
+    const uint16_t *tA, *tB;
+    int nkt;
 };
 
 // Offset tables of problem pr: rowA, rowC [M], colB, colC [N], kA, kB [K].
@@ -99,5 +113,16 @@ void launch_batch_skinny(int blocks, cudaStream_t s, const BatchProb *probs, con
                          int64_t wrap, const int64_t *tables);
 // Resident CTAs per SM of the packed tile kernel (shared-memory bound).
 int batch_packed_ctas_per_sm();
+
+// Tensor-core method (k_batch_tc.cu).  Packing items: problem, operand,
+// 128-row block, K tile of 64 (one packed tile).  Tile kernel: one CTA per
+// SM, items (problem, 128 x 128 output tile) dealt statically.
+struct TcPackItem {
+    int prob, operand, block, ktile;
+};
+void launch_batch_tc_pack(int blocks, cudaStream_t s, const BatchProb *probs, const TcPackItem *items, int64_t n,
+                          int64_t wrap, const int64_t *tables);
+cudaError_t launch_batch_tc_tiles(int ctas, cudaStream_t s, const BatchProb *probs, const uint2 *work, int64_t nwork,
+                                  int64_t wrap, const int64_t *tables, int *err);
 
 }  // namespace gett

@@ -449,20 +449,24 @@ int batch_shape_rule(int64_t M, int64_t N)
 
 bool batch_skinny_shape(int64_t M, int64_t N) { return std::min(M, N) <= SKINNY_MAX_SHORT; }
 
-int batch_heuristic_config(int64_t M, int64_t N, int64_t K)
+int batch_heuristic_config(int64_t M, int64_t N, int64_t K, int dtype)
 {
     const int shape = batch_shape_rule(M, N);
     if (K <= 8) return shape;
     if (batch_skinny_shape(M, N)) return CFG_SKINNY;
+    if (dtype == GETT_BATCH_BF16 && K >= 256 && M >= 128 && N >= 128) return CFG_TC;
     return NSHAPE + shape;
 }
 
 // A configuration is valid for a problem unless it asks for the skinny
-// kernel on a problem without a free class of at most 8 indices.
-bool batch_config_valid(int cfg, int64_t M, int64_t N)
+// kernel on a problem without a free class of at most 8 indices, or for the
+// tensor cores with float operands.
+bool batch_config_valid(int cfg, int64_t M, int64_t N, int dtype)
 {
     if (cfg < 0 || cfg >= NCFG) return false;
-    return cfg != CFG_SKINNY || batch_skinny_shape(M, N);
+    if (cfg == CFG_SKINNY) return batch_skinny_shape(M, N);
+    if (cfg == CFG_TC) return dtype == GETT_BATCH_BF16;
+    return true;
 }
 
 }  // namespace gett
@@ -487,6 +491,11 @@ struct gett_batch {
     gett::PackItem *d_pack = nullptr;
     gett::SkinnyItem *d_skinny = nullptr;
     gett::SkinnyItem *d_skinny_by_problem = nullptr;
+    uint2 *d_tc_work = nullptr;              // tensor-core tiles (sorted)
+    uint2 *d_tc_work_by_problem = nullptr;
+    gett::TcPackItem *d_tc_pack = nullptr;   // their packing items (grouped by problem)
+    uint16_t *d_tiles16 = nullptr;           // packed bf16 tiles of the TC method
+    int64_t ntc = 0, ntcpack = 0;
     int64_t *d_tables = nullptr;
     float *d_packed = nullptr;           // tile-blocked operands of packed problems
     unsigned long long *d_counter = nullptr;  // work counter of the gather kernel (and one spare)
@@ -500,6 +509,7 @@ struct gett_batch {
     std::vector<int> reduce_of;          // per user index: descriptor index if split, else -1
     // per user index: start and count in each by-problem list
     std::vector<int64_t> gw_start, gw_count, pw_start, pw_count, pk_start, pk_count, sk_start, sk_count;
+    std::vector<int64_t> tw_start, tw_count, tk_start, tk_count;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap = nullptr;
@@ -526,7 +536,8 @@ extern "C" int gett_batch_config_method(int config)
 
 extern "C" int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const int64_t *INCA, int RANKB,
                                            const int64_t *EXTB, const int64_t *INCB, int CONTS, const int *CONTA,
-                                           const int *CONTB, const int *PERM, const int64_t *INCC, int *config)
+                                           const int *CONTB, const int *PERM, const int64_t *INCC, int dtype,
+                                           int *config)
 {
     if (!config) return GETT_ERR_ARG;
     Args a{RANKA, EXTA, INCA, RANKB, EXTB, INCB, CONTS, CONTA, CONTB, PERM, INCC};
@@ -535,13 +546,13 @@ extern "C" int gett_batch_heuristic_config(int RANKA, const int64_t *EXTA, const
     int rc = make_plan(a, &p, &bad);
     set_last_error_arg(bad);
     if (rc != GETT_OK) return rc;
-    *config = p.empty ? 0 : batch_heuristic_config(p.M, p.N, p.K);
+    *config = p.empty ? 0 : batch_heuristic_config(p.M, p.N, p.K, dtype);
     return GETT_OK;
 }
 
 extern "C" int gett_batch_config_valid(int RANKA, const int64_t *EXTA, const int64_t *INCA, int RANKB,
                                        const int64_t *EXTB, const int64_t *INCB, int CONTS, const int *CONTA,
-                                       const int *CONTB, const int *PERM, const int64_t *INCC, int config)
+                                       const int *CONTB, const int *PERM, const int64_t *INCC, int dtype, int config)
 {
     Args a{RANKA, EXTA, INCA, RANKB, EXTB, INCB, CONTS, CONTA, CONTB, PERM, INCC};
     Plan p;
@@ -549,7 +560,7 @@ extern "C" int gett_batch_config_valid(int RANKA, const int64_t *EXTA, const int
     int rc = make_plan(a, &p, &bad);
     set_last_error_arg(bad);
     if (rc != GETT_OK) return rc;
-    return batch_config_valid(config, p.M, p.N) ? 1 : 0;
+    return batch_config_valid(config, p.M, p.N, dtype) ? 1 : 0;
 }
 
 namespace {
@@ -561,6 +572,7 @@ namespace {
 constexpr int64_t kMaxClassIndices = (int64_t)1 << 31;
 constexpr int64_t kMaxTableEntries = (int64_t)1 << 31;
 constexpr int64_t kMaxPackedFloats = (int64_t)1 << 30;
+constexpr int64_t kMaxTcElems = (int64_t)1 << 30;  // bf16 tiles of the TC method (2 GB)
 constexpr int64_t kSkinnyLaneSlice = 256;   // K per warp item, lanes along the long class
 constexpr int64_t kSkinnySumSlice = 2048;   // K per warp item, lanes along the sum
 
@@ -655,20 +667,21 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
         else if (o.select == GETT_BATCH_SELECT_TABLE) cfg = o.configs[i];
         else if (o.select == GETT_BATCH_SELECT_LEARNED) {
             bool valid[NCFG];
-            for (int c = 0; c < NCFG; ++c) valid[c] = batch_config_valid(c, p.M, p.N);
+            for (int c = 0; c < NCFG; ++c) valid[c] = batch_config_valid(c, p.M, p.N, d.dtype);
             cfg = learned_batch_config(p, d.dtype, NCFG, valid);
         }
         if ((o.select == GETT_BATCH_SELECT_TUNED || o.select == GETT_BATCH_SELECT_LEARNED) &&
-            !batch_config_valid(cfg, p.M, p.N)) {
+            !batch_config_valid(cfg, p.M, p.N, d.dtype)) {
             int v0 = -1, v1 = 0, v2 = 0;
-            if (tune_db_lookup(GETT_TUNE_BATCH, d.dtype, p, &v0, &v1, &v2) && batch_config_valid(v0, p.M, p.N)) {
+            if (tune_db_lookup(GETT_TUNE_BATCH, d.dtype, p, &v0, &v1, &v2) &&
+                batch_config_valid(v0, p.M, p.N, d.dtype)) {
                 cfg = v0;
                 ++tuned_hits;
             }
         }
-        if (!batch_config_valid(cfg, p.M, p.N)) {
+        if (!batch_config_valid(cfg, p.M, p.N, d.dtype)) {
             if (o.select != GETT_BATCH_SELECT_HEURISTIC) ++fallbacks;
-            cfg = batch_heuristic_config(p.M, p.N, p.K);
+            cfg = batch_heuristic_config(p.M, p.N, p.K, d.dtype);
         }
         BatchProb b{};
         b.A = static_cast<const char *>(d.A) + p.offA * (int64_t)esz;
@@ -686,7 +699,8 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
         // short sums take the gathered direct path whatever the tile method
         b.method = (p.K <= 8 && cfg_method(cfg) == BM_PACK) ? BM_GATHER : cfg_method(cfg);
         {
-            const int64_t tm = (p.M + b.bm - 1) / b.bm, tn = (p.N + b.bn - 1) / b.bn;
+            const int tbm = b.method == BM_TC ? TC_BM : b.bm, tbn = b.method == BM_TC ? TC_BN : b.bn;
+            const int64_t tm = (p.M + tbm - 1) / tbm, tn = (p.N + tbn - 1) / tbn;
             if (tm * tn > (int64_t)INT32_MAX) {  // M, N <= 2^31 each: the product fits int64
                 set_last_error_arg(0);
                 if (bad_index) *bad_index = i;
@@ -746,13 +760,33 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     constexpr int64_t kMaxSteps = 96, kMaxSplits = 512;  // kMaxSteps * BK <= kStageK
     double total_cost = 0;
     for (const BatchProb &pr : hp)
-        if (pr.method != BM_SKINNY) total_cost += (double)pr.tiles_m * pr.tiles_n * pr.bm * pr.bn * (double)pr.K;
+        if (pr.method != BM_SKINNY && pr.method != BM_TC)
+            total_cost += (double)pr.tiles_m * pr.tiles_n * pr.bm * pr.bn * (double)pr.K;
     const double target = std::max(total_cost / (2.0 * ctas), 1.0);
-    int64_t partial_floats = 0, packed_floats = 0;
-    std::vector<int64_t> partial_off(hp.size(), -1), packed_off(hp.size(), -1);
+    int64_t partial_floats = 0, packed_floats = 0, tc_elems = 0;
+    std::vector<int64_t> partial_off(hp.size(), -1), packed_off(hp.size(), -1), tc_off(hp.size(), -1);
     for (size_t j = 0; j < hp.size(); ++j) {
         BatchProb &pr = hp[j];
         int64_t S = 1, kps = pr.K;
+        if (pr.method == BM_TC) {
+            // one slice (the tensor cores make long sums short); 128 x 64 tiles
+            pr.nkt = (int)((pr.K + TC_BK - 1) / TC_BK);
+            const int64_t ea = (int64_t)pr.tiles_m * pr.nkt * TC_TILE_ELEMS;
+            const int64_t eb = (int64_t)pr.tiles_n * pr.nkt * TC_TILE_ELEMS;
+            if (tc_elems + ea + eb > kMaxTcElems) {
+                // the tile buffer is full: gather this one instead
+                pr.method = BM_GATHER;
+                pr.tiles_m = (int)((pr.M + pr.bm - 1) / pr.bm);
+                pr.tiles_n = (int)((pr.N + pr.bn - 1) / pr.bn);
+            } else {
+                tc_off[j] = tc_elems;
+                tc_elems += ea + eb;
+                pr.splits = 1;
+                pr.kps = pr.K;
+                pr.tpi = 1;
+                continue;
+            }
+        }
         if (pr.method == BM_SKINNY) {
             const int64_t L = std::max(pr.M, pr.N), Sh = std::min(pr.M, pr.N);
             pr.long_is_a = pr.M >= pr.N ? 1 : 0;
@@ -809,14 +843,17 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     b->sms = sms;
     std::vector<int64_t> tables((size_t)std::max<int64_t>(table_len, 1));
     // per-problem lists (grouped) and their costs
-    std::vector<uint2> gwork, pwork;
+    std::vector<uint2> gwork, pwork, twork;
     std::vector<PackItem> pack;
+    std::vector<TcPackItem> tpack;
     std::vector<SkinnyItem> skinny;
-    std::vector<double> gcost, pcost, scost;
+    std::vector<double> gcost, pcost, scost, tcost;
     b->gw_start.assign(n, 0); b->gw_count.assign(n, 0);
     b->pw_start.assign(n, 0); b->pw_count.assign(n, 0);
     b->pk_start.assign(n, 0); b->pk_count.assign(n, 0);
     b->sk_start.assign(n, 0); b->sk_count.assign(n, 0);
+    b->tw_start.assign(n, 0); b->tw_count.assign(n, 0);
+    b->tk_start.assign(n, 0); b->tk_count.assign(n, 0);
     for (size_t j = 0; j < hp.size(); ++j) {
         const Plan &p = plans[hp_index[j]];
         BatchProb &pr = hp[j];
@@ -852,6 +889,21 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
                     for (int ch = 0; ch < chunks; ++ch) pack.push_back(PackItem{(int)j, op, bl, ch});
             }
             b->pk_count[ui] = (int64_t)pack.size() - b->pk_start[ui];
+        } else if (pr.method == BM_TC) {
+            b->tw_start[ui] = (int64_t)twork.size();
+            const int nitems = pr.tiles_m * pr.tiles_n;
+            for (int tt = 0; tt < nitems; ++tt) {
+                twork.push_back(make_uint2((unsigned)j, (unsigned)tt));
+                tcost.push_back((double)pr.nkt);
+            }
+            b->tw_count[ui] = nitems;
+            b->tk_start[ui] = (int64_t)tpack.size();
+            for (int op = 0; op < 2; ++op) {
+                const int blocks = op == 0 ? pr.tiles_m : pr.tiles_n;
+                for (int bl = 0; bl < blocks; ++bl)
+                    for (int kt = 0; kt < pr.nkt; ++kt) tpack.push_back(TcPackItem{(int)j, op, bl, kt});
+            }
+            b->tk_count[ui] = (int64_t)tpack.size() - b->tk_start[ui];
         } else {
             b->sk_start[ui] = (int64_t)skinny.size();
             const int64_t L = std::max(pr.M, pr.N);
@@ -874,6 +926,9 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     b->nreduce = (int)reduce_list.size();
     const std::vector<uint2> gsorted = by_cost(gwork, gcost), psorted = by_cost(pwork, pcost);
     const std::vector<SkinnyItem> ssorted = by_cost(skinny, scost);
+    const std::vector<uint2> tsorted = by_cost(twork, tcost);
+    b->ntc = (int64_t)tsorted.size();
+    b->ntcpack = (int64_t)tpack.size();
     b->nwork = (int64_t)gsorted.size();
     b->npacked = (int64_t)psorted.size();
     b->npack = (int64_t)pack.size();
@@ -883,6 +938,13 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
 
     e = cudaMalloc(&b->d_partial, sizeof(float) * (size_t)std::max<int64_t>(partial_floats, 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_packed, sizeof(float) * (size_t)std::max<int64_t>(packed_floats, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles16, sizeof(uint16_t) * (size_t)std::max<int64_t>(tc_elems, 1));
+    if (e == cudaSuccess)
+        for (size_t j = 0; j < hp.size(); ++j)
+            if (tc_off[j] >= 0) {
+                hp[j].tA = b->d_tiles16 + tc_off[j];
+                hp[j].tB = b->d_tiles16 + tc_off[j] + (int64_t)hp[j].tiles_m * hp[j].nkt * TC_TILE_ELEMS;
+            }
     if (e == cudaSuccess)
         for (size_t j = 0; j < hp.size(); ++j) {
             hp[j].partial = partial_off[j] >= 0 ? b->d_partial + partial_off[j] : nullptr;
@@ -901,6 +963,9 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     if (e == cudaSuccess) e = upload(&b->d_work_by_problem, gwork);
     if (e == cudaSuccess) e = upload(&b->d_packed_by_problem, pwork);
     if (e == cudaSuccess) e = upload(&b->d_skinny_by_problem, skinny);
+    if (e == cudaSuccess) e = upload(&b->d_tc_work, tsorted);
+    if (e == cudaSuccess) e = upload(&b->d_tc_work_by_problem, twork);
+    if (e == cudaSuccess) e = upload(&b->d_tc_pack, tpack);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) b->d_err = device_error_word();
     if (e == cudaSuccess && !b->d_err) e = cudaErrorInitializationError;
@@ -945,6 +1010,10 @@ struct Ranges {
     const int *red;
     int nred;
     int64_t copies;
+    const uint2 *tw;
+    int64_t tn;
+    const TcPackItem *tk;
+    int64_t tkn;
 };
 
 cudaError_t enqueue_ranges(gett_batch *b, const Ranges &r, cudaStream_t s)
@@ -958,6 +1027,14 @@ cudaError_t enqueue_ranges(gett_batch *b, const Ranges &r, cudaStream_t s)
     if (r.kn > 0)
         launch_batch_pack((int)std::min<int64_t>(r.kn * c, (int64_t)b->sms * 8), s, b->d_probs, r.pk, r.kn * c, r.kn,
                           b->d_tables);
+    if (r.tkn > 0)
+        launch_batch_tc_pack((int)std::min<int64_t>(r.tkn * c, (int64_t)b->sms * 8), s, b->d_probs, r.tk, r.tkn * c,
+                             r.tkn, b->d_tables);
+    if (r.tn > 0) {
+        const cudaError_t te = launch_batch_tc_tiles((int)std::min<int64_t>(b->sms, r.tn * c), s, b->d_probs, r.tw,
+                                                     r.tn * c, r.tn, b->d_tables, b->d_err);
+        if (te != cudaSuccess) return te;
+    }
     if (r.pn > 0) {
         const int ctas = (int)std::min<int64_t>((int64_t)b->sms * batch_packed_ctas_per_sm(), r.pn * c);
         launch_batch_packed_tiles(batch_packed_ctas_per_sm(), ctas, s, b->d_probs, r.pw, r.pn * c, r.pn, b->d_tables,
@@ -980,7 +1057,8 @@ cudaError_t enqueue_ranges(gett_batch *b, const Ranges &r, cudaStream_t s)
 static cudaError_t enqueue(gett_batch *b, cudaStream_t s)
 {
     const Ranges r{b->d_work, b->nwork, b->d_packed_work, b->npacked, b->d_pack, b->npack,
-                   b->d_skinny, b->nskinny, b->d_reduce, b->nreduce, 1};
+                   b->d_skinny, b->nskinny, b->d_reduce, b->nreduce, 1,
+                   b->d_tc_work, b->ntc, b->d_tc_pack, b->ntcpack};
     return enqueue_ranges(b, r, s);
 }
 
@@ -1031,19 +1109,22 @@ extern "C" int gett_batch_profile(gett_batch *b, int reps, int mode, float *ms_o
     cudaEventCreate(&e1);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         ms_out[i] = 0.f;
-        const int64_t cnt = b->gw_count[i] + b->pw_count[i] + b->sk_count[i];
+        const int64_t cnt = b->gw_count[i] + b->pw_count[i] + b->sk_count[i] + b->tw_count[i];
         if (cnt == 0) continue;
         // throughput mode: enough copies of the problem's items to give every
-        // persistent CTA (skinny: every warp) several, so the time reflects
-        // its cost in a full GPU
-        const int64_t slots = b->sk_count[i] > 0 ? (int64_t)b->sms * 32 : (int64_t)b->ctas;
+        // persistent CTA (skinny: every warp; tensor cores: every SM) several,
+        // so the time reflects its cost in a full GPU
+        const int64_t slots = b->sk_count[i] > 0 ? (int64_t)b->sms * 32
+                              : (b->tw_count[i] > 0 ? (int64_t)b->sms : (int64_t)b->ctas);
         const int64_t copies = mode == 1 ? std::min<int64_t>(64, std::max<int64_t>(1, (4 * slots + cnt - 1) / cnt)) : 1;
         const int red = b->reduce_of[i];
         const Ranges r{b->d_work_by_problem + b->gw_start[i], b->gw_count[i],
                        b->d_packed_by_problem + b->pw_start[i], b->pw_count[i],
                        b->d_pack + b->pk_start[i], b->pk_count[i],
                        b->d_skinny_by_problem + b->sk_start[i], b->sk_count[i],
-                       red >= 0 ? b->d_reduce + red : nullptr, red >= 0 ? 1 : 0, copies};
+                       red >= 0 ? b->d_reduce + red : nullptr, red >= 0 ? 1 : 0, copies,
+                       b->d_tc_work_by_problem + b->tw_start[i], b->tw_count[i],
+                       b->d_tc_pack + b->tk_start[i], b->tk_count[i]};
         e = enqueue_ranges(b, r, s);  // warm-up
         cudaEventRecord(e0, s);
         for (int rr = 0; rr < reps && e == cudaSuccess; ++rr) e = enqueue_ranges(b, r, s);
@@ -1069,7 +1150,7 @@ extern "C" int gett_batch_get_info(const gett_batch *b, gett_batch_info *info)
     std::memset(info, 0, sizeof(*info));
     info->n = b->n;
     info->nonempty = b->nonempty;
-    info->tiles = b->nwork + b->npacked + b->nskinny;
+    info->tiles = b->nwork + b->npacked + b->nskinny + b->ntc;
     info->flops = b->flops;
     for (int i = 0; i < GETT_BATCH_MAX_CONFIGS; ++i) info->config_count[i] = b->config_count[i];
     info->fallbacks = b->fallbacks;
@@ -1078,6 +1159,8 @@ extern "C" int gett_batch_get_info(const gett_batch *b, gett_batch_info *info)
     info->pack_items = b->npack;
     info->skinny_items = b->nskinny;
     info->tuned_hits = b->tuned_hits;
+    info->tc_items = b->ntc;
+    info->tc_pack_items = b->ntcpack;
     return GETT_OK;
 }
 
@@ -1089,7 +1172,8 @@ extern "C" int gett_batch_destroy(gett_batch *b)
     if (b->cap) cudaStreamDestroy(b->cap);
     void *bufs[] = {b->d_probs, b->d_work, b->d_packed_work, b->d_pack, b->d_skinny, b->d_skinny_by_problem,
                     b->d_tables, b->d_packed, b->d_counter, b->d_work_by_problem, b->d_packed_by_problem,
-                    b->d_partial, b->d_reduce};
+                    b->d_partial, b->d_reduce, b->d_tc_work, b->d_tc_work_by_problem, b->d_tc_pack,
+                    b->d_tiles16};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete b;

@@ -95,9 +95,9 @@ class DeviceBuffers:
 
 def valid_mask(probs):
     """valid[i][c]: configuration c can run problem i (SKINNY needs a free
-    class of at most 8 indices)."""
+    class of at most 8 indices, TC bf16 operands)."""
     nc = gb.num_configs()
-    return np.array([[gb.config_valid(args_of(pr), c) for c in range(nc)] for pr in probs], dtype=bool)
+    return np.array([[gb.config_valid(args_of(pr), c, pr["dtype"]) for c in range(nc)] for pr in probs], dtype=bool)
 
 
 def measure(probs, reps=3, chunk=1024, log=None):
@@ -310,7 +310,7 @@ def main(argv=None):
     model = train(Xtr, Ttr, epochs=args.epochs)
     log(f"trained, final loss {model['final_loss']:.4f}")
     pred, finite = predict_configs(model, Xte, np.isfinite(Tte))
-    heur = np.array([gb.heuristic_config(args_of(pr)) for pr in te])
+    heur = np.array([gb.heuristic_config(args_of(pr), pr["dtype"]) for pr in te])
     tuned = np.nanargmin(Tte, axis=1)
     pred_used = np.where(finite, pred, heur)
     rep = {

@@ -84,7 +84,7 @@ def check_all(probs, dev, times=1):
         assert np.all(np.abs(g - r) <= 2.0 * (K + 2) * times * 2.0 ** -24 * bound + 1e-30)
 
 
-@pytest.mark.parametrize("select,config", [("heuristic", 0)] + [("fixed", c) for c in range(9)])
+@pytest.mark.parametrize("select,config", [("heuristic", 0)] + [("fixed", c) for c in range(10)])
 def test_batch_matches_oracle(select, config):
     import torch
     probs = make_batch_problems(150, 1 + config)
@@ -94,6 +94,9 @@ def test_batch_matches_oracle(select, config):
     assert info["n"] == 150 and info["tiles"] > 0
     if select == "fixed" and gb.config_method(config) == 1:
         assert info["packed_items"] > 0 and info["pack_items"] > 0
+    if select == "fixed" and gb.config_method(config) == 3:
+        # the bf16 problems run on the tensor cores, the float ones fall back
+        assert info["tc_items"] > 0 and info["tc_pack_items"] > 0 and info["fallbacks"] > 0
     if select == "heuristic":
         assert info["packed_items"] > 0 and info["gather_items"] > 0
     b.launch()
@@ -126,8 +129,44 @@ def test_skinny_heavy_batch(select):
 
 
 def test_config_descriptions():
-    assert gb.num_configs() == 9
-    assert [gb.config_method(c) for c in range(9)] == [0] * 4 + [1] * 4 + [2]
+    assert gb.num_configs() == 10
+    assert [gb.config_method(c) for c in range(10)] == [0] * 4 + [1] * 4 + [2, 3]
+
+
+def make_tc_problems(n, seed):
+    """bf16 problems for the tensor-core method: ragged M, N, K over several
+    128 x 128 tiles and 64-wide K tiles (K from 1 to a few hundred), random
+    layouts and output permutations."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for i in range(n):
+        m, nn, k1 = int(rng.integers(1, 300)), int(rng.integers(1, 300)), int(rng.integers(1, 40))
+        k2 = int(rng.integers(1, 12))
+        if i % 2:
+            sig = synth.Signature((m, k1, k2), (k2, nn, k1), (1, 2), (2, 0), (1, 0))
+        else:
+            sig = synth.Signature((k1, m), (nn, k1), (0,), (1,), (0, 1))
+        kinds = tuple(rng.choice(["contig", "padded", "rowmajor", "negative"], 3))
+        p = synth.make_problem(sig, rng, np.float64, "uniform", kinds, "uniform")
+        probs.append(("sb", problem_for("sb", p)))
+    return probs
+
+
+def test_tensor_core_method_matches_oracle():
+    """The TC method: bf16 problems packed into swizzled 128 x 64 tiles and
+    multiplied by tcgen05 in one grouped launch, graph-replayed twice
+    (accumulating), element by element against the oracle."""
+    import torch
+    probs = make_tc_problems(40, 41)
+    dev, descs = upload_all(probs)
+    b = gb.Batch(descs, select="fixed", config=9)
+    info = b.info()
+    assert info["tc_items"] > 0 and info["config_count"][9] == 40 and info["fallbacks"] == 0
+    b.launch(graph=True)
+    b.launch(graph=True)
+    torch.cuda.synchronize()
+    check_all(probs, dev, times=2)
+    b.close()
 
 
 @pytest.mark.parametrize("ctas_per_sm", [1, 3, 4, 6])
