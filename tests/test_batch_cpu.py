@@ -150,3 +150,17 @@ def test_broadcast_class_beyond_the_table_limit():
     descs = [desc(0), desc(1, EXTA=(8, big), INCA=(1, 0), EXTB=(big, 6), INCB=(0, 5))]
     e = rejected(descs)
     assert e.status == gett.GETT_ERR_UNSUPPORTED and e.bad_index == 1
+
+
+def test_shipped_planner_model_matches_the_configuration_space():
+    """The trained planner weights beside the package predict one score per
+    batched configuration the library offers (a stale file from a smaller
+    configuration space would be refused by install_model at run time)."""
+    import os
+    from paper_2410_06770_gb300 import tune
+    path = os.path.join(os.path.dirname(gb.__file__), "planner_mlp.npz")
+    model = tune.load_model(path)
+    assert model["nout"] == gb.num_configs()
+    assert model["mean"].shape == model["std"].shape == (24,)
+    h, n = model["hidden"], model["nout"]
+    assert model["params"].size == (24 * h + h) + (h * h + h) + (h * n + n)
