@@ -726,6 +726,8 @@ def measure_batched(n=4096, ffma_tflops=None):
     if os.path.exists(MODEL_PATH):
         tune.install(tune.load_model(MODEL_PATH))
         out["batched_learned"] = tune.throughput(probs, "learned")
+        # the same launch with every kernel on one stream (no concurrent branches)
+        out["batched_learned_serial"] = tune.throughput(probs, "learned", serial=True)
         gb.clear_model()
     out["speedup_batched_vs_per_call"] = out["per_call"]["ms"] / out["batched_heuristic"]["ms"]
     if ffma_tflops:

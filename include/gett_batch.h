@@ -38,8 +38,10 @@
  * C must be injective (the same sufficient test as single calls), and the C
  * of one problem may overlap neither another problem's C nor any problem's A
  * or B (address ranges; GETT_ERR_ALIAS).  Operands may be shared.
- * Launches of one handle are stream ordered; concurrent launches of the same
- * handle on different streams race on its work counter.
+ * Launches of one handle are stream ordered (a launch's internal branches
+ * wait for the work enqueued before it and the launch stream waits for them);
+ * concurrent launches of the same handle on different streams race on its
+ * work counter and its branch streams.
  */
 #ifndef GETT_BATCH_H
 #define GETT_BATCH_H
@@ -86,6 +88,13 @@ typedef struct gett_batch_options {
                                  4 use kernels compiled for 2, 3 and 4
                                  resident CTAs (128, 80, 64 registers a
                                  thread), more than 4 the 4 one            */
+    int serial;               /* 0: the independent method chains of a launch
+                                 (packing + packed tiles, tensor-core packing
+                                 + tiles, gathered tiles, skinny items) run
+                                 as concurrent branches on internal streams
+                                 forked from and joined back into the
+                                 launch stream before the reduction; 1: all
+                                 kernels in order on the launch stream      */
 } gett_batch_options;
 
 typedef struct gett_batch gett_batch;

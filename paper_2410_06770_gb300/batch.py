@@ -26,7 +26,7 @@ class ProblemDesc(ctypes.Structure):
 
 class BatchOptions(ctypes.Structure):
     _fields_ = [("select", ctypes.c_int), ("config", ctypes.c_int), ("configs", _ip),
-                ("ctas_per_sm", ctypes.c_int)]
+                ("ctas_per_sm", ctypes.c_int), ("serial", ctypes.c_int)]
 
 
 MAX_CONFIGS = 16
@@ -92,7 +92,8 @@ def _f(a: np.ndarray):
 class Batch:
     """One planned batch of contractions (float C; float or bf16 A/B)."""
 
-    def __init__(self, problems: Sequence[dict], select="heuristic", config=0, configs=None, ctas_per_sm=0):
+    def __init__(self, problems: Sequence[dict], select="heuristic", config=0, configs=None, ctas_per_sm=0,
+                 serial=False):
         L = _bind()
         self._keep = []
         n = len(problems)
@@ -122,6 +123,7 @@ class Batch:
             self._keep.append(ca)
             o.configs = ctypes.cast(ca, _ip)
         o.ctas_per_sm = int(ctas_per_sm)
+        o.serial = int(serial)  # 0/1 (bool); other values are rejected by the library
         h = ctypes.c_void_p()
         bad = ctypes.c_int(-1)
         st = L.gett_batch_create(n, arr, ctypes.byref(o), ctypes.byref(h), ctypes.byref(bad))

@@ -513,6 +513,13 @@ struct gett_batch {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap = nullptr;
+    // concurrent branches of a launch: the method chains other than the
+    // packed one run on these streams, forked from and joined back into the
+    // launch stream (created with the handle unless `serial`)
+    bool serial = false;
+    cudaStream_t branch[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
 };
 
 using namespace gett;
@@ -609,6 +616,7 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     if (o.select < GETT_BATCH_SELECT_HEURISTIC || o.select > GETT_BATCH_SELECT_TUNED) return GETT_ERR_ARG;
     if (o.select == GETT_BATCH_SELECT_FIXED && (o.config < 0 || o.config >= NCFG)) return GETT_ERR_ARG;
     if (o.select == GETT_BATCH_SELECT_TABLE && !o.configs) return GETT_ERR_ARG;
+    if (o.serial != 0 && o.serial != 1) return GETT_ERR_ARG;
 
     std::vector<Plan> plans(n);
     std::vector<BatchProb> hp;
@@ -967,6 +975,14 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     if (e == cudaSuccess) e = upload(&b->d_tc_work_by_problem, twork);
     if (e == cudaSuccess) e = upload(&b->d_tc_pack, tpack);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 2 * sizeof(unsigned long long));
+    b->serial = o.serial != 0;
+    if (e == cudaSuccess && !b->serial) {
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+        }
+    }
     if (e == cudaSuccess) b->d_err = device_error_word();
     if (e == cudaSuccess && !b->d_err) e = cudaErrorInitializationError;
     if (e != cudaSuccess) {
@@ -1016,24 +1032,49 @@ struct Ranges {
     int64_t tkn;
 };
 
-cudaError_t enqueue_ranges(gett_batch *b, const Ranges &r, cudaStream_t s)
+// The method chains of a launch touch disjoint outputs (every problem runs
+// one method, and problems' C regions do not overlap) and disjoint
+// workspaces, so they are independent: (1) packing + packed tiles,
+// (2) tensor-core packing + tensor-core tiles, (3) gathered tiles and short
+// sums, (4) skinny warp items.  The ordered reduction of K-slice partials
+// runs after all of them.  Unless the handle is serial, chains 2-4 run on
+// branch streams that wait for an event recorded on the launch stream, and
+// the launch stream waits for each branch's join event before the
+// reduction; the same calls build a forked graph under stream capture.
+// Each chain's kernels are persistent and sized to the whole GPU, so a
+// branch mostly fills the SMs the others leave idle (ramps, tails,
+// latency-bound stretches).
+cudaError_t enqueue_ranges(gett_batch *b, const Ranges &r, cudaStream_t s, bool concurrent)
 {
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int64_t c = r.copies;
-    // 1. pack the operands of packed problems, 2. their tiles, 3. gathered
-    // tiles and short sums, 4. skinny warp items, 5. the ordered reduction of
-    // K-slice partials
+    const bool has[3] = {r.tkn > 0 || r.tn > 0, r.gn > 0, r.sn > 0};
+    const bool fork = concurrent && b->fork;
+    cudaStream_t bs[3] = {s, s, s};
+    if (fork) {
+        e = cudaEventRecord(b->fork, s);
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            if (has[i]) {
+                bs[i] = b->branch[i];
+                e = cudaStreamWaitEvent(bs[i], b->fork, 0);
+            }
+        if (e != cudaSuccess) return e;
+    }
+    // issue order as in a serial launch: packing (chain 1), tensor-core
+    // packing and tiles (chain 2), packed tiles (chain 1), gathered tiles
+    // (chain 3; its work counter was reset on the launch stream before the
+    // fork), skinny items (chain 4)
     if (r.kn > 0)
         launch_batch_pack((int)std::min<int64_t>(r.kn * c, (int64_t)b->sms * 8), s, b->d_probs, r.pk, r.kn * c, r.kn,
                           b->d_tables);
     if (r.tkn > 0)
-        launch_batch_tc_pack((int)std::min<int64_t>(r.tkn * c, (int64_t)b->sms * 8), s, b->d_probs, r.tk, r.tkn * c,
-                             r.tkn, b->d_tables);
+        launch_batch_tc_pack((int)std::min<int64_t>(r.tkn * c, (int64_t)b->sms * 8), bs[0], b->d_probs, r.tk,
+                             r.tkn * c, r.tkn, b->d_tables);
     if (r.tn > 0) {
-        const cudaError_t te = launch_batch_tc_tiles((int)std::min<int64_t>(b->sms, r.tn * c), s, b->d_probs, r.tw,
-                                                     r.tn * c, r.tn, b->d_tables, b->d_err);
-        if (te != cudaSuccess) return te;
+        e = launch_batch_tc_tiles((int)std::min<int64_t>(b->sms, r.tn * c), bs[0], b->d_probs, r.tw, r.tn * c,
+                                  r.tn, b->d_tables, b->d_err);
+        if (e != cudaSuccess) return e;
     }
     if (r.pn > 0) {
         const int ctas = (int)std::min<int64_t>((int64_t)b->sms * batch_packed_ctas_per_sm(), r.pn * c);
@@ -1042,11 +1083,21 @@ cudaError_t enqueue_ranges(gett_batch *b, const Ranges &r, cudaStream_t s)
     }
     if (r.gn > 0) {
         const int ctas = (int)std::min<int64_t>(b->ctas, r.gn * c);
-        launch_batch_kernel(b->cps, ctas, s, b->d_probs, r.gw, r.gn * c, r.gn, b->d_tables, b->d_counter);
+        launch_batch_kernel(b->cps, ctas, bs[1], b->d_probs, r.gw, r.gn * c, r.gn, b->d_tables, b->d_counter);
     }
     if (r.sn > 0)
-        launch_batch_skinny((int)std::min<int64_t>((r.sn * c + 7) / 8, (int64_t)b->sms * 4), s, b->d_probs, r.sk,
+        launch_batch_skinny((int)std::min<int64_t>((r.sn * c + 7) / 8, (int64_t)b->sms * 4), bs[2], b->d_probs, r.sk,
                             r.sn * c, r.sn, b->d_tables);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (fork) {
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            if (has[i]) {
+                e = cudaEventRecord(b->join[i], bs[i]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[i], 0);
+            }
+        if (e != cudaSuccess) return e;
+    }
     if (r.nred > 0)
         batch_reduce_kernel<<<std::min(r.nred, b->ctas), 256, 0, s>>>(b->d_probs, r.red, r.nred, b->d_tables);
     return cudaGetLastError();
@@ -1059,7 +1110,7 @@ static cudaError_t enqueue(gett_batch *b, cudaStream_t s)
     const Ranges r{b->d_work, b->nwork, b->d_packed_work, b->npacked, b->d_pack, b->npack,
                    b->d_skinny, b->nskinny, b->d_reduce, b->nreduce, 1,
                    b->d_tc_work, b->ntc, b->d_tc_pack, b->ntcpack};
-    return enqueue_ranges(b, r, s);
+    return enqueue_ranges(b, r, s, !b->serial);
 }
 
 extern "C" int gett_batch_launch(gett_batch *b, void *stream)
@@ -1125,9 +1176,11 @@ extern "C" int gett_batch_profile(gett_batch *b, int reps, int mode, float *ms_o
                        red >= 0 ? b->d_reduce + red : nullptr, red >= 0 ? 1 : 0, copies,
                        b->d_tc_work_by_problem + b->tw_start[i], b->tw_count[i],
                        b->d_tc_pack + b->tk_start[i], b->tk_count[i]};
-        e = enqueue_ranges(b, r, s);  // warm-up
+        // one problem runs one method: its chain needs no branch streams (and
+        // every configuration is timed on the same single stream)
+        e = enqueue_ranges(b, r, s, false);  // warm-up
         cudaEventRecord(e0, s);
-        for (int rr = 0; rr < reps && e == cudaSuccess; ++rr) e = enqueue_ranges(b, r, s);
+        for (int rr = 0; rr < reps && e == cudaSuccess; ++rr) e = enqueue_ranges(b, r, s, false);
         cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -1170,6 +1223,11 @@ extern "C" int gett_batch_destroy(gett_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (int i = 0; i < 3; ++i) {
+        if (b->branch[i]) cudaStreamDestroy(b->branch[i]);
+        if (b->join[i]) cudaEventDestroy(b->join[i]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     void *bufs[] = {b->d_probs, b->d_work, b->d_packed_work, b->d_pack, b->d_skinny, b->d_skinny_by_problem,
                     b->d_tables, b->d_packed, b->d_counter, b->d_work_by_problem, b->d_packed_by_problem,
                     b->d_partial, b->d_reduce, b->d_tc_work, b->d_tc_work_by_problem, b->d_tc_pack,

@@ -246,11 +246,12 @@ def tune_single(prefix, p, reps=5, record=True):
     return times, (fam, cfg, sk)
 
 
-def throughput(probs, select, configs=None, reps=10):
-    """Contractions/s and TFLOP/s of one persistent launch (graph replay)."""
+def throughput(probs, select, configs=None, reps=10, serial=False):
+    """Contractions/s and TFLOP/s of one batched launch (graph replay; the
+    method chains as concurrent branches unless serial)."""
     import torch
     bufs = DeviceBuffers(probs)
-    b = gb.Batch(bufs.descs, select=select, configs=configs)
+    b = gb.Batch(bufs.descs, select=select, configs=configs, serial=serial)
     info = b.info()
     stream = torch.cuda.current_stream()
     for _ in range(3):

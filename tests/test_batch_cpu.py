@@ -139,6 +139,7 @@ def test_selection_options_validated():
     assert rejected(descs, select="fixed", config=gb.num_configs()).status == gett.GETT_ERR_ARG
     assert rejected(descs, select="fixed", config=-1).status == gett.GETT_ERR_ARG
     assert rejected(descs, select="table", configs=None).status == gett.GETT_ERR_ARG
+    assert rejected(descs, serial=2).status == gett.GETT_ERR_ARG
 
 
 def test_broadcast_class_beyond_the_table_limit():

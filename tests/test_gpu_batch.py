@@ -209,6 +209,41 @@ def test_batch_deterministic():
         assert np.array_equal(x, y)
 
 
+def test_concurrent_branches_match_serial_launch():
+    """A batch that uses every method (gathered, packed, skinny, tensor-core
+    tiles, K-slice reduction): its method chains run as concurrent branches
+    forked from the launch stream, eagerly and graph-captured, on a side
+    stream whose earlier work (zeroing every C) they must wait for; the
+    results equal the single-stream launch bit for bit and the oracle."""
+    import torch
+    probs = (make_batch_problems(60, 71) + make_skinny_problems(30, 72) + make_tc_problems(20, 73))
+    outs = {}
+    for mode in ("serial", "eager", "graph"):
+        dev, descs = upload_all(probs)
+        # heuristic choices, and the tensor cores for the bf16 problems
+        configs = [-1] * 90 + [9] * 20
+        b = gb.Batch(descs, select="table", configs=configs, serial=(mode == "serial"))
+        info = b.info()
+        assert min(info["gather_items"], info["packed_items"], info["skinny_items"], info["tc_items"]) > 0
+        side = torch.cuda.Stream()
+        saved = [dC.clone() for (_, _, dC) in dev]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            # queued first on the launch stream: C <- 0, then C <- saved C;
+            # a branch that ran ahead of these would see the zeros or race them
+            for (_, _, dC), c0 in zip(dev, saved):
+                dC.zero_()
+                torch.cuda._sleep(20000)
+                dC.copy_(c0)
+            b.launch(stream=side.cuda_stream, graph=(mode == "graph"))
+        side.synchronize()
+        outs[mode] = [download(dC, np.float32).copy() for (_, _, dC) in dev]
+        check_all(probs, dev)
+        b.close()
+    for x, y, z in zip(outs["serial"], outs["eager"], outs["graph"]):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+
+
 def test_batch_rejects_overlapping_outputs():
     import torch
     probs = make_batch_problems(2, 11)
