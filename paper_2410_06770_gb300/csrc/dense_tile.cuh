@@ -153,13 +153,38 @@ __device__ __forceinline__ void dense_tile(const TileArgs &p, typename Tr<T>::Ac
         cc[j] = n < p.N ? p.colC[n] : 0;
     }
     if (p.sc.mode == SCALE_ACC) {
+        // every load of C before any store when a thread's outputs take at
+        // most 128 bytes (larger register tiles, whose tiles run long sums,
+        // keep the plain loop): a load after a store through another
+        // pointer cannot be hoisted above it, so interleaved
+        // read-modify-writes would each pay a full round trip; the tile's
+        // outputs are distinct (C is injective)
+        if constexpr (sizeof(Acc) * TM * TN > 128) {
 #pragma unroll
-        for (int i = 0; i < TM; ++i) {
-            int64_t m = m0 + tm + i * (BM / TM);
+            for (int i = 0; i < TM; ++i) {
+                int64_t m = m0 + tm + i * (BM / TM);
 #pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                int64_t n = n0 + tn + j * (BN / TN);
-                if (m < p.M && n < p.N) R::store_add(C + rc[i] + cc[j], acc[i][j]);
+                for (int j = 0; j < TN; ++j) {
+                    int64_t n = n0 + tn + j * (BN / TN);
+                    if (m < p.M && n < p.N) R::store_add(C + rc[i] + cc[j], acc[i][j]);
+                }
+            }
+        } else {
+            Acc cv[TM][TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) {
+                const bool vm = m0 + tm + i * (BM / TM) < p.M;
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+                    cv[i][j] = vm && n0 + tn + j * (BN / TN) < p.N ? R::load_c(C + rc[i] + cc[j]) : R::zero();
+            }
+#pragma unroll
+            for (int i = 0; i < TM; ++i) {
+                const bool vm = m0 + tm + i * (BM / TM) < p.M;
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+                    if (vm && n0 + tn + j * (BN / TN) < p.N)
+                        R::store_c(C + rc[i] + cc[j], R::add(cv[i][j], acc[i][j]));
             }
         }
     } else {

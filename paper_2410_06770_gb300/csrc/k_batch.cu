@@ -176,19 +176,31 @@ __device__ __forceinline__ void gather_tile_async(const BatchProb &pr, const int
         }
         return;
     }
+    // offsets first, then a row's loads of C before its stores: a load that
+    // follows a store through another pointer cannot be hoisted above it, so
+    // interleaved read-modify-writes would each pay a full round trip (the
+    // tile's outputs are distinct: C is injective).  Row by row keeps the
+    // 64-register build's live values down.
+    int64_t rc[TM], cc[TN];
+    bool vm[TM], vn[TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-        const int64_t m = m0 + tm + i * RM;
-        if (m >= pr.M) continue;
-        const int64_t rc = t.rowC[m];
+        vm[i] = m0 + tm + i * RM < pr.M;
+        rc[i] = vm[i] ? t.rowC[m0 + tm + i * RM] : 0;
+    }
 #pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            const int64_t nn = n0 + tn + j * RN;
-            if (nn < pr.N) {
-                float *dst = pr.C + rc + t.colC[nn];
-                *dst = *dst + acc[i][j];
-            }
-        }
+    for (int j = 0; j < TN; ++j) {
+        vn[j] = n0 + tn + j * RN < pr.N;
+        cc[j] = vn[j] ? t.colC[n0 + tn + j * RN] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        float cv[TN];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cv[j] = vm[i] && vn[j] ? pr.C[rc[i] + cc[j]] : 0.f;
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+            if (vm[i] && vn[j]) pr.C[rc[i] + cc[j]] = cv[j] + acc[i][j];
     }
 }
 
@@ -400,14 +412,33 @@ __global__ void __launch_bounds__(256) batch_reduce_kernel(const BatchProb *__re
         const int64_t *rowC = t + pr.M;
         const int64_t *colC = t + 2 * pr.M + pr.N;
         const int64_t MN = pr.M * pr.N;
-        for (int64_t i = threadIdx.x; i < MN; i += blockDim.x) {
-            int64_t m, n;
-            if (pr.c_m_fast) { m = i % pr.M; n = i / pr.M; }
-            else { n = i % pr.N; m = i / pr.N; }
-            float sum = pr.partial[i];
-            for (int sp = 1; sp < pr.splits; ++sp) sum += pr.partial[(int64_t)sp * MN + i];
-            float *dst = pr.C + rowC[m] + colC[n];
-            *dst = *dst + sum;
+        // four outputs a thread per pass: their sums and every load of C go
+        // before the stores (a load after a store through another pointer
+        // cannot be hoisted above it); slices still add in order
+        constexpr int U = 4;
+        for (int64_t i0 = threadIdx.x; i0 < MN; i0 += U * (int64_t)blockDim.x) {
+            int64_t off[U];
+            float sum[U], cv[U];
+            bool v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = i0 + (int64_t)u * blockDim.x;
+                v[u] = i < MN;
+                int64_t m = 0, n = 0;
+                if (v[u]) {
+                    if (pr.c_m_fast) { m = i % pr.M; n = i / pr.M; }
+                    else { n = i % pr.N; m = i / pr.N; }
+                }
+                off[u] = v[u] ? rowC[m] + colC[n] : 0;
+                sum[u] = v[u] ? pr.partial[i] : 0.f;
+                for (int sp = 1; sp < pr.splits; ++sp)
+                    if (v[u]) sum[u] += pr.partial[(int64_t)sp * MN + i];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) cv[u] = v[u] ? pr.C[off[u]] : 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (v[u]) pr.C[off[u]] = cv[u] + sum[u];
         }
     }
 }

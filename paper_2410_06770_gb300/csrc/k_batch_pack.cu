@@ -241,18 +241,34 @@ __device__ __forceinline__ bool packed_tile(const BatchProb &pr, const int64_t *
             }
         }
     } else {
+        // C <- C + tile in three phases: offsets, every load, every store.
+        // Interleaved load/store pairs would serialise: the compiler cannot
+        // move a load above a store through another pointer, so each output
+        // would pay a full memory round trip.  The outputs of one tile are
+        // distinct (C is injective), so the loads may all go first.
+        float *rowp[TM];
+        int64_t cc[TN];
+        bool vm[TM], vn[TN];
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
-            const int64_t m = m0 + tm + i * RM;
-#pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                const int64_t n = n0 + tn + j * RN;
-                if (m < pr.M && n < pr.N) {
-                    float *dst = pr.C + s_rc[tm + i * RM] + s_cc[tn + j * RN];
-                    *dst = *dst + acc[i][j];
-                }
-            }
+            vm[i] = m0 + tm + i * RM < pr.M;
+            rowp[i] = pr.C + (vm[i] ? s_rc[tm + i * RM] : 0);
         }
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            vn[j] = n0 + tn + j * RN < pr.N;
+            cc[j] = vn[j] ? s_cc[tn + j * RN] : 0;
+        }
+        float cv[TM][TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) cv[i][j] = vm[i] && vn[j] ? rowp[i][cc[j]] : 0.f;
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j)
+                if (vm[i] && vn[j]) rowp[i][cc[j]] = cv[i][j] + acc[i][j];
     }
     return true;
 }
@@ -368,14 +384,11 @@ __global__ void __launch_bounds__(256, 4) batch_skinny_kernel(const BatchProb *_
         const int dtype = pr.dtype;
         const int64_t k0 = (int64_t)it.slice * pr.kslice, k1 = min(pr.K, k0 + pr.kslice);
         float *P = pr.splits > 1 ? pr.partial + (int64_t)it.slice * pr.M * pr.N : nullptr;
-        auto out = [&](int64_t l, int s, float v) {
+        auto pidx = [&](int64_t l, int s) {
             const int64_t m = la ? l : s, nn = la ? s : l;
-            if (P) P[pr.c_m_fast ? nn * pr.M + m : m * pr.N + nn] = v;
-            else {
-                float *dst = pr.C + t.rowC[m] + t.colC[nn];
-                *dst = *dst + v;
-            }
+            return pr.c_m_fast ? nn * pr.M + m : m * pr.N + nn;
         };
+        auto coff = [&](int64_t l, int s) { return la ? t.rowC[l] + t.colC[s] : t.rowC[s] + t.colC[l]; };
         if constexpr (!LANES_K) {
             // lanes along the long class: lane l keeps S running sums over the slice
             const int64_t l = it.l0 + lane;
@@ -403,10 +416,25 @@ __global__ void __launch_bounds__(256, 4) batch_skinny_kernel(const BatchProb *_
                         if (s < S) acc[s] = fmaf(x, load_f(Y, oy[s] + ky, dtype), acc[s]);
                 }
             }
-            if (valid)
+            if (valid) {
+                if (P) {
 #pragma unroll
-                for (int s = 0; s < SKINNY_MAX_SHORT; ++s)
-                    if (s < S) out(l, s, acc[s]);
+                    for (int s = 0; s < SKINNY_MAX_SHORT; ++s)
+                        if (s < S) P[pidx(l, s)] = acc[s];
+                } else {
+                    // offsets, then every load, then every store (a load
+                    // after a store through another pointer cannot be hoisted)
+                    int64_t off[SKINNY_MAX_SHORT];
+                    float cv[SKINNY_MAX_SHORT];
+#pragma unroll
+                    for (int s = 0; s < SKINNY_MAX_SHORT; ++s) off[s] = s < S ? coff(l, s) : 0;
+#pragma unroll
+                    for (int s = 0; s < SKINNY_MAX_SHORT; ++s) cv[s] = s < S ? pr.C[off[s]] : 0.f;
+#pragma unroll
+                    for (int s = 0; s < SKINNY_MAX_SHORT; ++s)
+                        if (s < S) pr.C[off[s]] = cv[s] + acc[s];
+                }
+            }
         } else {
             // few outputs (L, S <= 4): lanes along the sum, then a fixed
             // shuffle tree per output
@@ -442,12 +470,31 @@ __global__ void __launch_bounds__(256, 4) batch_skinny_kernel(const BatchProb *_
                 for (int b = 0; b < 4; ++b)
 #pragma unroll
                     for (int d = 16; d > 0; d >>= 1) acc[a][b] += __shfl_down_sync(0xffffffffu, acc[a][b], d);
-            if (lane == 0)
+            if (lane == 0) {
+                if (P) {
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b)
-                        if (a < Li && b < S) out(a, b, acc[a][b]);
+                        for (int b = 0; b < 4; ++b)
+                            if (a < Li && b < S) P[pidx(a, b)] = acc[a][b];
+                } else {
+                    int64_t off[4][4];
+                    float cv[4][4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) off[a][b] = a < Li && b < S ? coff(a, b) : 0;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) cv[a][b] = a < Li && b < S ? pr.C[off[a][b]] : 0.f;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            if (a < Li && b < S) pr.C[off[a][b]] = cv[a][b] + acc[a][b];
+                }
+            }
         }
     }
 }

@@ -211,23 +211,32 @@ __global__ void __launch_bounds__(T_THREADS, 1) batch_tc_kernel(const BatchProb 
             tc::tc_fence_after();
             const int64_t m = (int64_t)tmi * TC_BM + q * 32 + lane;
             const bool vm = m < pr.M;
-            const int64_t rc = vm ? t.rowC[m] : 0;
+            float *crow = pr.C + (vm ? t.rowC[m] : 0);
 #pragma unroll
             for (int cb = 0; cb < TC_BN / 64; ++cb) {
                 uint32_t v[32];
                 const int col = h * (TC_BN / 2) + cb * 32;
+                // the 32 columns' offsets: one coalesced load (lane i holds
+                // column col + i), broadcast by shuffles
+                const int64_t nl = (int64_t)tni * TC_BN + col + lane;
+                const int64_t ccl = nl < pr.N ? t.colC[nl] : 0;
+                const int64_t left = pr.N - ((int64_t)tni * TC_BN + col);
+                const int ncols = left < 32 ? (int)left : 32;
+                int64_t cc[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) cc[i] = __shfl_sync(0xffffffffu, ccl, i);
+                // every load of C before any store: interleaved
+                // read-modify-writes would serialise (a load after a store
+                // through another pointer cannot be hoisted above it); the
+                // accumulator is read while those loads are in flight
+                float cv[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) cv[i] = vm && i < ncols ? crow[cc[i]] : 0.f;
                 tc::tmem_ld_32x32b_x32(tmem_base + lane_addr + buf * TC_BN + col, v);
                 tc::tmem_ld_wait();
-                if (vm) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int64_t n = (int64_t)tni * TC_BN + col + i;
-                        if (n < pr.N) {
-                            float *dst = pr.C + rc + t.colC[n];
-                            *dst = *dst + __uint_as_float(v[i]);
-                        }
-                    }
-                }
+                for (int i = 0; i < 32; ++i)
+                    if (vm && i < ncols) crow[cc[i]] = cv[i] + __uint_as_float(v[i]);
             }
             tc::tc_fence_before();
             __syncwarp();
