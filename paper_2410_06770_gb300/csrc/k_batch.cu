@@ -258,68 +258,79 @@ __device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tab
 }
 
 // Short sums (K <= 8, one K slice): each thread forms its TM x TN outputs
-// straight from gathered loads -- no shared-memory staging, no barriers, no
-// padding of K to the tile's BK.  Same thread-to-output mapping as the staged
-// tile (lanes along C's smaller increment); each output starts from C's value
-// and adds the products with k ascending, Alg. 1's order.
+// straight from gathered loads -- no operand staging, no padding of K to the
+// tile's BK.  The tile's row and column offsets (rowA, rowC, colB, colC) and
+// the sum's K offsets are staged in shared memory first (one coalesced load
+// a thread, one round trip), so the operand loads of every k depend on
+// shared-memory reads only and the offsets take no registers.  Same
+// thread-to-output mapping as the staged tile (lanes along C's smaller
+// increment); each output starts from C's value and adds the products with
+// k ascending, Alg. 1's order.
 template <class T, int CFG>
-__device__ __forceinline__ void run_direct(const BatchProb &pr, const int64_t *tables, int item)
+__device__ __forceinline__ void run_direct(const BatchProb &pr, const int64_t *tables, int tile, int64_t *s_off,
+                                           int64_t *s_k)
 {
     using R = Tr<T>;
     using Acc = typename R::Acc;
     constexpr BCfg c = kB[CFG];
-    constexpr int TM = c.tm, TN = c.tn, RM = c.bm / c.tm, RN = c.bn / c.tn;
-    const int tile = item;  // one slice
-    const int64_t m0 = (int64_t)(tile / pr.tiles_n) * c.bm, n0 = (int64_t)(tile % pr.tiles_n) * c.bn;
+    constexpr int BM = c.bm, BN = c.bn, TM = c.tm, TN = c.tn, RM = BM / TM, RN = BN / TN;
+    static_assert(2 * (BM + BN) <= BT, "one offset a thread");
+    const int64_t M = pr.M, N = pr.N, K = pr.K;
+    const int64_t m0 = (int64_t)(tile / pr.tiles_n) * BM, n0 = (int64_t)(tile % pr.tiles_n) * BN;
     const int64_t *rowA = tables + pr.tab;
-    const int64_t *rowC = rowA + pr.M, *colB = rowC + pr.M, *colC = colB + pr.N, *kA = colC + pr.N;
-    const int64_t *kB = kA + pr.K;
+    const int64_t *rowC = rowA + M, *colB = rowC + M, *colC = colB + N, *kA = colC + N;
+    const int64_t *kB = kA + K;
     const int tid = threadIdx.x;
+    // s_off: [0, BM) rowA, [BM, 2 BM) rowC, [2 BM, 2 BM + BN) colB, then colC
+    if (tid < 2 * BM) {
+        const int r = tid % BM;
+        s_off[tid] = m0 + r < M ? (tid < BM ? rowA : rowC)[m0 + r] : 0;
+    } else if (tid < 2 * (BM + BN)) {
+        const int q = (tid - 2 * BM) % BN;
+        s_off[tid] = n0 + q < N ? (tid < 2 * BM + BN ? colB : colC)[n0 + q] : 0;
+    }
+    if (tid < 16) s_k[tid] = (tid & 7) < K ? (tid < 8 ? kA : kB)[tid & 7] : 0;
+    __syncthreads();
     int tm, tn;
     if (pr.c_m_fast) { tm = tid % RM; tn = tid / RM; }
     else { tn = tid % RN; tm = tid / RN; }
     const T *A = static_cast<const T *>(pr.A);
     const T *B = static_cast<const T *>(pr.B);
-    int64_t oa[TM], oc[TM], ob[TN], od[TN];
     bool vm[TM], vn[TN];
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        const int64_t m = m0 + tm + i * RM;
-        vm[i] = m < pr.M;
-        oa[i] = vm[i] ? rowA[m] : 0;
-        oc[i] = vm[i] ? rowC[m] : 0;
-    }
+    for (int i = 0; i < TM; ++i) vm[i] = m0 + tm + i * RM < M;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) {
-        const int64_t n = n0 + tn + j * RN;
-        vn[j] = n < pr.N;
-        ob[j] = vn[j] ? colB[n] : 0;
-        od[j] = vn[j] ? colC[n] : 0;
-    }
+    for (int j = 0; j < TN; ++j) vn[j] = n0 + tn + j * RN < N;
     // C is read before the sum (the batch only accumulates): its loads are
     // in flight together with the operands' instead of after them
     Acc acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = (vm[i] && vn[j]) ? pr.C[oc[i] + od[j]] : R::zero();
-    for (int64_t k = 0; k < pr.K; ++k) {
-        const int64_t ka = kA[k], kb = kB[k];
-        Acc a[TM], b[TN];
+        for (int j = 0; j < TN; ++j)
+            acc[i][j] = (vm[i] && vn[j]) ? pr.C[s_off[BM + tm + i * RM] + s_off[2 * BM + BN + tn + j * RN]]
+                                         : R::zero();
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = vm[i] ? R::load(A + oa[i] + ka) : R::zero();
+    for (int k = 0; k < 8; ++k) {
+        if (k < K) {
+            const int64_t ka = s_k[k], kb = s_k[8 + k];
+            Acc a[TM], b[TN];
 #pragma unroll
-        for (int j = 0; j < TN; ++j) b[j] = vn[j] ? R::load(B + ob[j] + kb) : R::zero();
+            for (int i = 0; i < TM; ++i) a[i] = vm[i] ? R::load(A + s_off[tm + i * RM] + ka) : R::zero();
 #pragma unroll
-        for (int i = 0; i < TM; ++i)
+            for (int j = 0; j < TN; ++j) b[j] = vn[j] ? R::load(B + s_off[2 * BM + tn + j * RN] + kb) : R::zero();
 #pragma unroll
-            for (int j = 0; j < TN; ++j) R::mac(acc[i][j], a[i], b[j]);
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) R::mac(acc[i][j], a[i], b[j]);
+        }
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j)
-            if (vm[i] && vn[j]) pr.C[oc[i] + od[j]] = acc[i][j];
+            if (vm[i] && vn[j]) pr.C[s_off[BM + tm + i * RM] + s_off[2 * BM + BN + tn + j * RN]] = acc[i][j];
+    __syncthreads();  // the next tile restages the offsets
 }
 
 // largest shared footprint over the configurations (floats / int64s)
@@ -347,6 +358,12 @@ __global__ void __launch_bounds__(BT, CPS) batch_kernel(const BatchProb *__restr
     __shared__ int64_t smem_i[smem_ints()];
     __shared__ int64_t skA[kStageK], skB[kStageK];
     __shared__ unsigned long long s_item;
+    // the item's problem descriptor, copied once by warp 0: fields are read
+    // from shared memory instead of living in registers (the build for four
+    // resident CTAs has 64 registers a thread)
+    __shared__ __align__(16) BatchProb s_pr;
+    constexpr int kWords = (int)(sizeof(BatchProb) / 4);
+    static_assert(sizeof(BatchProb) % 4 == 0 && kWords <= 64, "descriptor copy by one warp, two words a lane");
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
     __syncthreads();
     unsigned long long it = s_item;
@@ -356,20 +373,28 @@ __global__ void __launch_bounds__(BT, CPS) batch_kernel(const BatchProb *__restr
         unsigned long long next = 0;
         if (threadIdx.x == 0) next = atomicAdd(counter, 1ull);
         const uint2 w = work[it % (unsigned long long)wrap];
-        const BatchProb pr = probs[w.x];
+        if (threadIdx.x < 32) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(probs + w.x);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&s_pr);
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (threadIdx.x + 32 * q < kWords) dst[threadIdx.x + 32 * q] = __ldg(src + threadIdx.x + 32 * q);
+        }
+        __syncthreads();
+        const BatchProb &pr = s_pr;
         const int key = pr.shape * 2 + pr.dtype;
         if (batch_direct(pr)) {
             const int tend = min(pr.tiles_m * pr.tiles_n, ((int)w.y + 1) * pr.tpi);
             for (int tile = (int)w.y * pr.tpi; tile < tend; ++tile) {
                 switch (key) {
-                case 0: run_direct<float, 0>(pr, tables, tile); break;
-                case 1: run_direct<uint16_t, 0>(pr, tables, tile); break;
-                case 2: run_direct<float, 1>(pr, tables, tile); break;
-                case 3: run_direct<uint16_t, 1>(pr, tables, tile); break;
-                case 4: run_direct<float, 2>(pr, tables, tile); break;
-                case 5: run_direct<uint16_t, 2>(pr, tables, tile); break;
-                case 6: run_direct<float, 3>(pr, tables, tile); break;
-                case 7: run_direct<uint16_t, 3>(pr, tables, tile); break;
+                case 0: run_direct<float, 0>(pr, tables, tile, skA, skB); break;
+                case 1: run_direct<uint16_t, 0>(pr, tables, tile, skA, skB); break;
+                case 2: run_direct<float, 1>(pr, tables, tile, skA, skB); break;
+                case 3: run_direct<uint16_t, 1>(pr, tables, tile, skA, skB); break;
+                case 4: run_direct<float, 2>(pr, tables, tile, skA, skB); break;
+                case 5: run_direct<uint16_t, 2>(pr, tables, tile, skA, skB); break;
+                case 6: run_direct<float, 3>(pr, tables, tile, skA, skB); break;
+                case 7: run_direct<uint16_t, 3>(pr, tables, tile, skA, skB); break;
                 default: break;
                 }
             }

@@ -41,7 +41,7 @@ __device__ __forceinline__ float load_f(const void *base, int64_t off, int dtype
 // ---------------------------------------------------------------------------
 constexpr int PK = 64;  // contracted indices per packing item
 
-__global__ void __launch_bounds__(256) batch_pack_kernel(const BatchProb *__restrict__ probs,
+__global__ void __launch_bounds__(256, 4) batch_pack_kernel(const BatchProb *__restrict__ probs,
                                                          const PackItem *__restrict__ items, int64_t n,
                                                          int64_t wrap, const int64_t *__restrict__ tables)
 {
@@ -67,19 +67,30 @@ __global__ void __launch_bounds__(256) batch_pack_kernel(const BatchProb *__rest
         if (tid < bw) srow[tid] = r0 + tid < rows ? rowT[r0 + tid] : 0;
         else if (tid >= 64 && tid < 64 + klen) sk[tid - 64] = k0 + (tid - 64) < K ? kT[k0 + (tid - 64)] : 0;
         __syncthreads();
-        const int nel = bw * klen;
-#pragma unroll 4
-        for (int e = tid; e < nel; e += 256) {
-            int w, kk;
-            if (fast) { w = e % bw; kk = e / bw; }
-            else { kk = e % klen; w = e / klen; }
-            float v = 0.f;
-            if (r0 + w < rows && k0 + kk < K) v = load_f(src, srow[w] + sk[kk], dtype);
-            tile[kk][w] = v;
+        // the block's 64 x bw elements, 16 a thread, every load issued before
+        // the first store to shared memory (one round trip, not one per
+        // element); bw is 32 or 64, so the index split is shifts and masks:
+        // along w first when that is the operand's smaller increment, else
+        // along k (64 wide), with out-of-block lanes idle
+        const int lbw = bw == 64 ? 6 : 5;
+        constexpr int NV = PK * 64 / 256;
+        float v[NV];
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+            const int e = tid + u * 256;
+            const int w = fast ? (e & (bw - 1)) : (e >> 6), kk = fast ? (e >> lbw) : (e & (PK - 1));
+            v[u] = w < bw && kk < klen && r0 + w < rows && k0 + kk < K ? load_f(src, srow[w] + sk[kk], dtype) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+            const int e = tid + u * 256;
+            const int w = fast ? (e & (bw - 1)) : (e >> 6), kk = fast ? (e >> lbw) : (e & (PK - 1));
+            if (w < bw && kk < klen) tile[kk][w] = v[u];
         }
         __syncthreads();
+        const int nel = bw * klen;
         for (int e = tid; e < nel; e += 256) {
-            const int kk = e / bw, w = e % bw;
+            const int kk = e >> lbw, w = e & (bw - 1);
             dst[(int64_t)kk * bw + w] = tile[kk][w];
         }
     }

@@ -41,7 +41,7 @@ __device__ __forceinline__ void tc_bulk_load(void *smem_dst, const void *gmem_sr
 // ---------------------------------------------------------------------------
 // packing into swizzled tiles
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) batch_tc_pack_kernel(const BatchProb *__restrict__ probs,
+__global__ void __launch_bounds__(256, 4) batch_tc_pack_kernel(const BatchProb *__restrict__ probs,
                                                             const TcPackItem *__restrict__ items, int64_t n,
                                                             int64_t wrap, const int64_t *__restrict__ tables)
 {
@@ -65,12 +65,23 @@ __global__ void __launch_bounds__(256) batch_tc_pack_kernel(const BatchProb *__r
         if (tid < 128) srow[tid] = r0 + tid < rows ? rowT[r0 + tid] : 0;
         else if (tid < 192) sk[tid - 128] = k0 + (tid - 128) < K ? kT[k0 + (tid - 128)] : 0;
         __syncthreads();
-#pragma unroll 4
-        for (int e = tid; e < 128 * TC_BK; e += 256) {
-            int r, kk;
-            if (fast) { r = e % 128; kk = e / 128; }
-            else { kk = e % TC_BK; r = e / TC_BK; }
-            tile[r][kk] = (r0 + r < rows && k0 + kk < K) ? __ldg(src + srow[r] + sk[kk]) : (uint16_t)0;
+        // 32 elements a thread in two halves of 16 loads, each half's loads
+        // all issued before its stores to shared memory
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint16_t v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int e = tid + (h * 16 + u) * 256;
+                const int r = fast ? (e & 127) : (e >> 6), kk = fast ? (e >> 7) : (e & (TC_BK - 1));
+                v[u] = (r0 + r < rows && k0 + kk < K) ? __ldg(src + srow[r] + sk[kk]) : (uint16_t)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int e = tid + (h * 16 + u) * 256;
+                const int r = fast ? (e & 127) : (e >> 6), kk = fast ? (e >> 7) : (e & (TC_BK - 1));
+                tile[r][kk] = v[u];
+            }
         }
         __syncthreads();
         // 16-byte chunks: chunk j of row r goes to chunk position j ^ (r & 7)
