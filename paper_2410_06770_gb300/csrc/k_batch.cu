@@ -259,78 +259,104 @@ __device__ __forceinline__ void run_tile(const BatchProb &pr, const int64_t *tab
 
 // Short sums (K <= 8, one K slice): each thread forms its TM x TN outputs
 // straight from gathered loads -- no operand staging, no padding of K to the
-// tile's BK.  The tile's row and column offsets (rowA, rowC, colB, colC) and
-// the sum's K offsets are staged in shared memory first (one coalesced load
-// a thread, one round trip), so the operand loads of every k depend on
-// shared-memory reads only and the offsets take no registers.  Same
-// thread-to-output mapping as the staged tile (lanes along C's smaller
-// increment); each output starts from C's value and adds the products with
-// k ascending, Alg. 1's order.
+// tile's BK.  A tile's row and column offsets (rowA, rowC, colB, colC) are
+// staged in shared memory, one coalesced load a thread, and so are the
+// sum's K offsets: the operand loads of every k then depend on
+// shared-memory reads only, and the offsets take no registers.  The offsets
+// of the item's next tile are loaded while the current tile's loads are in
+// flight and stored into the other half of a double buffer, so a tile costs
+// one round trip and one barrier.  Same thread-to-output mapping as the
+// staged tile (lanes along C's smaller increment); each output starts from
+// C's value and adds the products with k ascending, Alg. 1's order.
+template <int CFG>
+__device__ __forceinline__ int64_t direct_offset(const BatchProb &pr, const int64_t *tables, int tile)
+{
+    constexpr int BM = kB[CFG].bm, BN = kB[CFG].bn;
+    const int64_t M = pr.M, N = pr.N;
+    const int64_t m0 = (int64_t)(tile / pr.tiles_n) * BM, n0 = (int64_t)(tile % pr.tiles_n) * BN;
+    const int64_t *rowA = tables + pr.tab;
+    const int64_t *rowC = rowA + M, *colB = rowC + M, *colC = colB + N;
+    const int tid = threadIdx.x;
+    // [0, BM) rowA, [BM, 2 BM) rowC, [2 BM, 2 BM + BN) colB, then colC
+    if (tid < 2 * BM) {
+        const int r = tid % BM;
+        return m0 + r < M ? (tid < BM ? rowA : rowC)[m0 + r] : 0;
+    }
+    if (tid < 2 * (BM + BN)) {
+        const int q = (tid - 2 * BM) % BN;
+        return n0 + q < N ? (tid < 2 * BM + BN ? colB : colC)[n0 + q] : 0;
+    }
+    return 0;
+}
+
+constexpr int kDirectOff = 2 * (64 + 64);  // offsets of one tile, largest shape
+
 template <class T, int CFG>
-__device__ __forceinline__ void run_direct(const BatchProb &pr, const int64_t *tables, int tile, int64_t *s_off,
-                                           int64_t *s_k)
+__device__ __forceinline__ void run_direct(const BatchProb &pr, const int64_t *tables, int t0, int t1,
+                                           int64_t *s_off, int64_t *s_k)
 {
     using R = Tr<T>;
     using Acc = typename R::Acc;
     constexpr BCfg c = kB[CFG];
     constexpr int BM = c.bm, BN = c.bn, TM = c.tm, TN = c.tn, RM = BM / TM, RN = BN / TN;
-    static_assert(2 * (BM + BN) <= BT, "one offset a thread");
+    static_assert(2 * (BM + BN) <= BT && 2 * (BM + BN) <= kDirectOff, "one offset a thread");
     const int64_t M = pr.M, N = pr.N, K = pr.K;
-    const int64_t m0 = (int64_t)(tile / pr.tiles_n) * BM, n0 = (int64_t)(tile % pr.tiles_n) * BN;
-    const int64_t *rowA = tables + pr.tab;
-    const int64_t *rowC = rowA + M, *colB = rowC + M, *colC = colB + N, *kA = colC + N;
-    const int64_t *kB = kA + K;
     const int tid = threadIdx.x;
-    // s_off: [0, BM) rowA, [BM, 2 BM) rowC, [2 BM, 2 BM + BN) colB, then colC
-    if (tid < 2 * BM) {
-        const int r = tid % BM;
-        s_off[tid] = m0 + r < M ? (tid < BM ? rowA : rowC)[m0 + r] : 0;
-    } else if (tid < 2 * (BM + BN)) {
-        const int q = (tid - 2 * BM) % BN;
-        s_off[tid] = n0 + q < N ? (tid < 2 * BM + BN ? colB : colC)[n0 + q] : 0;
+    {
+        const int64_t v = direct_offset<CFG>(pr, tables, t0);
+        if (tid < 2 * (BM + BN)) s_off[tid] = v;
+        const int64_t *kA = tables + pr.tab + 2 * M + 2 * N;
+        if (tid < 16) s_k[tid] = (tid & 7) < K ? kA[(tid < 8 ? 0 : K) + (tid & 7)] : 0;
     }
-    if (tid < 16) s_k[tid] = (tid & 7) < K ? (tid < 8 ? kA : kB)[tid & 7] : 0;
     __syncthreads();
     int tm, tn;
     if (pr.c_m_fast) { tm = tid % RM; tn = tid / RM; }
     else { tn = tid % RN; tm = tid / RN; }
     const T *A = static_cast<const T *>(pr.A);
     const T *B = static_cast<const T *>(pr.B);
-    bool vm[TM], vn[TN];
+    for (int tile = t0; tile < t1; ++tile) {
+        const int64_t *so = s_off + ((tile - t0) & 1) * kDirectOff;
+        // the next tile's offset: in flight with this tile's loads
+        const int64_t nv = tile + 1 < t1 ? direct_offset<CFG>(pr, tables, tile + 1) : 0;
+        const int64_t m0 = (int64_t)(tile / pr.tiles_n) * BM, n0 = (int64_t)(tile % pr.tiles_n) * BN;
+        bool vm[TM], vn[TN];
 #pragma unroll
-    for (int i = 0; i < TM; ++i) vm[i] = m0 + tm + i * RM < M;
+        for (int i = 0; i < TM; ++i) vm[i] = m0 + tm + i * RM < M;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) vn[j] = n0 + tn + j * RN < N;
-    // C is read before the sum (the batch only accumulates): its loads are
-    // in flight together with the operands' instead of after them
-    Acc acc[TM][TN];
+        for (int j = 0; j < TN; ++j) vn[j] = n0 + tn + j * RN < N;
+        // C is read before the sum (the batch only accumulates): its loads
+        // are in flight together with the operands' instead of after them
+        Acc acc[TM][TN];
 #pragma unroll
-    for (int i = 0; i < TM; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j)
-            acc[i][j] = (vm[i] && vn[j]) ? pr.C[s_off[BM + tm + i * RM] + s_off[2 * BM + BN + tn + j * RN]]
-                                         : R::zero();
+            for (int j = 0; j < TN; ++j)
+                acc[i][j] = (vm[i] && vn[j]) ? pr.C[so[BM + tm + i * RM] + so[2 * BM + BN + tn + j * RN]] : R::zero();
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        if (k < K) {
-            const int64_t ka = s_k[k], kb = s_k[8 + k];
-            Acc a[TM], b[TN];
+        for (int k = 0; k < 8; ++k) {
+            if (k < K) {
+                const int64_t ka = s_k[k], kb = s_k[8 + k];
+                Acc a[TM], b[TN];
 #pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = vm[i] ? R::load(A + s_off[tm + i * RM] + ka) : R::zero();
+                for (int i = 0; i < TM; ++i) a[i] = vm[i] ? R::load(A + so[tm + i * RM] + ka) : R::zero();
 #pragma unroll
-            for (int j = 0; j < TN; ++j) b[j] = vn[j] ? R::load(B + s_off[2 * BM + tn + j * RN] + kb) : R::zero();
+                for (int j = 0; j < TN; ++j) b[j] = vn[j] ? R::load(B + so[2 * BM + tn + j * RN] + kb) : R::zero();
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) R::mac(acc[i][j], a[i], b[j]);
+                    for (int j = 0; j < TN; ++j) R::mac(acc[i][j], a[i], b[j]);
+            }
         }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j)
+                if (vm[i] && vn[j]) pr.C[so[BM + tm + i * RM] + so[2 * BM + BN + tn + j * RN]] = acc[i][j];
+        // the other buffer was last read in the previous tile, which every
+        // thread finished before the barrier that closed it
+        if (tile + 1 < t1 && tid < 2 * (BM + BN)) s_off[(((tile - t0) & 1) ^ 1) * kDirectOff + tid] = nv;
+        __syncthreads();
     }
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j)
-            if (vm[i] && vn[j]) pr.C[s_off[BM + tm + i * RM] + s_off[2 * BM + BN + tn + j * RN]] = acc[i][j];
-    __syncthreads();  // the next tile restages the offsets
 }
 
 // largest shared footprint over the configurations (floats / int64s)
@@ -383,22 +409,7 @@ __global__ void __launch_bounds__(BT, CPS) batch_kernel(const BatchProb *__restr
         __syncthreads();
         const BatchProb &pr = s_pr;
         const int key = pr.shape * 2 + pr.dtype;
-        if (batch_direct(pr)) {
-            const int tend = min(pr.tiles_m * pr.tiles_n, ((int)w.y + 1) * pr.tpi);
-            for (int tile = (int)w.y * pr.tpi; tile < tend; ++tile) {
-                switch (key) {
-                case 0: run_direct<float, 0>(pr, tables, tile, skA, skB); break;
-                case 1: run_direct<uint16_t, 0>(pr, tables, tile, skA, skB); break;
-                case 2: run_direct<float, 1>(pr, tables, tile, skA, skB); break;
-                case 3: run_direct<uint16_t, 1>(pr, tables, tile, skA, skB); break;
-                case 4: run_direct<float, 2>(pr, tables, tile, skA, skB); break;
-                case 5: run_direct<uint16_t, 2>(pr, tables, tile, skA, skB); break;
-                case 6: run_direct<float, 3>(pr, tables, tile, skA, skB); break;
-                case 7: run_direct<uint16_t, 3>(pr, tables, tile, skA, skB); break;
-                default: break;
-                }
-            }
-        } else switch (key) {
+        switch (key) {
         case 0: run_tile<float, 0>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
         case 1: run_tile<uint16_t, 0>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
         case 2: run_tile<float, 1>(pr, tables, w.y, smem_f, smem_i, skA, skB); break;
@@ -423,6 +434,61 @@ void launch_batch_kernel(int cps, int ctas, cudaStream_t s, const BatchProb *pro
     if (cps >= 4) batch_kernel<4><<<ctas, BT, 0, s>>>(probs, work, nwork, wrap, tables, counter);
     else if (cps == 3) batch_kernel<3><<<ctas, BT, 0, s>>>(probs, work, nwork, wrap, tables, counter);
     else batch_kernel<2><<<ctas, BT, 0, s>>>(probs, work, nwork, wrap, tables, counter);
+}
+
+// Short sums (K <= 8): items are runs of tiles of one problem, taken from
+// their own atomic counter.  Apart from the staged offsets the kernel holds
+// no shared memory, so four CTAs of 256 threads share an SM with the other
+// branches' kernels.
+__global__ void __launch_bounds__(BT, 4) batch_direct_kernel(const BatchProb *__restrict__ probs,
+                                                             const uint2 *__restrict__ work, int64_t nwork,
+                                                             int64_t wrap, const int64_t *__restrict__ tables,
+                                                             unsigned long long *counter)
+{
+    __shared__ int64_t s_off[2 * kDirectOff], s_k[16];
+    __shared__ unsigned long long s_item;
+    __shared__ __align__(16) BatchProb s_pr;
+    constexpr int kWords = (int)(sizeof(BatchProb) / 4);
+    static_assert(sizeof(BatchProb) % 4 == 0 && kWords <= 64, "descriptor copy by one warp, two words a lane");
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
+    __syncthreads();
+    unsigned long long it = s_item;
+    while (it < (unsigned long long)nwork) {
+        unsigned long long next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1ull);
+        const uint2 w = work[it % (unsigned long long)wrap];
+        if (threadIdx.x < 32) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(probs + w.x);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&s_pr);
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (threadIdx.x + 32 * q < kWords) dst[threadIdx.x + 32 * q] = __ldg(src + threadIdx.x + 32 * q);
+        }
+        __syncthreads();
+        const BatchProb &pr = s_pr;
+        const int key = pr.shape * 2 + pr.dtype;
+        const int t0 = (int)w.y * pr.tpi, t1 = min(pr.tiles_m * pr.tiles_n, t0 + pr.tpi);
+        switch (key) {
+        case 0: run_direct<float, 0>(pr, tables, t0, t1, s_off, s_k); break;
+        case 1: run_direct<uint16_t, 0>(pr, tables, t0, t1, s_off, s_k); break;
+        case 2: run_direct<float, 1>(pr, tables, t0, t1, s_off, s_k); break;
+        case 3: run_direct<uint16_t, 1>(pr, tables, t0, t1, s_off, s_k); break;
+        case 4: run_direct<float, 2>(pr, tables, t0, t1, s_off, s_k); break;
+        case 5: run_direct<uint16_t, 2>(pr, tables, t0, t1, s_off, s_k); break;
+        case 6: run_direct<float, 3>(pr, tables, t0, t1, s_off, s_k); break;
+        case 7: run_direct<uint16_t, 3>(pr, tables, t0, t1, s_off, s_k); break;
+        default: break;
+        }
+        if (threadIdx.x == 0) s_item = next;
+        __syncthreads();  // (run_direct ends with a barrier: s_pr is free too)
+        it = s_item;
+    }
+}
+
+void launch_batch_direct(int ctas, cudaStream_t s, const BatchProb *probs, const uint2 *work, int64_t nwork,
+                         int64_t wrap, const int64_t *tables, unsigned long long *counter)
+{
+    batch_direct_kernel<<<ctas, BT, 0, s>>>(probs, work, nwork, wrap, tables, counter);
 }
 
 // Adds the K-slice partial tiles of every split problem into C, slices in
@@ -557,6 +623,9 @@ struct gett_batch {
     unsigned long long *d_counter = nullptr;  // work counter of the gather kernel (and one spare)
     // every list again grouped by problem (the autotuner times one problem)
     uint2 *d_work_by_problem = nullptr;
+    uint2 *d_direct = nullptr;               // short-sum tile runs (sorted) and grouped by problem
+    uint2 *d_direct_by_problem = nullptr;
+    int64_t ndirect = 0;
     uint2 *d_packed_by_problem = nullptr;
     float *d_partial = nullptr;          // K-slice partials of split problems
     int *d_reduce = nullptr;             // indices (into the descriptor table) of split problems
@@ -565,7 +634,7 @@ struct gett_batch {
     std::vector<int> reduce_of;          // per user index: descriptor index if split, else -1
     // per user index: start and count in each by-problem list
     std::vector<int64_t> gw_start, gw_count, pw_start, pw_count, pk_start, pk_count, sk_start, sk_count;
-    std::vector<int64_t> tw_start, tw_count, tk_start, tk_count;
+    std::vector<int64_t> tw_start, tw_count, tk_start, tk_count, dw_start, dw_count;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap = nullptr;
@@ -573,9 +642,9 @@ struct gett_batch {
     // packed one run on these streams, forked from and joined back into the
     // launch stream (created with the handle unless `serial`)
     bool serial = false;
-    cudaStream_t branch[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t branch[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t fork = nullptr;
-    cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t join[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 using namespace gett;
@@ -907,17 +976,18 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     b->sms = sms;
     std::vector<int64_t> tables((size_t)std::max<int64_t>(table_len, 1));
     // per-problem lists (grouped) and their costs
-    std::vector<uint2> gwork, pwork, twork;
+    std::vector<uint2> gwork, pwork, twork, dwork;
     std::vector<PackItem> pack;
     std::vector<TcPackItem> tpack;
     std::vector<SkinnyItem> skinny;
-    std::vector<double> gcost, pcost, scost, tcost;
+    std::vector<double> gcost, pcost, scost, tcost, dcost;
     b->gw_start.assign(n, 0); b->gw_count.assign(n, 0);
     b->pw_start.assign(n, 0); b->pw_count.assign(n, 0);
     b->pk_start.assign(n, 0); b->pk_count.assign(n, 0);
     b->sk_start.assign(n, 0); b->sk_count.assign(n, 0);
     b->tw_start.assign(n, 0); b->tw_count.assign(n, 0);
     b->tk_start.assign(n, 0); b->tk_count.assign(n, 0);
+    b->dw_start.assign(n, 0); b->dw_count.assign(n, 0);
     for (size_t j = 0; j < hp.size(); ++j) {
         const Plan &p = plans[hp_index[j]];
         BatchProb &pr = hp[j];
@@ -930,13 +1000,17 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
         b->config_count[pr.cfg]++;
         const double tile_area = (double)pr.bm * pr.bn;
         if (pr.method == BM_GATHER) {
-            b->gw_start[ui] = (int64_t)gwork.size();
+            // short sums go to their own kernel
+            const bool dir = batch_direct(pr);
+            std::vector<uint2> &lst = dir ? dwork : gwork;
+            std::vector<double> &cst = dir ? dcost : gcost;
+            (dir ? b->dw_start : b->gw_start)[ui] = (int64_t)lst.size();
             const int nitems = batch_items(pr);
             for (int tt = 0; tt < nitems; ++tt) {
-                gwork.push_back(make_uint2((unsigned)j, (unsigned)tt));
-                gcost.push_back(tile_area * (double)pr.kps * pr.tpi);
+                lst.push_back(make_uint2((unsigned)j, (unsigned)tt));
+                cst.push_back(tile_area * (double)pr.kps * pr.tpi);
             }
-            b->gw_count[ui] = nitems;
+            (dir ? b->dw_count : b->gw_count)[ui] = nitems;
         } else if (pr.method == BM_PACK) {
             b->pw_start[ui] = (int64_t)pwork.size();
             const int nitems = pr.tiles_m * pr.tiles_n * pr.splits;
@@ -991,6 +1065,8 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     const std::vector<uint2> gsorted = by_cost(gwork, gcost), psorted = by_cost(pwork, pcost);
     const std::vector<SkinnyItem> ssorted = by_cost(skinny, scost);
     const std::vector<uint2> tsorted = by_cost(twork, tcost);
+    const std::vector<uint2> dsorted = by_cost(dwork, dcost);
+    b->ndirect = (int64_t)dsorted.size();
     b->ntc = (int64_t)tsorted.size();
     b->ntcpack = (int64_t)tpack.size();
     b->nwork = (int64_t)gsorted.size();
@@ -1030,11 +1106,13 @@ int batch_create_impl(int n, const gett_problem_desc *probs, const gett_batch_op
     if (e == cudaSuccess) e = upload(&b->d_tc_work, tsorted);
     if (e == cudaSuccess) e = upload(&b->d_tc_work_by_problem, twork);
     if (e == cudaSuccess) e = upload(&b->d_tc_pack, tpack);
+    if (e == cudaSuccess) e = upload(&b->d_direct, dsorted);
+    if (e == cudaSuccess) e = upload(&b->d_direct_by_problem, dwork);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 2 * sizeof(unsigned long long));
     b->serial = o.serial != 0;
     if (e == cudaSuccess && !b->serial) {
         e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-        for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
             e = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
         }
@@ -1086,14 +1164,16 @@ struct Ranges {
     int64_t tn;
     const TcPackItem *tk;
     int64_t tkn;
+    const uint2 *dw;  // short-sum tile runs
+    int64_t dn;
 };
 
 // The method chains of a launch touch disjoint outputs (every problem runs
 // one method, and problems' C regions do not overlap) and disjoint
 // workspaces, so they are independent: (1) packing + packed tiles,
-// (2) tensor-core packing + tensor-core tiles, (3) gathered tiles and short
-// sums, (4) skinny warp items.  The ordered reduction of K-slice partials
-// runs after all of them.  Unless the handle is serial, chains 2-4 run on
+// (2) tensor-core packing + tensor-core tiles, (3) gathered tiles, (4) skinny
+// warp items, (5) short sums.  The ordered reduction of K-slice partials
+// runs after all of them.  Unless the launch is serial, chains 2-5 run on
 // branch streams that wait for an event recorded on the launch stream, and
 // the launch stream waits for each branch's join event before the
 // reduction; the same calls build a forked graph under stream capture.
@@ -1105,12 +1185,12 @@ cudaError_t enqueue_ranges(gett_batch *b, const Ranges &r, cudaStream_t s, bool 
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int64_t c = r.copies;
-    const bool has[3] = {r.tkn > 0 || r.tn > 0, r.gn > 0, r.sn > 0};
+    const bool has[4] = {r.tkn > 0 || r.tn > 0, r.gn > 0, r.sn > 0, r.dn > 0};
     const bool fork = concurrent && b->fork;
-    cudaStream_t bs[3] = {s, s, s};
+    cudaStream_t bs[4] = {s, s, s, s};
     if (fork) {
         e = cudaEventRecord(b->fork, s);
-        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i)
             if (has[i]) {
                 bs[i] = b->branch[i];
                 e = cudaStreamWaitEvent(bs[i], b->fork, 0);
@@ -1119,8 +1199,8 @@ cudaError_t enqueue_ranges(gett_batch *b, const Ranges &r, cudaStream_t s, bool 
     }
     // issue order as in a serial launch: packing (chain 1), tensor-core
     // packing and tiles (chain 2), packed tiles (chain 1), gathered tiles
-    // (chain 3; its work counter was reset on the launch stream before the
-    // fork), skinny items (chain 4)
+    // (chain 3; the work counters were reset on the launch stream before the
+    // fork), skinny items (chain 4), short sums (chain 5)
     if (r.kn > 0)
         launch_batch_pack((int)std::min<int64_t>(r.kn * c, (int64_t)b->sms * 8), s, b->d_probs, r.pk, r.kn * c, r.kn,
                           b->d_tables);
@@ -1144,10 +1224,13 @@ cudaError_t enqueue_ranges(gett_batch *b, const Ranges &r, cudaStream_t s, bool 
     if (r.sn > 0)
         launch_batch_skinny((int)std::min<int64_t>((r.sn * c + 7) / 8, (int64_t)b->sms * 4), bs[2], b->d_probs, r.sk,
                             r.sn * c, r.sn, b->d_tables);
+    if (r.dn > 0)
+        launch_batch_direct((int)std::min<int64_t>((int64_t)b->sms * 4, r.dn * c), bs[3], b->d_probs, r.dw, r.dn * c,
+                            r.dn, b->d_tables, b->d_counter + 1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (fork) {
-        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i)
             if (has[i]) {
                 e = cudaEventRecord(b->join[i], bs[i]);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[i], 0);
@@ -1165,7 +1248,7 @@ static cudaError_t enqueue(gett_batch *b, cudaStream_t s)
 {
     const Ranges r{b->d_work, b->nwork, b->d_packed_work, b->npacked, b->d_pack, b->npack,
                    b->d_skinny, b->nskinny, b->d_reduce, b->nreduce, 1,
-                   b->d_tc_work, b->ntc, b->d_tc_pack, b->ntcpack};
+                   b->d_tc_work, b->ntc, b->d_tc_pack, b->ntcpack, b->d_direct, b->ndirect};
     return enqueue_ranges(b, r, s, !b->serial);
 }
 
@@ -1216,7 +1299,7 @@ extern "C" int gett_batch_profile(gett_batch *b, int reps, int mode, float *ms_o
     cudaEventCreate(&e1);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         ms_out[i] = 0.f;
-        const int64_t cnt = b->gw_count[i] + b->pw_count[i] + b->sk_count[i] + b->tw_count[i];
+        const int64_t cnt = b->gw_count[i] + b->pw_count[i] + b->sk_count[i] + b->tw_count[i] + b->dw_count[i];
         if (cnt == 0) continue;
         // throughput mode: enough copies of the problem's items to give every
         // persistent CTA (skinny: every warp; tensor cores: every SM) several,
@@ -1231,7 +1314,8 @@ extern "C" int gett_batch_profile(gett_batch *b, int reps, int mode, float *ms_o
                        b->d_skinny_by_problem + b->sk_start[i], b->sk_count[i],
                        red >= 0 ? b->d_reduce + red : nullptr, red >= 0 ? 1 : 0, copies,
                        b->d_tc_work_by_problem + b->tw_start[i], b->tw_count[i],
-                       b->d_tc_pack + b->tk_start[i], b->tk_count[i]};
+                       b->d_tc_pack + b->tk_start[i], b->tk_count[i],
+                       b->d_direct_by_problem + b->dw_start[i], b->dw_count[i]};
         // one problem runs one method: its chain needs no branch streams (and
         // every configuration is timed on the same single stream)
         e = enqueue_ranges(b, r, s, false);  // warm-up
@@ -1259,11 +1343,11 @@ extern "C" int gett_batch_get_info(const gett_batch *b, gett_batch_info *info)
     std::memset(info, 0, sizeof(*info));
     info->n = b->n;
     info->nonempty = b->nonempty;
-    info->tiles = b->nwork + b->npacked + b->nskinny + b->ntc;
+    info->tiles = b->nwork + b->npacked + b->nskinny + b->ntc + b->ndirect;
     info->flops = b->flops;
     for (int i = 0; i < GETT_BATCH_MAX_CONFIGS; ++i) info->config_count[i] = b->config_count[i];
     info->fallbacks = b->fallbacks;
-    info->gather_items = b->nwork;
+    info->gather_items = b->nwork + b->ndirect;
     info->packed_items = b->npacked;
     info->pack_items = b->npack;
     info->skinny_items = b->nskinny;
@@ -1279,7 +1363,7 @@ extern "C" int gett_batch_destroy(gett_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
         if (b->branch[i]) cudaStreamDestroy(b->branch[i]);
         if (b->join[i]) cudaEventDestroy(b->join[i]);
     }
@@ -1287,7 +1371,7 @@ extern "C" int gett_batch_destroy(gett_batch *b)
     void *bufs[] = {b->d_probs, b->d_work, b->d_packed_work, b->d_pack, b->d_skinny, b->d_skinny_by_problem,
                     b->d_tables, b->d_packed, b->d_counter, b->d_work_by_problem, b->d_packed_by_problem,
                     b->d_partial, b->d_reduce, b->d_tc_work, b->d_tc_work_by_problem, b->d_tc_pack,
-                    b->d_tiles16};
+                    b->d_tiles16, b->d_direct, b->d_direct_by_problem};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete b;
