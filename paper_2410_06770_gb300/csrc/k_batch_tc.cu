@@ -218,7 +218,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) batch_tc_kernel(const BatchProb 
             const BatchTables t = batch_tables(pr, tables);
             const int tmi = (int)w.y / pr.tiles_n, tni = (int)w.y % pr.tiles_n;
             const int buf = (int)(itc & 1);
-            if (!tc::mbar_wait(&accf[buf], (itc >> 1) & 1, err, kTcWaitError)) break;
+            // a warp-uniform give-up: tcgen05.ld and the shuffles below need
+            // every lane of the warp
+            const bool got = tc::mbar_wait(&accf[buf], (itc >> 1) & 1, err, kTcWaitError);
+            if (!__all_sync(0xffffffffu, got)) break;
             tc::tc_fence_after();
             const int64_t m = (int64_t)tmi * TC_BM + q * 32 + lane;
             const bool vm = m < pr.M;

@@ -182,7 +182,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         bool ok = true;
         for (int c = 0; c < chunks; ++c) {
             const int buf = c & 1;
-            if (!tc::mbar_wait(&accf[buf], (c >> 1) & 1, p.err, tc::ERR_WAIT_ACC_FULL)) {
+            // the give-up is made warp-uniform: tcgen05.ld below (and the
+            // shuffles of the store) need every lane of the warp
+            const bool got = tc::mbar_wait(&accf[buf], (c >> 1) & 1, p.err, tc::ERR_WAIT_ACC_FULL);
+            if (!__all_sync(0xffffffffu, got)) {
                 ok = false;
                 break;
             }
@@ -209,8 +212,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acce[buf]);
         }
-        if (ok && m < p.M) {
-            if (MODE == TC_MODE_MOD) {
+        if (MODE == TC_MODE_MOD) {
+            if (ok && m < p.M) {
                 const float half = 0.5f * (pm - 1.f);
                 int8_t *R = p.R + (int64_t)z * p.N * p.M;
 #pragma unroll
@@ -221,19 +224,49 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     r = r < -half ? r + pm : r;
                     if (n < p.N) R[n * p.M + m] = (int8_t)__float2int_rn(r);
                 }
-            } else {
-                float *C = p.C + (int64_t)z * p.c_slice + p.rowC[m];
-                const bool row_marked = p.flagA && p.flagA[m];
+            }
+        } else if (__all_sync(0xffffffffu, ok)) {
+            // the warp's 128 columns: lane l loads the offset and mark of
+            // columns 32 j + l (j < 4) once, and shuffles broadcast them;
+            // then C is read eight columns at a time with every load issued
+            // before the group's stores (a load after a store through
+            // another pointer cannot be hoisted above it, so one
+            // read-modify-write per column would each pay a round trip)
+            const int64_t nb = (int64_t)tn * BN + h * 128;
+            int64_t ccol[4];
+            uint32_t cskip[4];
 #pragma unroll
-                for (int i = 0; i < 128; ++i) {
-                    const int64_t n = (int64_t)tn * BN + h * 128 + i;
-                    if (n < p.N && !row_marked && !(p.flagB && p.flagB[n])) {
-                        float *dst = C + p.colC[n];
-                        if (p.smode == SCALE_ACC) *dst = *dst + res[i];
-                        else if (p.smode == SCALE_AX) *dst = p.alpha * res[i];
-                        else *dst = p.alpha * res[i] + p.beta * *dst;
-                    }
+            for (int j = 0; j < 4; ++j) {
+                const int64_t n = nb + 32 * j + lane;
+                ccol[j] = n < p.N ? p.colC[n] : 0;
+                cskip[j] = n < p.N ? (p.flagB ? p.flagB[n] : 0u) : 1u;
+            }
+            const bool row_ok = m < p.M && !(p.flagA && p.flagA[m]);
+            float *crow = p.C + (int64_t)z * p.c_slice + (m < p.M ? p.rowC[m] : 0);
+#pragma unroll
+            for (int g = 0; g < 128; g += 8) {
+                int64_t off[8];
+                bool st[8];
+                float cv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    // every lane runs both shuffles (a shuffle under a
+                    // per-lane condition would pair with other lanes' later
+                    // shuffles and return wrong offsets)
+                    const int i = g + u;
+                    off[u] = __shfl_sync(0xffffffffu, ccol[i >> 5], i & 31);
+                    const uint32_t skip = __shfl_sync(0xffffffffu, cskip[i >> 5], i & 31);
+                    st[u] = row_ok && skip == 0u;
                 }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cv[u] = st[u] && p.smode != SCALE_AX ? crow[off[u]] : 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (st[u]) {
+                        const float r = res[g + u];
+                        crow[off[u]] = p.smode == SCALE_ACC ? cv[u] + r
+                                       : (p.smode == SCALE_AX ? p.alpha * r : p.alpha * r + p.beta * cv[u]);
+                    }
             }
         }
     }

@@ -1,6 +1,7 @@
 """Run one contraction of a named workload through the C ABI, for profilers.
 
     python -m paper_2410_06770_gb300.profile_case WORKLOAD [SCALE] [--calls N] [--algo A] [--tuned]
+        [--learned] [--serial]
 
 WORKLOAD: cc, cc_perm_transA (extents a..d = SCALE, i,j = SCALE/4), stream
 (A(SCALE, SCALE, 64) x B(64, 8)), small, gemv (A(SCALE, SCALE) x B(SCALE, 2),
@@ -10,7 +11,9 @@ batched (SCALE contractions of the batched workload, one
 persistent launch per call).  gemv and inner draw uniform values on the device.  Inputs are generated on the host,
 copied once, then the call is made N times (default 2) and synchronised.
 --tuned loads the package's tuning database first (the configuration the
-bench's calls use).
+bench's calls use).  For batched: --learned selects configurations with the
+package's trained planner (the bench's learned launch), --serial launches
+every kernel on one stream (a profiler then sees one kernel at a time).
 """
 import argparse
 import sys
@@ -24,6 +27,8 @@ def main(argv=None):
     ap.add_argument("--algo", default="native")
     ap.add_argument("--prefix", default="d")
     ap.add_argument("--tuned", action="store_true")
+    ap.add_argument("--learned", action="store_true")
+    ap.add_argument("--serial", action="store_true")
     args = ap.parse_args(argv)
     import os
 
@@ -38,7 +43,10 @@ def main(argv=None):
         from . import tune
         probs = tune.draw_problems(args.scale, 7, 64)
         bufs = tune.DeviceBuffers(probs)
-        b = gb.Batch(bufs.descs)
+        if args.learned:
+            tune.install(tune.load_model(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                      "planner_mlp.npz")))
+        b = gb.Batch(bufs.descs, select="learned" if args.learned else "heuristic", serial=args.serial)
         for _ in range(args.calls):
             b.launch()
         torch.cuda.synchronize()
@@ -89,6 +97,11 @@ def main(argv=None):
         p = synth.cfg_small_dgett()
     else:
         raise SystemExit(f"unknown workload {args.workload}")
+    if args.prefix in ("s", "c"):
+        # single-precision calls read fp32 (complex64) operands
+        import numpy as np
+        t = np.float32 if args.prefix == "s" else np.complex64
+        p.A, p.B, p.C = p.A.astype(t), p.B.astype(t), p.C.astype(t)
     dA = torch.from_numpy(p.A).cuda()
     dB = torch.from_numpy(p.B).cuda()
     dC = torch.from_numpy(p.C).cuda()
