@@ -32,7 +32,7 @@ namespace gett {
 
 namespace {
 
-constexpr int TR = 32, TKP = 64, PT = 256;
+constexpr int TR = 64, TKP = 64, PT = 256;
 
 __device__ __forceinline__ uint16_t f2bf_bits(float x)
 {
@@ -58,58 +58,87 @@ struct PieceMap {
 // Writes, for every row, nblocks blocks of Kb (>= K, multiple of 64) packed
 // values; block b holds piece pm.piece[b] of the row's K values followed by
 // zeros up to Kb, so every 64-wide K tile belongs to exactly one block.
+//
+// A CTA takes 64 x 64 tiles: the tile's row and K offsets (one round trip),
+// then its 16 loads a thread, all issued before the first store to shared
+// memory, along whichever index has the smaller increment; then each thread
+// splits 8 consecutive k of one row into pieces and writes every block's
+// 8 bf16 values as one 16-byte store (the packed pitch, Kb and the tile
+// start are multiples of 8 elements, the buffer 256-byte aligned).
 template <class T>
-__global__ void __launch_bounds__(PT) pack_pieces_kernel(const T *__restrict__ src, const int64_t *__restrict__ rowT,
+__global__ void __launch_bounds__(PT, 4) pack_pieces_kernel(const T *__restrict__ src, const int64_t *__restrict__ rowT,
                                                         const int64_t *__restrict__ kT, int64_t rows, int64_t K,
                                                         int64_t Kb, int row_fast, PieceMap pm,
                                                         uint16_t *__restrict__ out, int64_t ld,
                                                         uint32_t *__restrict__ flags, uint32_t *__restrict__ any)
 {
+    static_assert(TR == 64 && TKP == 64 && PT == 256, "index split below");
     __shared__ float tile[TR][TKP + 1];
     __shared__ int64_t srow[TR];
     __shared__ int64_t sk[TKP];
     const int64_t tiles_k = (Kb + TKP - 1) / TKP;
     const int64_t ntiles = ((rows + TR - 1) / TR) * tiles_k;
+    const int tid = threadIdx.x;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t r0 = (t / tiles_k) * TR, k0 = (t % tiles_k) * TKP;
         __syncthreads();
-        if (threadIdx.x < TR) srow[threadIdx.x] = r0 + threadIdx.x < rows ? rowT[r0 + threadIdx.x] : 0;
-        if (threadIdx.x < TKP) sk[threadIdx.x] = k0 + threadIdx.x < K ? kT[k0 + threadIdx.x] : 0;
+        if (tid < TR) srow[tid] = r0 + tid < rows ? rowT[r0 + tid] : 0;
+        else if (tid < TR + TKP) sk[tid - TR] = k0 + (tid - TR) < K ? kT[k0 + (tid - TR)] : 0;
         __syncthreads();
+        constexpr int NV = TR * TKP / PT;
+        float v[NV];
 #pragma unroll
-        for (int j = 0; j < TR * TKP / PT; ++j) {
-            int e = threadIdx.x + j * PT;
-            int r, k;
-            if (row_fast) { r = e % TR; k = e / TR; }
-            else { k = e % TKP; r = e / TKP; }
-            float v = 0.f;
-            if (r0 + r < rows && k0 + k < K) v = load_as_float<T>(src + srow[r] + sk[k]);
-            tile[r][k] = v;
+        for (int j = 0; j < NV; ++j) {
+            const int e = tid + j * PT;
+            const int r = row_fast ? (e & (TR - 1)) : (e >> 6), k = row_fast ? (e >> 6) : (e & (TKP - 1));
+            v[j] = r0 + r < rows && k0 + k < K ? load_as_float<T>(src + srow[r] + sk[k]) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            const int e = tid + j * PT;
+            const int r = row_fast ? (e & (TR - 1)) : (e >> 6), k = row_fast ? (e >> 6) : (e & (TKP - 1));
+            tile[r][k] = v[j];
         }
         __syncthreads();
+        // thread: k8 = 8 (tid & 7), rows tid >> 3 and 32 + (tid >> 3)
 #pragma unroll
-        for (int j = 0; j < TR * TKP / PT; ++j) {
-            int e = threadIdx.x + j * PT;
-            int k = e % TKP, r = e / TKP;
-            if (r0 + r >= rows || k0 + k >= Kb) continue;
-            float x = tile[r][k];  // zero for k >= K
-            uint16_t hb = f2bf_bits(x);
-            if ((hb & 0x7F80u) == 0x7F80u) {
-                // Inf / NaN, or beyond the bf16 range: mark the row, pack zeros
-                // (plain stores of one value: the races are benign)
+        for (int h = 0; h < 2; ++h) {
+            const int r = (tid >> 3) + 32 * h, k8 = (tid & 7) * 8;
+            if (r0 + r >= rows) continue;
+            uint32_t hw[4], mw[4], lw[4];
+            bool bad = false;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float x = tile[r][k8 + q];  // zero for k >= K
+                uint16_t hb = f2bf_bits(x);
+                if ((hb & 0x7F80u) == 0x7F80u) {
+                    // Inf / NaN, or beyond the bf16 range: mark the row, pack zeros
+                    bad = true;
+                    x = 0.f;
+                    hb = 0;
+                }
+                const float r1 = x - bf_bits2f(hb);
+                const uint16_t mb = f2bf_bits(r1);
+                const float r2 = r1 - bf_bits2f(mb);
+                const uint16_t lb = f2bf_bits(r2);
+                const int sh = (q & 1) * 16;
+                if ((q & 1) == 0) hw[q >> 1] = mw[q >> 1] = lw[q >> 1] = 0u;
+                hw[q >> 1] |= (uint32_t)hb << sh;
+                mw[q >> 1] |= (uint32_t)mb << sh;
+                lw[q >> 1] |= (uint32_t)lb << sh;
+            }
+            if (bad) {
+                // plain stores of one value: the races are benign
                 flags[r0 + r] = 1u;
                 *any = 1u;
-                x = 0.f;
-                hb = 0;
             }
-            const float r1 = x - bf_bits2f(hb);
-            const uint16_t mb = f2bf_bits(r1);
-            const float r2 = r1 - bf_bits2f(mb);
-            const uint16_t lb = f2bf_bits(r2);
-            uint16_t *o = out + (r0 + r) * ld + k0 + k;
+            const uint4 vh = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            const uint4 vm = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+            const uint4 vl = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            uint16_t *o = out + (r0 + r) * ld + k0 + k8;
             for (int b = 0; b < pm.nblocks; ++b) {
                 const int pc = pm.piece[b];
-                o[b * Kb] = pc == 0 ? hb : (pc == 1 ? mb : lb);
+                *reinterpret_cast<uint4 *>(o + b * Kb) = pc == 0 ? vh : (pc == 1 ? vm : vl);
             }
         }
     }
@@ -214,6 +243,8 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
                             int num_sms, int *err, cudaStream_t s)
 {
     if (t != DT_F32 && t != DT_BF16) return cudaErrorInvalidValue;
+    // the packed operands start 256-byte aligned (16-byte vector stores)
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return cudaErrorInvalidValue;
     char *w = static_cast<char *>(ws);
     int64_t *rowA = reinterpret_cast<int64_t *>(w);
     int64_t *rowC = rowA + pl.M, *colB = rowC + pl.M, *colC = colB + pl.N, *kA = colC + pl.N, *kB = kA + pl.K;
@@ -246,8 +277,9 @@ cudaError_t launch_tc_split(const Plan &pl, DType t, int algo, const void *A, co
     pieces_for(split_algo, true, &pa);
     pieces_for(split_algo, false, &pb);
     auto blocks_for = [&](int64_t rows) {
+        // four resident CTAs an SM (64 registers a thread), each looping over tiles
         int64_t n = ((rows + TR - 1) / TR) * ((Kb + TKP - 1) / TKP);
-        return (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * 8));
+        return (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * 4));
     };
     // bf16 operands that TMA can read where they are skip the packing copy
     // (their Inf / NaN then meet the tensor core's IEEE arithmetic directly)
