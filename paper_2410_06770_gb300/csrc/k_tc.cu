@@ -7,7 +7,10 @@
 // The strided gather, the permutation and the precision logic live in the
 // packing kernels and in the epilogues.
 //
-// CTA = one 128 x 256 output tile of one slice.  Warp 0 issues TMA loads of
+// Persistent: one CTA per SM walks the 128 x 256 output tiles of every slice
+// with a stride of the grid; TMEM, the barriers and the shared-memory ring
+// live across its tiles, so the next tile's loads and MMAs run while the
+// epilogue finishes the previous one.  Warp 0 issues TMA loads of
 // 128x64 (A) and 256x64 (B) bf16 tiles, 128-byte swizzled, into a 4-stage
 // shared-memory ring; warp 1 owns the TMEM allocation and issues the
 // tcgen05.mma instructions (M=128, N=256, K=16, four per stage) from one
@@ -35,6 +38,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -77,10 +81,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     constexpr uint32_t NCOLS = 512;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x;
-    const int tn = tile % p.tiles_n;
-    const int tm = tile / p.tiles_n;
-    const int z = blockIdx.y;
+    // tiles t = z * tiles_m * tiles_n + tm * tiles_n + tn, this CTA's being
+    // blockIdx.x, blockIdx.x + gridDim.x, ... (the CTAs in flight work on a
+    // window of consecutive tiles: row blocks of A shared by their column
+    // tiles, one slice of B)
+    const int tiles_mn = p.tiles_m * p.tiles_n;
+    const int64_t ntile = (int64_t)tiles_mn * p.tiles_z;
     const int nkt = (p.K + BK - 1) / BK;
     const int kc = p.kc_tiles > 0 ? p.kc_tiles : (nkt > 0 ? nkt : 1);
     const int chunks = (nkt + kc - 1) / kc;
@@ -106,19 +112,30 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (lane == 0) {
             tc::prefetch_tmap(&tmA);
             tc::prefetch_tmap(&tmB);
-            int kt = 0;
-            for (; kt < nkt; ++kt) {
-                const int s = kt % STAGES;
-                if (!tc::mbar_wait(&empty[s], ((kt / STAGES) & 1) ^ 1, p.err, tc::ERR_WAIT_EMPTY)) break;
-                uint8_t *sa = base + s * STAGE_BYTES;
-                tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                tc::tma_load_3d(sa, &tmA, &full[s], kt * BK, tm * BM, z);
-                tc::tma_load_3d(sa + A_BYTES, &tmB, &full[s], kt * BK, tn * BN, z);
+            // g counts the stage fills of this CTA over all its tiles: fill g
+            // uses slot g % STAGES, phase (g / STAGES) & 1, so the ring runs
+            // on from one tile into the next
+            uint32_t g = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+                const int z = (int)(t / tiles_mn), tl = (int)(t % tiles_mn);
+                const int tm = tl / p.tiles_n, tn = tl % p.tiles_n;
+                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                    const int s = (int)(g % STAGES);
+                    if (!tc::mbar_wait(&empty[s], ((g / STAGES) & 1) ^ 1, p.err, tc::ERR_WAIT_EMPTY)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *sa = base + s * STAGE_BYTES;
+                    tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    tc::tma_load_3d(sa, &tmA, &full[s], kt * BK, tm * BM, z);
+                    tc::tma_load_3d(sa + A_BYTES, &tmB, &full[s], kt * BK, tn * BN, z);
+                }
             }
-            if (kt < nkt) {
+            if (!ok) {
                 // gave up: let the copies already issued land before the CTA
                 // exits (clock-bounded waits; the error word is already set)
-                for (int j = (kt > STAGES ? kt - STAGES : 0); j < kt; ++j)
+                for (uint32_t j = (g > STAGES ? g - STAGES : 0); j < g; ++j)
                     tc::mbar_drain(&full[j % STAGES], (j / STAGES) & 1);
             }
         }
@@ -126,37 +143,39 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
             bool ok = true;
-            int kt = 0;
-            for (int c = 0; c < chunks && ok; ++c) {
-                const int buf = c & 1;
-                if (!tc::mbar_wait(&acce[buf], ((c >> 1) & 1) ^ 1, p.err, tc::ERR_WAIT_ACC_EMPTY)) {
-                    ok = false;
-                    break;
-                }
-                tc::tc_fence_after();
-                const uint32_t d = tmem_base + buf * BN;
-                const int kend = min(nkt, (c + 1) * kc);
-                const int kbeg = kt;
-                for (; kt < kend; ++kt) {
-                    const int s = kt % STAGES;
-                    if (!tc::mbar_wait(&full[s], (kt / STAGES) & 1, p.err, tc::ERR_WAIT_FULL)) {
+            uint32_t g = 0;   // stage uses, as the producer counts them
+            uint32_t cc = 0;  // accumulator chunks over all tiles: buffer cc & 1
+            for (int64_t t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+                for (int c = 0; c < chunks; ++c, ++cc) {
+                    const int buf = (int)(cc & 1);
+                    if (!tc::mbar_wait(&acce[buf], ((cc >> 1) & 1) ^ 1, p.err, tc::ERR_WAIT_ACC_EMPTY)) {
                         ok = false;
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t sa = tc::smem_u32(base + s * STAGE_BYTES);
-                    const uint64_t ad = tc::smem_desc_sw128(sa);
-                    const uint64_t bd = tc::smem_desc_sw128(sa + A_BYTES);
+                    const uint32_t d = tmem_base + buf * BN;
+                    const int kbeg = c * kc, kend = min(nkt, (c + 1) * kc);
+                    for (int kt = kbeg; kt < kend; ++kt, ++g) {
+                        const int s = (int)(g % STAGES);
+                        if (!tc::mbar_wait(&full[s], (g / STAGES) & 1, p.err, tc::ERR_WAIT_FULL)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        const uint32_t sa = tc::smem_u32(base + s * STAGE_BYTES);
+                        const uint64_t ad = tc::smem_desc_sw128(sa);
+                        const uint64_t bd = tc::smem_desc_sw128(sa + A_BYTES);
 #pragma unroll
-                    for (int j = 0; j < BK / 16; ++j) {
-                        // advance 16 bf16 (32 bytes) along K inside the swizzled row
-                        tc::umma_bf16(d, ad + (uint64_t)(j * 2), bd + (uint64_t)(j * 2), idesc,
-                                      (kt > kbeg || j > 0) ? 1u : 0u);
+                        for (int j = 0; j < BK / 16; ++j) {
+                            // advance 16 bf16 (32 bytes) along K inside the swizzled row
+                            tc::umma_bf16(d, ad + (uint64_t)(j * 2), bd + (uint64_t)(j * 2), idesc,
+                                          (kt > kbeg || j > 0) ? 1u : 0u);
+                        }
+                        tc::umma_commit(&empty[s]);
                     }
-                    tc::umma_commit(&empty[s]);
+                    if (!ok) break;
+                    tc::umma_commit(&accf[buf]);
                 }
-                if (!ok) break;
-                tc::umma_commit(&accf[buf]);
             }
             if (!ok) {
                 // gave up with MMAs possibly still writing TMEM: one more commit
@@ -167,106 +186,114 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
         }
     } else {
-        // epilogue warps
+        // epilogue warps: the same tiles in the same order; the chunk count
+        // cc runs on across tiles like the MMA warp's, so while these warps
+        // finish a tile (its last fold and its store) the MMAs of the next
+        // tile already fill the other accumulator
         const int ew = warp - 2;
         const int q = warp & 3;   // TMEM lane quarter this warp may access
         const int h = ew >> 2;    // 128-column half
         const int row = q * 32 + lane;
-        const int64_t m = (int64_t)tm * BM + row;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-        const float pm = MODE == TC_MODE_MOD ? c_moduli[z] : 1.f;
-        const float inv = 1.0f / pm;
-        float res[128];
-#pragma unroll
-        for (int i = 0; i < 128; ++i) res[i] = 0.f;
+        uint32_t cc = 0;
         bool ok = true;
-        for (int c = 0; c < chunks; ++c) {
-            const int buf = c & 1;
-            // the give-up is made warp-uniform: tcgen05.ld below (and the
-            // shuffles of the store) need every lane of the warp
-            const bool got = tc::mbar_wait(&accf[buf], (c >> 1) & 1, p.err, tc::ERR_WAIT_ACC_FULL);
-            if (!__all_sync(0xffffffffu, got)) {
-                ok = false;
-                break;
-            }
-            tc::tc_fence_after();
+        for (int64_t t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+            const int z = (int)(t / tiles_mn), tl = (int)(t % tiles_mn);
+            const int tm = tl / p.tiles_n, tn = tl % p.tiles_n;
+            const int64_t m = (int64_t)tm * BM + row;
+            const float pm = MODE == TC_MODE_MOD ? c_moduli[z] : 1.f;
+            const float inv = 1.0f / pm;
+            float res[128];
 #pragma unroll
-            for (int cb = 0; cb < 4; ++cb) {
-                uint32_t v[32];
-                tc::tmem_ld_32x32b_x32(tmem_base + lane_addr + buf * BN + h * 128 + cb * 32, v);
-                tc::tmem_ld_wait();
+            for (int i = 0; i < 128; ++i) res[i] = 0.f;
+            for (int c = 0; c < chunks; ++c, ++cc) {
+                const int buf = (int)(cc & 1);
+                // the give-up is made warp-uniform: tcgen05.ld below (and the
+                // shuffles of the store) need every lane of the warp
+                const bool got = tc::mbar_wait(&accf[buf], (cc >> 1) & 1, p.err, tc::ERR_WAIT_ACC_FULL);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const float x = res[cb * 32 + i] + __uint_as_float(v[i]);
-                    if (MODE == TC_MODE_MOD) {
-                        // exact: |res| <= p/2 + 3 and |chunk sum| < 2^24 - 2^8;
-                        // q = nearest integer of x / p via the 1.5 * 2^23 constant
-                        const float qq = __fadd_rn(__fmaf_rn(x, inv, 12582912.0f), -12582912.0f);
-                        res[cb * 32 + i] = fmaf(-qq, pm, x);
-                    } else {
-                        res[cb * 32 + i] = x;
+                for (int cb = 0; cb < 4; ++cb) {
+                    uint32_t v[32];
+                    tc::tmem_ld_32x32b_x32(tmem_base + lane_addr + buf * BN + h * 128 + cb * 32, v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float x = res[cb * 32 + i] + __uint_as_float(v[i]);
+                        if (MODE == TC_MODE_MOD) {
+                            // exact: |res| <= p/2 + 3 and |chunk sum| < 2^24 - 2^8;
+                            // q = nearest integer of x / p via the 1.5 * 2^23 constant
+                            const float qq = __fadd_rn(__fmaf_rn(x, inv, 12582912.0f), -12582912.0f);
+                            res[cb * 32 + i] = fmaf(-qq, pm, x);
+                        } else {
+                            res[cb * 32 + i] = x;
+                        }
                     }
                 }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&acce[buf]);
             }
-            tc::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&acce[buf]);
-        }
-        if (MODE == TC_MODE_MOD) {
-            if (ok && m < p.M) {
-                const float half = 0.5f * (pm - 1.f);
-                int8_t *R = p.R + (int64_t)z * p.N * p.M;
+            if (MODE == TC_MODE_MOD) {
+                if (ok && m < p.M) {
+                    const float half = 0.5f * (pm - 1.f);
+                    int8_t *R = p.R + (int64_t)z * p.N * p.M;
 #pragma unroll
-                for (int i = 0; i < 128; ++i) {
-                    const int64_t n = (int64_t)tn * BN + h * 128 + i;
-                    float r = res[i];
-                    r = r > half ? r - pm : r;
-                    r = r < -half ? r + pm : r;
-                    if (n < p.N) R[n * p.M + m] = (int8_t)__float2int_rn(r);
-                }
-            }
-        } else if (__all_sync(0xffffffffu, ok)) {
-            // the warp's 128 columns: lane l loads the offset and mark of
-            // columns 32 j + l (j < 4) once, and shuffles broadcast them;
-            // then C is read eight columns at a time with every load issued
-            // before the group's stores (a load after a store through
-            // another pointer cannot be hoisted above it, so one
-            // read-modify-write per column would each pay a round trip)
-            const int64_t nb = (int64_t)tn * BN + h * 128;
-            int64_t ccol[4];
-            uint32_t cskip[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int64_t n = nb + 32 * j + lane;
-                ccol[j] = n < p.N ? p.colC[n] : 0;
-                cskip[j] = n < p.N ? (p.flagB ? p.flagB[n] : 0u) : 1u;
-            }
-            const bool row_ok = m < p.M && !(p.flagA && p.flagA[m]);
-            float *crow = p.C + (int64_t)z * p.c_slice + (m < p.M ? p.rowC[m] : 0);
-#pragma unroll
-            for (int g = 0; g < 128; g += 8) {
-                int64_t off[8];
-                bool st[8];
-                float cv[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    // every lane runs both shuffles (a shuffle under a
-                    // per-lane condition would pair with other lanes' later
-                    // shuffles and return wrong offsets)
-                    const int i = g + u;
-                    off[u] = __shfl_sync(0xffffffffu, ccol[i >> 5], i & 31);
-                    const uint32_t skip = __shfl_sync(0xffffffffu, cskip[i >> 5], i & 31);
-                    st[u] = row_ok && skip == 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) cv[u] = st[u] && p.smode != SCALE_AX ? crow[off[u]] : 0.f;
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (st[u]) {
-                        const float r = res[g + u];
-                        crow[off[u]] = p.smode == SCALE_ACC ? cv[u] + r
-                                       : (p.smode == SCALE_AX ? p.alpha * r : p.alpha * r + p.beta * cv[u]);
+                    for (int i = 0; i < 128; ++i) {
+                        const int64_t n = (int64_t)tn * BN + h * 128 + i;
+                        float r = res[i];
+                        r = r > half ? r - pm : r;
+                        r = r < -half ? r + pm : r;
+                        if (n < p.N) R[n * p.M + m] = (int8_t)__float2int_rn(r);
                     }
+                }
+            } else if (__all_sync(0xffffffffu, ok)) {
+                // the warp's 128 columns: lane l loads the offset and mark of
+                // columns 32 j + l (j < 4) once, and shuffles broadcast them;
+                // then C is read eight columns at a time with every load issued
+                // before the group's stores (a load after a store through
+                // another pointer cannot be hoisted above it, so one
+                // read-modify-write per column would each pay a round trip)
+                const int64_t nb = (int64_t)tn * BN + h * 128;
+                int64_t ccol[4];
+                uint32_t cskip[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t n = nb + 32 * j + lane;
+                    ccol[j] = n < p.N ? p.colC[n] : 0;
+                    cskip[j] = n < p.N ? (p.flagB ? p.flagB[n] : 0u) : 1u;
+                }
+                const bool row_ok = m < p.M && !(p.flagA && p.flagA[m]);
+                float *crow = p.C + (int64_t)z * p.c_slice + (m < p.M ? p.rowC[m] : 0);
+#pragma unroll
+                for (int g = 0; g < 128; g += 8) {
+                    int64_t off[8];
+                    bool st[8];
+                    float cv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        // every lane runs both shuffles (a shuffle under a
+                        // per-lane condition would pair with other lanes' later
+                        // shuffles and return wrong offsets)
+                        const int i = g + u;
+                        off[u] = __shfl_sync(0xffffffffu, ccol[i >> 5], i & 31);
+                        const uint32_t skip = __shfl_sync(0xffffffffu, cskip[i >> 5], i & 31);
+                        st[u] = row_ok && skip == 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) cv[u] = st[u] && p.smode != SCALE_AX ? crow[off[u]] : 0.f;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (st[u]) {
+                            const float r = res[g + u];
+                            crow[off[u]] = p.smode == SCALE_ACC ? cv[u] + r
+                                           : (p.smode == SCALE_AX ? p.alpha * r : p.alpha * r + p.beta * cv[u]);
+                        }
+                }
             }
         }
     }
@@ -350,9 +377,16 @@ cudaError_t launch_tc_gemm(int mode, const void *Ap, const void *Bp, int64_t Z, 
     TcGemmParams p = prm;
     p.tiles_m = (int)((p.M + BM - 1) / BM);
     p.tiles_n = (int)((p.N + BN - 1) / BN);
+    p.tiles_z = (int)Z;
     if ((int64_t)p.tiles_m * p.tiles_n > INT32_MAX) return cudaErrorInvalidValue;
-    dim3 grid(p.tiles_m * p.tiles_n, (unsigned)Z);
-    cudaError_t e;
+    // persistent: one CTA per SM (its shared memory and 512 TMEM columns
+    // allow no second), each walking the tiles with a stride of the grid
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t ntile = (int64_t)p.tiles_m * p.tiles_n * Z;
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ntile, sms)));
     if (mode == TC_MODE_MOD) {
         if (p.kc_tiles < 1 || p.kc_tiles * BK > OZ_CHUNK_K) return cudaErrorInvalidValue;
         e = cudaFuncSetAttribute(tc_gemm_kernel<TC_MODE_MOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,

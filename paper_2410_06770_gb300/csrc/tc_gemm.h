@@ -18,7 +18,7 @@ constexpr int OZ_CHUNK_K = 1024;
 
 struct TcGemmParams {
     int64_t M, N, K;     // D_z is M x N, sum over K
-    int tiles_m, tiles_n;  // filled by the launcher
+    int tiles_m, tiles_n, tiles_z;  // filled by the launcher (tiles_z = Z)
     int kc_tiles;        // MODE_MOD: 64-wide K tiles per exact fp32 chunk
     int *err;            // device error word (bounded waits)
     // MODE_MOD: slice z is reduced modulo kOzModuli[z]
