@@ -9,7 +9,10 @@
 // the tile kernel stages its operands with bulk copies (cp.async.bulk, an
 // mbarrier per stage) through a ring of PSTAGES shared-memory stages instead
 // of chains of gathered loads.  bf16 operands are widened exactly to fp32
-// while packing.
+// while packing.  Within a K step the block's rows are interleaved -- row w
+// at position (w % 16) T + w / 16, T = bw / 16 the register tile's height --
+// so the T rows one thread multiplies are adjacent and arrive as one vector
+// read from shared memory.
 //
 // The packing kernel reads a 64 x bm (bn) block of the strided operand along
 // whichever of its two indices has the smaller increment, transposes it
@@ -88,10 +91,16 @@ __global__ void __launch_bounds__(256, 4) batch_pack_kernel(const BatchProb *__r
             if (w < bw && kk < klen) tile[kk][w] = v[u];
         }
         __syncthreads();
+        // rows interleaved for the tile kernel: row w goes to position
+        // (w % 16) T + w / 16, T = bw / 16 (every shape's register tile),
+        // so a thread's T rows w = t + 16 i are adjacent; written in
+        // position order (coalesced), read from the row they hold
         const int nel = bw * klen;
+        const int T = bw >> 4;
         for (int e = tid; e < nel; e += 256) {
-            const int kk = e >> lbw, w = e & (bw - 1);
-            dst[(int64_t)kk * bw + w] = tile[kk][w];
+            const int kk = e >> lbw, pos = e & (bw - 1);
+            const int w = (pos % T) * 16 + pos / T;
+            dst[(int64_t)kk * bw + pos] = tile[kk][w];
         }
     }
 }
@@ -99,6 +108,19 @@ __global__ void __launch_bounds__(256, 4) batch_pack_kernel(const BatchProb *__r
 // ---------------------------------------------------------------------------
 // packed tiles
 // ---------------------------------------------------------------------------
+// T consecutive floats of shared memory (T = 2 or 4, aligned to T floats)
+template <int T>
+__device__ __forceinline__ void load_run(const float *p, float (&v)[T])
+{
+    static_assert(T == 2 || T == 4, "register tile of 2 or 4");
+    if constexpr (T == 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else {
+        const float2 x = *reinterpret_cast<const float2 *>(p);
+        v[0] = x.x; v[1] = x.y;
+    }
+}
 constexpr int PSTAGES = 6;
 constexpr int PBK = 16;  // every shape's BK
 constexpr int PSTAGE_FLOATS = PBK * 128;  // largest bm + bn is 128
@@ -209,11 +231,11 @@ __device__ __forceinline__ bool packed_tile(const BatchProb &pr, const int64_t *
             const float *sB = sA + PBK * BM;
 #pragma unroll
             for (int kk = 0; kk < PBK; ++kk) {
+                // the packed rows are interleaved (row w at (w % 16) TM + w / 16):
+                // a thread's TM rows tm + 16 i sit side by side, one vector read
                 float a[TM], b[TN];
-#pragma unroll
-                for (int i = 0; i < TM; ++i) a[i] = sA[kk * BM + tm + i * RM];
-#pragma unroll
-                for (int j = 0; j < TN; ++j) b[j] = sB[kk * BN + tn + j * RN];
+                load_run<TM>(sA + kk * BM + tm * TM, a);
+                load_run<TN>(sB + kk * BN + tn * TN, b);
 #pragma unroll
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -518,7 +540,10 @@ void launch_batch_pack(int blocks, cudaStream_t s, const BatchProb *probs, const
     if (n > 0) batch_pack_kernel<<<blocks, 256, 0, s>>>(probs, items, n, wrap, tables);
 }
 
-int batch_packed_ctas_per_sm() { return 4; }
+// three resident CTAs an SM: 80 registers a thread hold the register tile,
+// the read-ahead descriptor and the ring's counters without spilling (at
+// four, 64 registers spilled inside the K loop)
+int batch_packed_ctas_per_sm() { return 3; }
 
 void launch_batch_packed_tiles(int cps, int ctas, cudaStream_t s, const BatchProb *probs, const uint2 *work,
                                int64_t nwork, int64_t wrap, const int64_t *tables, int *err)
@@ -526,9 +551,9 @@ void launch_batch_packed_tiles(int cps, int ctas, cudaStream_t s, const BatchPro
     if (nwork <= 0) return;
     (void)cps;
     static const cudaError_t attr =
-        cudaFuncSetAttribute(batch_packed_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PSMEM);
+        cudaFuncSetAttribute(batch_packed_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PSMEM);
     (void)attr;
-    batch_packed_kernel<4><<<ctas, BT, PSMEM, s>>>(probs, work, nwork, wrap, tables, err);
+    batch_packed_kernel<3><<<ctas, BT, PSMEM, s>>>(probs, work, nwork, wrap, tables, err);
 }
 
 void launch_batch_skinny(int blocks, cudaStream_t s, const BatchProb *probs, const SkinnyItem *items, int64_t n,
