@@ -330,50 +330,63 @@ __global__ void __launch_bounds__(PT) oz_residue_kernel(const double *__restrict
         cp_async_wait<OZ_STAGES - 1>();
         __syncthreads();
         const int64_t r0 = (t / tiles_k) * RTR, k0 = (t % tiles_k) * RTKP;
+        // a thread takes 8 consecutive k of one row (four f32x2 pairs) and
+        // writes each plane's 8 residues as one 16-byte store (the pitch,
+        // the plane pitch and the tile start are multiples of 8 elements,
+        // the planes 16-byte aligned: checked by the launcher)
+        static_assert(RTR * RTKP == 8 * PT, "one group of 8 a thread");
+        {
+            const int r = threadIdx.x >> 3, k = (threadIdx.x & 7) * 8;
+            if (r0 + r < rows && k0 + k < K) {
+                constexpr uint64_t kNeg2p23 = pair_bits(0xCB000000u, 0xCB000000u);  // -2^23
+                uint64_t limb[4][4];  // [pair][limb]
 #pragma unroll
-        for (int j = 0; j < RTR * RTKP / (2 * PT); ++j) {
-            const int e = threadIdx.x + j * PT;
-            const int kp = e % (RTKP / 2), r = e / (RTKP / 2);
-            const int k = 2 * kp;
-            if (r0 + r >= rows || k0 + k >= K) continue;
-            // four 13-bit limbs of the scaled integer, sign applied to the limbs,
-            // converted to float through the 2^23 mantissa (no conversion op);
-            // the two elements travel as one f32x2 pair
-            uint32_t lb[4][2], sgb[2];
+                for (int pq = 0; pq < 4; ++pq) {
+                    // four 13-bit limbs of the scaled integer, sign applied to the
+                    // limbs, converted to float through the 2^23 mantissa (no
+                    // conversion op); the two elements travel as one f32x2 pair
+                    uint32_t lb[4][2], sgb[2];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const uint64_t bits = tile(buf, r, k + u);
-                const uint64_t v = scaled_int(bits & 0x7FFFFFFFFFFFFFFFull, sshift[buf][r]);
-                // k >= neg_from: the value enters negated (the -Im block of the
-                // real form of a complex matrix)
-                const bool neg = ((bits >> 63) != 0) != (k0 + k + u >= neg_from);
-                sgb[u] = neg ? 0xBF800000u : 0x3F800000u;  // -1.0f / 1.0f
-                lb[0][u] = 0x4B000000u | (uint32_t)(v & 0x1FFF);
-                lb[1][u] = 0x4B000000u | (uint32_t)((v >> 13) & 0x1FFF);
-                lb[2][u] = 0x4B000000u | (uint32_t)((v >> 26) & 0x1FFF);
-                lb[3][u] = 0x4B000000u | (uint32_t)(v >> 39);
-            }
-            constexpr uint64_t kNeg2p23 = pair_bits(0xCB000000u, 0xCB000000u);  // -2^23
-            const uint64_t sg = pair_bits(sgb[0], sgb[1]);
-            uint64_t limb[4];
+                    for (int u = 0; u < 2; ++u) {
+                        const int kk = k + 2 * pq + u;
+                        const uint64_t bits = tile(buf, r, kk);
+                        const uint64_t v = scaled_int(bits & 0x7FFFFFFFFFFFFFFFull, sshift[buf][r]);
+                        // k >= neg_from: the value enters negated (the -Im block of
+                        // the real form of a complex matrix)
+                        const bool neg = ((bits >> 63) != 0) != (k0 + kk >= neg_from);
+                        sgb[u] = neg ? 0xBF800000u : 0x3F800000u;  // -1.0f / 1.0f
+                        lb[0][u] = 0x4B000000u | (uint32_t)(v & 0x1FFF);
+                        lb[1][u] = 0x4B000000u | (uint32_t)((v >> 13) & 0x1FFF);
+                        lb[2][u] = 0x4B000000u | (uint32_t)((v >> 26) & 0x1FFF);
+                        lb[3][u] = 0x4B000000u | (uint32_t)(v >> 39);
+                    }
+                    const uint64_t sg = pair_bits(sgb[0], sgb[1]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) limb[i] = mul2(add2(pair_bits(lb[i][0], lb[i][1]), kNeg2p23), sg);
-            constexpr uint64_t kMagic = pair_bits(0x4B400000u, 0x4B400000u);     // 1.5 * 2^23
-            constexpr uint64_t kNegMagic = pair_bits(0xCB400000u, 0xCB400000u);
-            uint32_t *o = reinterpret_cast<uint32_t *>(out + (r0 + r) * ld + k0 + k);
-            const int64_t plane2 = plane / 2;  // plane pitch in 32-bit words (plane is even)
+                    for (int q = 0; q < 4; ++q) limb[pq][q] = mul2(add2(pair_bits(lb[q][0], lb[q][1]), kNeg2p23), sg);
+                }
+                constexpr uint64_t kMagic = pair_bits(0x4B400000u, 0x4B400000u);     // 1.5 * 2^23
+                constexpr uint64_t kNegMagic = pair_bits(0xCB400000u, 0xCB400000u);
+                uint4 *o = reinterpret_cast<uint4 *>(out + (r0 + r) * ld + k0 + k);
+                const int64_t plane16 = plane / 8;  // plane pitch in 16-byte units
 #pragma unroll
-            for (int l = 0; l < L; ++l, o += plane2) {
-                // |s| <= 127 * 3 * 8191 + 8192 < 2^22: exact; nearest rounding of
-                // s / p is exact for odd p, so the residue lies in [-(p-1)/2, (p-1)/2]
-                uint64_t sum = fma2(limb[1], c.k13[l], limb[0]);
-                sum = fma2(limb[2], c.k26[l], sum);
-                sum = fma2(limb[3], c.k39[l], sum);
-                const uint64_t q = add2(fma2(sum, c.kinv[l], kMagic), kNegMagic);
-                const uint64_t x = fma2(q, c.knegp[l], sum);
-                // |x| <= 127 has at most 7 significant bits: its bf16 pattern is the
-                // upper half of the fp32 pattern; pack both upper halves at once
-                *o = __byte_perm((uint32_t)x, (uint32_t)(x >> 32), 0x7632);
+                for (int l = 0; l < L; ++l, o += plane16) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int pq = 0; pq < 4; ++pq) {
+                        // |s| <= 127 * 3 * 8191 + 8192 < 2^22: exact; nearest
+                        // rounding of s / p is exact for odd p, so the residue
+                        // lies in [-(p-1)/2, (p-1)/2]
+                        uint64_t sum = fma2(limb[pq][1], c.k13[l], limb[pq][0]);
+                        sum = fma2(limb[pq][2], c.k26[l], sum);
+                        sum = fma2(limb[pq][3], c.k39[l], sum);
+                        const uint64_t q = add2(fma2(sum, c.kinv[l], kMagic), kNegMagic);
+                        const uint64_t x = fma2(q, c.knegp[l], sum);
+                        // |x| <= 127 has at most 7 significant bits: its bf16
+                        // pattern is the upper half of the fp32 pattern
+                        w[pq] = __byte_perm((uint32_t)x, (uint32_t)(x >> 32), 0x7632);
+                    }
+                    *o = make_uint4(w[0], w[1], w[2], w[3]);
+                }
             }
         }
         __syncthreads();
@@ -409,6 +422,9 @@ cudaError_t launch_residues(const double *src, const int64_t *rowT, const int64_
 {
     if (plane < 0) plane = rows * ld;
     if (neg_from < 0) neg_from = K;
+    // 16-byte stores of 8 residues: the planes, the pitch and the plane pitch
+    // must keep every group of 8 on a 16-byte boundary
+    if ((reinterpret_cast<uintptr_t>(out) & 15) || (ld & 7) || (plane & 7)) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
 #define CASE(LL)                                                                                          \
     case LL:                                                                                              \
