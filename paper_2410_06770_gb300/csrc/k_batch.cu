@@ -1,18 +1,20 @@
-// k_batch.cu -- thousands of xGETT contractions in one persistent launch.
+// k_batch.cu -- thousands of xGETT contractions in one batched launch.
 //
 // gett_batch_create plans every problem on the host (validation, squeeze,
-// flips, fusion -- the same planner as single calls), picks a tile
-// configuration per problem (heuristic, fixed, caller table or learned
-// model), decodes the offset tables of all problems into one buffer, and
-// builds a work list with one entry per output tile, sorted by decreasing
-// tile cost so long tiles start first.  The persistent kernel runs
-// ctas_per_sm CTAs per SM; each CTA takes the next work item from an atomic
-// counter and computes that tile with the shared CUDA-core tile routine
-// (float arithmetic; bf16 operands are widened on load).  Tiles whose K
-// extent would make them far longer than a CTA's average share are split
-// into K slices; slices write partial tiles that a second kernel adds into C
-// in slice order.  Every output element is therefore summed in a fixed order
-// and results do not depend on scheduling.
+// flips, fusion -- the same planner as single calls), picks a configuration
+// per problem (heuristic, fixed, caller table, tuning database or learned
+// model: a tile shape and a method), decodes the offset tables of all
+// problems into one buffer, and builds one work list per method, sorted by
+// decreasing cost so long items start first.  This file holds the gathered
+// tiles (persistent CTAs taking items from an atomic counter and computing a
+// tile through the offset tables), the short sums (their own kernel and
+// counter), the ordered reduction of K-slice partials and the launch itself:
+// the method chains run as concurrent branches of one stream-ordered (and
+// graph-capturable) launch.  Tiles whose K extent would make them far longer
+// than a CTA's average share are split into K slices; slices write partial
+// tiles that the reduction adds into C in slice order.  Every output element
+// is therefore summed in a fixed order and results do not depend on
+// scheduling.
 #include <cuda_runtime.h>
 
 #include <algorithm>
