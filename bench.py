@@ -13,7 +13,7 @@ permutation (i,a,j,b) and row-major A, the streaming outer product, the small
 cores (every output compared with the native FP64 call), every precision form
 on log-uniform data (against native FP64 on the same inputs), complex
 split ZGETT), the inner product (REDUCE) and matrix-vector (SKINNY) kernels
-against their HBM and FP64-FMA floors, and the batched persistent launch of
+against their HBM and FP64-FMA floors, and the batched launch of
 4096 contractions (heuristic, tuned and learned configurations).
 
 `e2e`: the same call with pinned host buffers; each step's uploads of A, B, C
@@ -685,7 +685,7 @@ TUNE_DB = os.path.join(ROOT, "paper_2410_06770_gb300", "tune_db.txt")
 
 
 def measure_batched(n=4096, ffma_tflops=None):
-    """The batched workload: one persistent launch (CUDA graph replay) for all
+    """The batched workload: one batched launch (CUDA graph replay) for all
     contractions vs one plain call per contraction, with heuristic, tuned and
     (if a trained model is committed) learned tile configurations.  Roofline:
     the sum over problems of max(2|C|K / FFMA peak, bytes / HBM), bytes = A

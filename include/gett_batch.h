@@ -1,5 +1,5 @@
 /*
- * gett_batch.h -- many xGETT contractions in one persistent launch
+ * gett_batch.h -- many xGETT contractions in one batched launch
  * (extension; the thesis defines single calls only, Sec. 5.7).
  *
  * Each problem is a full xGETT call (the 14 arguments of Sec. 5.7, same
@@ -8,20 +8,21 @@
  * every problem on the host, chooses a configuration per problem (a method
  * and a tile shape, below), uploads one descriptor table, one offset-table
  * buffer and the work lists, and returns an opaque handle.
- * gett_batch_launch enqueues the whole batch as one fixed sequence of
- * persistent kernels on one stream -- packing of the tensor-core problems'
- * operands, their tensor-core tiles, packing of the packed problems'
- * operands, packed tiles, gathered tiles and short sums, skinny warp items,
- * the ordered addition of K-slice partials -- with the tiles of the
- * gathered kernel taken from an atomic work counter and the others dealt to
- * the CTAs statically; gett_batch_launch_graph does the same through a CUDA graph
- * captured on first use and replayed afterwards.
+ * gett_batch_launch enqueues the whole batch as per-method chains of
+ * persistent kernels -- packing + packed tiles, tensor-core packing +
+ * tensor-core tiles, gathered tiles, skinny warp items, short sums -- which
+ * run as concurrent branches forked from the launch stream (or in order on
+ * it, with options.serial), then the ordered addition of K-slice partials;
+ * the gathered tiles and the short sums take items from atomic work
+ * counters, the others deal them to the CTAs statically.
+ * gett_batch_launch_graph does the same through a CUDA graph captured on
+ * first use and replayed afterwards.
  *
  * Configurations (gett_batch_num_configs() of them):
  *   0..3  GATHER with tile shape 0..3: tiles read A and B through the
  *         planner's class offset tables (its logical mode fusion only);
  *         sums of at most 8 terms form their outputs straight from gathered
- *         loads whatever the method;
+ *         loads (a kernel of their own);
  *   4..7  PACK with tile shape 0..3: A and B are first copied into
  *         tile-blocked dense matrices (each class's modes physically fused
  *         into one contiguous index; bf16 widened to float), which the tiles
@@ -108,7 +109,8 @@ typedef struct gett_batch_info {
     double flops;             /* 2*M*N*K summed over problems               */
     int config_count[GETT_BATCH_MAX_CONFIGS]; /* problems per configuration */
     int fallbacks;            /* learned/table choices replaced by the heuristic */
-    int64_t gather_items;     /* work items of each kernel of a launch      */
+    int64_t gather_items;     /* work items of each kernel of a launch
+                                 (gathered tiles and short-sum tile runs)   */
     int64_t packed_items;
     int64_t pack_items;
     int64_t skinny_items;

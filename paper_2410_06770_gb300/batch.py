@@ -1,4 +1,4 @@
-"""ctypes binding of the batched persistent launch (gett_batch.h) and of the
+"""ctypes binding of the batched launch (gett_batch.h) and of the
 learned planner's network (gett_learn.h).  Argument marshalling only."""
 from __future__ import annotations
 

@@ -622,7 +622,7 @@ struct gett_batch {
     int64_t ntc = 0, ntcpack = 0;
     int64_t *d_tables = nullptr;
     float *d_packed = nullptr;           // tile-blocked operands of packed problems
-    unsigned long long *d_counter = nullptr;  // work counter of the gather kernel (and one spare)
+    unsigned long long *d_counter = nullptr;  // work counters: [0] gathered tiles, [1] short sums
     // every list again grouped by problem (the autotuner times one problem)
     uint2 *d_work_by_problem = nullptr;
     uint2 *d_direct = nullptr;               // short-sum tile runs (sorted) and grouped by problem
