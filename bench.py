@@ -380,7 +380,7 @@ def gpu_arm(args, dist: Dist):
 
     if not args.no_e2e:
         result["e2e"] = e2e_measure(p, flops, call_host=None, dA=dA, dB=dB, dC=dC, a=a, stream=stream,
-                                    steps=args.steps)
+                                    steps=args.steps, dev=dev)
     held = {}
     if not args.no_forms and dist.world == 1:
         del dA, dB, dC
@@ -461,7 +461,7 @@ def cpu_baseline_leg(p, seconds, held, plain_tflops):
     return cpu, split
 
 
-def e2e_measure(p, flops, call_host, dA, dB, dC, a, stream, steps):
+def e2e_measure(p, flops, call_host, dA, dB, dC, a, stream, steps, dev=0):
     """Host buffers in pinned memory.  Every step copies its A, B and C from
     the host, runs the dgett call and copies C back, all inside the timed
     region.  Two device buffer sets and separate H2D / D2H streams let step
@@ -476,7 +476,9 @@ def e2e_measure(p, flops, call_host, dA, dB, dC, a, stream, steps):
     outs = [torch.empty_like(hC).pin_memory(), torch.empty_like(hC).pin_memory()]
     h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def run(nsteps, e_start=None):
+    calls = []  # (start, end) events of each timed call on the compute stream
+
+    def run(nsteps, timed=False):
         free = [None, None]
         for i in range(nsteps):
             k = i % 2
@@ -490,9 +492,14 @@ def e2e_measure(p, flops, call_host, dA, dB, dC, a, stream, steps):
                 ready = torch.cuda.Event()
                 ready.record(h2d)
             stream.wait_event(ready)
+            if timed:
+                calls.append((torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)))
+                calls[-1][0].record(stream)
             gett.xgett("d", a["RANKA"], a["EXTA"], a["INCA"], xA, a["RANKB"], a["EXTB"], a["INCB"], xB,
                        a["CONTS"], a["CONTA"], a["CONTB"], a["PERM"], a["INCC"], xC,
                        a_off=p.la.off, b_off=p.lb.off, c_off=p.lc.off, mode="async", stream=stream.cuda_stream)
+            if timed:
+                calls[-1][1].record(stream)
             done = torch.cuda.Event()
             done.record(stream)
             with torch.cuda.stream(d2h):
@@ -507,17 +514,24 @@ def e2e_measure(p, flops, call_host, dA, dB, dC, a, stream, steps):
     run(2)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(dev)
+    sampler.start()
     e0.record(stream)
     h2d.wait_stream(stream)
-    run(steps)
+    run(steps, timed=True)
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / steps
+    call_ms = statistics.mean(c0.elapsed_time(c1) for c0, c1 in calls)
     bi = hA.numel() * 8 + hB.numel() * 8 + hC.numel() * 8
     bo = outs[0].numel() * 8
     del sets[1]
+    # call_ms: the contraction alone inside this pipeline (device time between
+    # its stream's events), to tell copy overhead from a slower call
     return {"value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": bi,
-            "d2h_bytes_per_step": bo, "ms_per_step": ms, "steps": steps,
+            "d2h_bytes_per_step": bo, "ms_per_step": ms, "steps": steps, "call_ms": call_ms,
+            "clocks": clocks,
             "pipeline": "2 device buffer sets; H2D of step i+1 overlaps the call of step i"}
 
 
